@@ -1,0 +1,272 @@
+/*
+ * mrhs.h - C ABI of the GB300 multiple-right-hand-side (MRHS) multigrid
+ * solver for the Wilson-clover Dirac equation (arXiv:2211.13719).
+ *
+ * The library solves D x = b for many right-hand sides (RHS) at once on one
+ * GPU (Sec. 1-2 of the paper: MRHS turns the many independent solves into
+ * one batched solve, reusing every gauge link and coarse link for all RHS).
+ *
+ * Conventions used by every call below
+ * ------------------------------------
+ * Lattice        dims = {Lx, Ly, Lz, Lt}; site index x + Lx*(y + Ly*(z + Lz*t)).
+ * Gauge field    [V][4][3][3] complex, interleaved (re, im); U[x][mu] is the
+ *                link from x to x + mu_hat, mu = 0..3 = x, y, z, t.
+ * Spinor fields  [V][12][nrhs] complex, component s*3 + c (spin s, colour c),
+ *                RHS index innermost (Sec. 2: one link load serves all RHS).
+ * Gamma basis    chiral: gamma_k = [[0, -i sigma_k], [i sigma_k, 0]],
+ *                gamma_t = [[0, 1], [1, 0]], gamma_5 = diag(1, 1, -1, -1).
+ * Operator       D = (4 + m) - 1/2 sum_mu [(1 - gamma_mu) U_mu(x) delta_{x+mu}
+ *                    + (1 + gamma_mu) U_mu(x - mu)^dagger delta_{x-mu}]
+ *                    + c_sw (i/4) sum_{mu nu} sigma_{mu nu} F_{mu nu}(x)
+ *                (Sec. 4 hopping and clover terms), F from the clover leaf
+ *                (Q - Q^dagger)/8, sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu].
+ * Coarse fields  [Vc][nc][nrhs] complex, nc = 2 * (number of null vectors),
+ *                coarse dof K = chi*N + k with chi = 0 for the upper spins
+ *                (Sec. 5: "nbasis" is twice the number of basis vectors).
+ * Coarse links   [Vc][9][nc][nc] complex; block d = 0 self, 1 + mu for the
+ *                neighbour at +mu, 5 + mu for the neighbour at -mu (Sec. 6).
+ * Complex        float2 / double2 (interleaved), bf16 pairs where stated.
+ *
+ * Pointers named *_dev are device pointers owned by the caller; *_host are
+ * host pointers owned by the caller.  Handles (mrhs_lattice, mrhs_mg,
+ * mrhs_server) own every device buffer they allocate (gauge field, clover
+ * term, MG hierarchy, Krylov workspace) until destroyed.  `stream` is a
+ * cudaStream_t passed as void* (NULL = the legacy default stream); kernels are
+ * enqueued on it and the call returns without synchronising unless stated.
+ *
+ * Errors: every call returns an mrhs_status and never aborts.  Arguments are
+ * validated on the host before any launch; a failed CUDA call returns
+ * MRHS_ERR_CUDA.  mrhs_last_error() gives a message for the calling thread.
+ * There is no CPU fallback: without a usable CUDA device every call that
+ * needs one fails with MRHS_ERR_CUDA.
+ */
+#ifndef MRHS_H
+#define MRHS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MRHS_OK = 0,
+    MRHS_PENDING = 1,
+    MRHS_ERR_INVALID = -1,
+    MRHS_ERR_OOM = -2,
+    MRHS_ERR_CUDA = -3,
+    MRHS_ERR_NOT_CONVERGED = -4,
+    MRHS_ERR_TIMEOUT = -5,
+    MRHS_ERR_BUSY = -6,
+    MRHS_ERR_NOT_FOUND = -7
+} mrhs_status;
+
+typedef enum {
+    MRHS_FP32 = 0,
+    MRHS_FP64 = 1,
+    MRHS_BF16 = 2
+} mrhs_precision;
+
+typedef struct mrhs_lattice mrhs_lattice;
+typedef struct mrhs_mg mrhs_mg;
+typedef struct mrhs_server mrhs_server;
+
+#define MRHS_MAX_LEVELS 3
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mrhs_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Lattice, gauge field, clover term                                   */
+/* ------------------------------------------------------------------ */
+
+/* Create a lattice on CUDA device `device`.  dims[mu] >= 1.  t_boundary is
+ * +1 (periodic) or -1 (antiperiodic fermion boundary in t: every hop that
+ * crosses t = Lt-1 <-> 0 gets a factor -1).  Paper: Sec. 4 (operator). */
+mrhs_status mrhs_create_lattice(const int dims[4], int t_boundary, int device,
+                                mrhs_lattice **out);
+void mrhs_destroy_lattice(mrhs_lattice *lat);
+
+/* Copy the gauge field (host, FP64, layout above) to the device; the
+ * library keeps FP64 and FP32 copies in its own link-major layout. */
+mrhs_status mrhs_load_gauge(mrhs_lattice *lat, const double *U_host);
+
+/* Build the clover term from the clover-leaf field strength (Sec. 4, the
+ * "compact" clover: two Hermitian 6x6 blocks per site in the chiral basis)
+ * with the mass folded into its diagonal: 4 + m + c_sw (i/4) sigma F.
+ * Requires a loaded gauge field. */
+mrhs_status mrhs_build_clover(mrhs_lattice *lat, double mass, double csw);
+
+/* Copy the compact clover term to the host: [V][2][36] doubles; per
+ * chirality block the 6 diagonal reals, then the 15 strictly-lower
+ * entries (row i > col j, order i*(i-1)/2 + j) as (re, im); component
+ * index within a block is s_local*3 + c. */
+mrhs_status mrhs_get_clover(mrhs_lattice *lat, double *clover_host);
+
+/* out_dev = D in_dev for nrhs >= 1 RHS (Sec. 4: hopping + clover fused),
+ * both [V][12][nrhs] complex in precision `prec` (MRHS_FP32 or MRHS_FP64).
+ * in and out must not overlap. */
+mrhs_status mrhs_apply_D(mrhs_lattice *lat, const void *in_dev, void *out_dev,
+                         int nrhs, mrhs_precision prec, void *stream);
+
+/* out_dev = y_dev - D in_dev (the fused residual used by the solvers). */
+mrhs_status mrhs_residual_D(mrhs_lattice *lat, const void *in_dev, const void *y_dev,
+                            void *out_dev, int nrhs, mrhs_precision prec, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Batched BLAS-1 over the RHS index (Sec. 7, "simultaneous" inner      */
+/* products).  A field is `rows` rows of `nrhs` complex values, RHS     */
+/* innermost (rows = sites * dof).  Results are complex double (double2) */
+/* on the device, one per RHS; sums run in a fixed order per RHS.       */
+/* ------------------------------------------------------------------ */
+
+/* out_dev[j*nrhs + r] = sum_i conj(basis_j[i][r]) w[i][r] for j < k, where
+ * basis_j = basis_dev + j * rows * nrhs (k fields stored back to back). */
+mrhs_status mrhs_blas_multi_dot(const void *basis_dev, int k, const void *w_dev,
+                                int64_t rows, int nrhs, mrhs_precision prec,
+                                void *out_dev, void *stream);
+
+/* out_dev[r] = sum_i |w[i][r]|^2 (double, one per RHS). */
+mrhs_status mrhs_blas_norm2(const void *w_dev, int64_t rows, int nrhs,
+                            mrhs_precision prec, double *out_dev, void *stream);
+
+/* w[i][r] += alpha * sum_j coef[j*nrhs + r] * basis_j[i][r]  (coef: double2). */
+mrhs_status mrhs_blas_lincomb(void *w_dev, const void *basis_dev, int k,
+                              const void *coef_dev, double alpha, int64_t rows,
+                              int nrhs, mrhs_precision prec, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Multigrid hierarchy                                                  */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int n_levels;                          /* 2 or 3                              */
+    int block[MRHS_MAX_LEVELS - 1][4];     /* aggregate extents, level l -> l+1   */
+    int n_vec[MRHS_MAX_LEVELS - 1];        /* null vectors N (nc = 2N), even <= 64 */
+    int setup_sweeps;                      /* GMRES cycles on A v = 0 per vector  */
+    int setup_m;                           /* their restart length                */
+    int smooth_m;                          /* post-smoothing GMRES iterations     */
+    int coarse_m;                          /* coarsest GMRES restart length       */
+    int coarse_cycles;                     /* coarsest GMRES cycles per V-cycle   */
+    int inter_m;                           /* intermediate FGMRES iterations      */
+    int inner_m;                           /* FP32 MG-FGMRES restart length       */
+    int inner_max_iters;                   /* FP32 MG-FGMRES iteration cap        */
+    double inner_tol;                      /* FP32 inner relative tolerance       */
+    int outer_m;                           /* FP64 outer FGMRES restart length    */
+    int max_outer_iters;                   /* FP64 outer iteration cap            */
+    int coarse_precision;                  /* MRHS_FP32 or MRHS_BF16 coarse links */
+    int max_rhs;                           /* largest nrhs a solve may use        */
+    int use_graph;                         /* replay the V-cycle as a CUDA graph  */
+    uint64_t seed;                         /* start vectors when none supplied    */
+    /* Optional host start vectors per level, [V_l][dof_l][n_vec[l]] complex
+     * FP64 (dof_0 = 12, dof_l = nc of level l).  NULL entries: random. */
+    const double *init_vecs[MRHS_MAX_LEVELS - 1];
+} mrhs_mg_params;
+
+/* Fill `p` with the defaults used for the 24^3x64 three-level workload. */
+void mrhs_mg_default_params(mrhs_mg_params *p);
+
+/* Build the hierarchy (Sec. 5 prolongators, Sec. 6 coarse operators):
+ * null vectors relaxed in FP32, chirally split and block-orthonormalised in
+ * FP64, Galerkin coarse links R D P, cast to the coarse precision.  The
+ * lattice must have gauge + clover and must outlive the hierarchy. */
+mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params,
+                          mrhs_mg **out);
+void mrhs_destroy_mg(mrhs_mg *mg);
+
+/* Level geometry: dims of level `level` (0 = fine) and its dof per site. */
+mrhs_status mrhs_mg_level_info(mrhs_mg *mg, int level, int dims[4], int *dof);
+
+/* Copy the block-orthonormalised, chirally split null vectors of level
+ * `level` -> level+1 to the host: [V_l][dof_l][N] complex FP64.  Column
+ * (chi, k) of the prolongator is this array restricted to the components
+ * of chirality chi and to one aggregate. */
+mrhs_status mrhs_mg_get_prolongator(mrhs_mg *mg, int level, double *host_out);
+
+/* Copy the coarse links of level `level` (>= 1) to the host as FP64,
+ * [Vc][9][nc][nc] complex (Sec. 6 stencil, layout above). */
+mrhs_status mrhs_mg_get_coarse_links(mrhs_mg *mg, int level, double *host_out);
+
+/* Restriction c = P^dagger psi from level `level` to level+1 (Sec. 5),
+ * FP32 fields (level-l layout in, coarse layout out). */
+mrhs_status mrhs_restrict(mrhs_mg *mg, int level, const void *fine_dev,
+                          void *coarse_dev, int nrhs, void *stream);
+
+/* Prolongation psi = P c from level+1 to level `level` (Sec. 5), FP32. */
+mrhs_status mrhs_prolong(mrhs_mg *mg, int level, const void *coarse_dev,
+                         void *fine_dev, int nrhs, void *stream);
+
+/* Coarse 9-point stencil out = D_c in on level `level` >= 1 (Sec. 6), FP32
+ * fields; links_prec MRHS_FP32 (CUDA cores) or MRHS_BF16 (tensor cores,
+ * FP32 accumulation; requires nc = 64). */
+mrhs_status mrhs_coarse_apply(mrhs_mg *mg, int level, const void *in_dev, void *out_dev,
+                              int nrhs, mrhs_precision links_prec, void *stream);
+
+/* One MG V-cycle z = M^{-1} v on the fine level (Sec. 8 preconditioner),
+ * FP32 fields [V][12][nrhs]. */
+mrhs_status mrhs_vcycle(mrhs_mg *mg, const void *v_dev, void *z_dev, int nrhs, void *stream);
+
+typedef struct {
+    int outer_iters;        /* FP64 FGMRES iterations                          */
+    int inner_iters;        /* FP32 MG-FGMRES iterations, summed               */
+    int vcycles;            /* V-cycles applied                                */
+    double seconds;         /* wall time of the solve                          */
+    double t_fine;          /* fine-level smoother + fine FP32 applies (s)     */
+    double t_restrict;      /* restriction (s)                                 */
+    double t_prolong;       /* prolongation (s)                                */
+    double t_coarse;        /* coarse-level solves (s)                         */
+    double t_outer;         /* FP64 outer work: residuals, Arnoldi (s)         */
+    double max_rel_residual;/* max over RHS of ||b - D x|| / ||b||, FP64 D     */
+} mrhs_solve_stats;
+
+/* Solve D x = b for nrhs <= max_rhs RHS to a relative true residual `tol`
+ * (checked with the FP64 operator).  b_dev, x_dev: FP64 device fields
+ * [V][12][nrhs]; x_dev is the start vector on entry (set it to zero for a
+ * cold start) and the solution on exit.  rel_res_host (optional, [nrhs])
+ * receives each RHS's final relative residual.  Synchronises `stream`.
+ * Returns MRHS_ERR_NOT_CONVERGED (x = best iterate) if the outer cap is
+ * reached first.  Component timing in `stats` (optional) follows the
+ * breakdown of the paper's Sec. 8 table. */
+mrhs_status mrhs_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, double tol,
+                       double *rel_res_host, mrhs_solve_stats *stats, void *stream);
+
+/* ------------------------------------------------------------------ */
+/* Serving: continuous batching of solve requests                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int max_queue;          /* pending requests accepted before MRHS_ERR_BUSY  */
+    double hbm_reserve_gb;  /* free HBM to keep when admitting a config        */
+} mrhs_server_params;
+
+typedef struct {
+    int state;              /* MRHS_PENDING, MRHS_OK or an error status        */
+    double latency_s;       /* submit -> completion                            */
+    double queue_s;         /* submit -> first slot admission                  */
+    int outer_iters;        /* outer iterations the request took part in      */
+    double max_rel_residual;
+} mrhs_request_stats;
+
+mrhs_status mrhs_server_create(const mrhs_server_params *params, mrhs_server **out);
+/* Make a resident hierarchy servable with `slots` RHS slots (<= max_rhs of
+ * its params); its Krylov workspace is sized for `slots`.  Admission fails
+ * with MRHS_ERR_OOM if free HBM minus the reserve cannot hold it. */
+mrhs_status mrhs_server_add_config(mrhs_server *srv, mrhs_mg *mg, int slots, int *config_id);
+/* Queue nrhs sources b_host ([V][12][nrhs] FP64, copied before return);
+ * x_host receives the solutions and must stay valid until mrhs_poll
+ * reports completion. */
+mrhs_status mrhs_submit(mrhs_server *srv, int config_id, const double *b_host, double *x_host,
+                        int nrhs, double tol, uint64_t *req_id);
+/* MRHS_PENDING while queued or running, MRHS_OK when x_host is written,
+ * an error status if the request failed; `stats` optional. */
+mrhs_status mrhs_poll(mrhs_server *srv, uint64_t req_id, mrhs_request_stats *stats);
+/* Block until every submitted request has completed. */
+mrhs_status mrhs_server_drain(mrhs_server *srv);
+void mrhs_server_destroy(mrhs_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRHS_H */

@@ -1,0 +1,485 @@
+// Fine-level Wilson-clover operator (paper Sec. 4): fused hopping + compact
+// clover (+ mass) with the RHS index innermost, plus the setup kernels that
+// lay the gauge field out link-major and build the compact clover term.
+//
+// Work decomposition: one thread per (site, group of R consecutive RHS).
+// Threads of one site are adjacent, so a warp reads each neighbour spinor
+// component as one contiguous segment (16-byte vector loads for R = 2 in
+// FP32) while every gauge link and clover entry is a single broadcast load
+// shared by all RHS of the site: the MRHS reuse of Sec. 2.  With few RHS a
+// warp spans many sites and the link-major (site-innermost) layout of U and
+// of the clover keeps those loads coalesced as well.
+//
+// Spin projection (chiral basis, gamma_mu = [[0, A_mu], [A_mu^+, 0]] with
+// A_k = -i sigma_k, A_t = 1): (1 -+ gamma_mu) psi has rank 2, so each hop
+// forms a 2-spin half spinor h = psi_up -+ A psi_dn, multiplies it by the
+// link, and rebuilds the lower spins from the two products.
+#include "internal.cuh"
+
+namespace mrhs {
+
+// ---------------------------------------------------------------- factors
+// multiply by one of +1, -1, +i, -i
+enum { FP = 0, FM = 1, FI = 2, FMI = 3 };
+template <int F, typename T> __device__ __forceinline__ cplx<T> fmul(cplx<T> a) {
+    if constexpr (F == FP) return a;
+    else if constexpr (F == FM) return {-a.re, -a.im};
+    else if constexpr (F == FI) return ti(a);
+    else return tmi(a);
+}
+template <int F> struct neg_f { static constexpr int v = F == FP ? FM : F == FM ? FP : F == FI ? FMI : FI; };
+
+// Half-spinor rule of direction MU for the forward hop (1 - gamma_mu):
+//   h0 = psi0 + F0 psi_{P0},  h1 = psi1 + F1 psi_{P1}
+//   acc2 += G2 (U h)_{Q2},    acc3 += G3 (U h)_{Q3},  acc0 += (U h)_0, acc1 += (U h)_1
+// The backward hop (1 + gamma_mu) negates F0, F1, G2, G3.
+template <int MU> struct Proj;
+template <> struct Proj<0> { static constexpr int P0 = 3, F0 = FI, P1 = 2, F1 = FI, Q2 = 1, G2 = FMI, Q3 = 0, G3 = FMI; };
+template <> struct Proj<1> { static constexpr int P0 = 3, F0 = FP, P1 = 2, F1 = FM, Q2 = 1, G2 = FM, Q3 = 0, G3 = FP; };
+template <> struct Proj<2> { static constexpr int P0 = 2, F0 = FI, P1 = 3, F1 = FMI, Q2 = 0, G2 = FMI, Q3 = 1, G3 = FI; };
+template <> struct Proj<3> { static constexpr int P0 = 2, F0 = FM, P1 = 3, F1 = FM, Q2 = 0, G2 = FM, Q3 = 1, G3 = FM; };
+
+// ------------------------------------------------------------ vector loads
+// R consecutive complex values of the input field at complex offset `off`.
+template <typename TIn, int R> struct Load;
+template <> struct Load<float, 1> {
+    template <typename Real> __device__ static void f(const void *p, int64_t off, cplx<Real> *v) {
+        float2 a = __ldg(reinterpret_cast<const float2 *>(p) + off);
+        v[0] = {(Real)a.x, (Real)a.y};
+    }
+};
+template <> struct Load<float, 2> {
+    template <typename Real> __device__ static void f(const void *p, int64_t off, cplx<Real> *v) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float2 *>(p) + off));
+        v[0] = {(Real)a.x, (Real)a.y};
+        v[1] = {(Real)a.z, (Real)a.w};
+    }
+};
+template <> struct Load<double, 1> {
+    template <typename Real> __device__ static void f(const void *p, int64_t off, cplx<Real> *v) {
+        double2 a = __ldg(reinterpret_cast<const double2 *>(p) + off);
+        v[0] = {(Real)a.x, (Real)a.y};
+    }
+};
+
+template <typename Real, int R> struct Store;
+template <> struct Store<float, 1> {
+    __device__ static void f(void *p, int64_t off, const cplx<float> *v) {
+        reinterpret_cast<float2 *>(p)[off] = make_float2(v[0].re, v[0].im);
+    }
+};
+template <> struct Store<float, 2> {
+    __device__ static void f(void *p, int64_t off, const cplx<float> *v) {
+        *reinterpret_cast<float4 *>(reinterpret_cast<float2 *>(p) + off) = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+    }
+};
+template <> struct Store<double, 1> {
+    __device__ static void f(void *p, int64_t off, const cplx<double> *v) {
+        reinterpret_cast<double2 *>(p)[off] = make_double2(v[0].re, v[0].im);
+    }
+};
+
+template <typename Real> __device__ __forceinline__ cplx<Real> ldc(const cplx<Real> *p, int64_t i) {
+    if constexpr (sizeof(Real) == 4) {
+        float2 a = __ldg(reinterpret_cast<const float2 *>(p) + i);
+        return {a.x, a.y};
+    } else {
+        double2 a = __ldg(reinterpret_cast<const double2 *>(p) + i);
+        return {a.x, a.y};
+    }
+}
+
+struct KArgs {
+    Geom g;
+    int n;        // RHS count
+    int G;        // RHS groups per site (n / R)
+    int64_t stride[4];
+};
+
+// ------------------------------------------------------------ one direction
+template <int MU, bool FWD, typename Real, typename TIn, int R>
+__device__ __forceinline__ void hop(cplx<Real> (&acc)[12][R], const cplx<Real> *__restrict__ U,
+                                    const TIn *__restrict__ in, const KArgs &a, int64_t nb,
+                                    int64_t link_site, Real sign, int r0) {
+    using P = Proj<MU>;
+    constexpr int F0 = FWD ? P::F0 : neg_f<P::F0>::v;
+    constexpr int F1 = FWD ? P::F1 : neg_f<P::F1>::v;
+    constexpr int G2 = FWD ? P::G2 : neg_f<P::G2>::v;
+    constexpr int G3 = FWD ? P::G3 : neg_f<P::G3>::v;
+    const int64_t V = a.g.V;
+    const int64_t base = nb * 12 * a.n + r0;
+    cplx<Real> h0[3][R], h1[3][R];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        cplx<Real> p0[R], p1[R], pa[R], pb[R];
+        Load<TIn, R>::f(in, base + (int64_t)(0 * 3 + c) * a.n, p0);
+        Load<TIn, R>::f(in, base + (int64_t)(1 * 3 + c) * a.n, p1);
+        Load<TIn, R>::f(in, base + (int64_t)(P::P0 * 3 + c) * a.n, pa);
+        Load<TIn, R>::f(in, base + (int64_t)(P::P1 * 3 + c) * a.n, pb);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            h0[c][r] = sign * (p0[r] + fmul<F0>(pa[r]));
+            h1[c][r] = sign * (p1[r] + fmul<F1>(pb[r]));
+        }
+    }
+#pragma unroll
+    for (int row = 0; row < 3; ++row) {
+        cplx<Real> u[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            // forward: row `row` of U_mu(x); backward: column `row` of U_mu(x - mu), conjugated
+            u[b] = FWD ? ldc(U, (int64_t)(MU * 9 + row * 3 + b) * V + link_site)
+                       : conj(ldc(U, (int64_t)(MU * 9 + b * 3 + row) * V + link_site));
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            cplx<Real> s0 = {0, 0}, s1 = {0, 0};
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                cmac(s0, u[b], h0[b][r]);
+                cmac(s1, u[b], h1[b][r]);
+            }
+            acc[0 * 3 + row][r] = acc[0 * 3 + row][r] + s0;
+            acc[1 * 3 + row][r] = acc[1 * 3 + row][r] + s1;
+            const cplx<Real> q2 = P::Q2 == 0 ? s0 : s1;
+            const cplx<Real> q3 = P::Q3 == 0 ? s0 : s1;
+            acc[2 * 3 + row][r] = acc[2 * 3 + row][r] + fmul<G2>(q2);
+            acc[3 * 3 + row][r] = acc[3 * 3 + row][r] + fmul<G3>(q3);
+        }
+    }
+}
+
+__device__ __forceinline__ bool hop_selected(const HopMask &m, int d, int loc, int B, bool fwd) {
+    if (m.dir >= 0 && m.dir != d) return false;
+    if (m.cross == 0) return true;
+    const bool crossing = fwd ? (loc == B - 1) : (loc == 0);
+    return m.cross == 1 ? crossing : !crossing;
+}
+
+template <int MU, typename Real, typename TIn, int R, bool GENERAL>
+__device__ __forceinline__ void hop_pair(cplx<Real> (&acc)[12][R], const cplx<Real> *__restrict__ U,
+                                         const TIn *__restrict__ in, const KArgs &a, int64_t site,
+                                         const int c[4], int r0, const HopMask &mask) {
+    const int L = a.g.L[MU];
+    const int64_t st = a.stride[MU];
+    const bool wrapF = (c[MU] == L - 1), wrapB = (c[MU] == 0);
+    const int64_t sf = wrapF ? site - st * (L - 1) : site + st;
+    const int64_t sb = wrapB ? site + st * (L - 1) : site - st;
+    const Real sgnF = (MU == 3 && wrapF) ? (Real)a.g.tb : (Real)1;
+    const Real sgnB = (MU == 3 && wrapB) ? (Real)a.g.tb : (Real)1;
+    bool doF = true, doB = true;
+    if constexpr (GENERAL) {
+        const int loc = c[MU] % mask.B[MU];
+        doF = hop_selected(mask, 1 + MU, loc, mask.B[MU], true);
+        doB = hop_selected(mask, 5 + MU, loc, mask.B[MU], false);
+    }
+    if (doF) hop<MU, true, Real, TIn, R>(acc, U, in, a, sf, site, sgnF, r0);
+    if (doB) hop<MU, false, Real, TIn, R>(acc, U, in, a, sb, sb, sgnB, r0);
+}
+
+// out = C psi - 1/2 sum(hops)  (RESID: out = y - that)
+template <typename Real, typename TIn, int R, bool RESID, bool GENERAL>
+__global__ void __launch_bounds__(128) k_dslash(const cplx<Real> *__restrict__ U, const cplx<Real> *__restrict__ C,
+                                                 const TIn *__restrict__ in, Real *__restrict__ out,
+                                                 const Real *__restrict__ y, KArgs a, HopMask mask) {
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t site = item / a.G;
+    if (site >= a.g.V) return;
+    const int r0 = (int)(item - site * a.G) * R;
+    int c[4];
+    site_to_coords(site, a.g.L, c);
+
+    cplx<Real> acc[12][R];
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[i][r] = {0, 0};
+
+    hop_pair<0, Real, TIn, R, GENERAL>(acc, U, in, a, site, c, r0, mask);
+    hop_pair<1, Real, TIn, R, GENERAL>(acc, U, in, a, site, c, r0, mask);
+    hop_pair<2, Real, TIn, R, GENERAL>(acc, U, in, a, site, c, r0, mask);
+    hop_pair<3, Real, TIn, R, GENERAL>(acc, U, in, a, site, c, r0, mask);
+
+    const bool diag = GENERAL ? (mask.diag != 0) : true;
+    const int64_t V = a.g.V;
+    const int64_t base = site * 12 * a.n + r0;
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        cplx<Real> v[6][R], o[6][R];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            Load<TIn, R>::f(in, base + (int64_t)(6 * chi + i) * a.n, v[i]);
+#pragma unroll
+            for (int r = 0; r < R; ++r) o[i][r] = {0, 0};
+        }
+        if (diag) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                const cplx<Real> d = ldc(C, (int64_t)(chi * 18 + q) * V + site);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    o[2 * q][r] = d.re * v[2 * q][r];
+                    o[2 * q + 1][r] = d.im * v[2 * q + 1][r];
+                }
+            }
+            int q = 3;
+#pragma unroll
+            for (int i = 1; i < 6; ++i) {
+#pragma unroll
+                for (int j = 0; j < i; ++j, ++q) {
+                    const cplx<Real> l = ldc(C, (int64_t)(chi * 18 + q) * V + site);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        cmac(o[i][r], l, v[j][r]);
+                        cmac_conj(o[j][r], l, v[i][r]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            cplx<Real> res[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                res[r] = o[i][r] - (Real)0.5 * acc[6 * chi + i][r];
+            }
+            const int64_t off = base + (int64_t)(6 * chi + i) * a.n;
+            if constexpr (RESID) {
+                cplx<Real> yy[R];
+                Load<Real, R>::f(y, off, yy);
+#pragma unroll
+                for (int r = 0; r < R; ++r) res[r] = yy[r] - res[r];
+            }
+            Store<Real, R>::f(out, off, res);
+        }
+    }
+}
+
+template <typename Real, typename TIn, int R, bool RESID, bool GENERAL>
+static void launch_dslash(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n,
+                          cudaStream_t s, const HopMask &mask) {
+    KArgs a;
+    a.g = lat.g;
+    a.n = n;
+    a.G = n / R;
+    a.stride[0] = 1;
+    a.stride[1] = lat.g.L[0];
+    a.stride[2] = (int64_t)lat.g.L[0] * lat.g.L[1];
+    a.stride[3] = (int64_t)lat.g.L[0] * lat.g.L[1] * lat.g.L[2];
+    const int64_t items = lat.g.V * a.G;
+    const int threads = 128;
+    const int64_t blocks = (items + threads - 1) / threads;
+    const cplx<Real> *U = sizeof(Real) == 4 ? lat.U32.as<cplx<Real>>() : lat.U64.as<cplx<Real>>();
+    const cplx<Real> *C = sizeof(Real) == 4 ? lat.C32.as<cplx<Real>>() : lat.C64.as<cplx<Real>>();
+    k_dslash<Real, TIn, R, RESID, GENERAL><<<(unsigned)blocks, threads, 0, s>>>(
+        U, C, static_cast<const TIn *>(in), static_cast<Real *>(out), static_cast<const Real *>(y), a, mask);
+    MRHS_LAUNCHED("k_dslash");
+}
+
+void dslash(const mrhs_lattice &lat, mrhs_precision compute, mrhs_precision in_prec, const void *in,
+            void *out, const void *y, int n, cudaStream_t s, const HopMask *mask) {
+    if (!lat.has_clover) fail(MRHS_ERR_INVALID, "clover term not built (call mrhs_build_clover)");
+    HopMask m{1, -1, 0, {1, 1, 1, 1}};
+    const bool general = mask != nullptr;
+    if (general) m = *mask;
+    const bool resid = y != nullptr;
+    if (general && resid) fail(MRHS_ERR_INVALID, "masked operator has no residual form");
+    if (compute == MRHS_FP32) {
+        if (in_prec != MRHS_FP32) fail(MRHS_ERR_INVALID, "FP32 operator needs FP32 input");
+        const bool r2 = (n % 2) == 0;
+        if (general) {
+            if (r2) launch_dslash<float, float, 2, false, true>(lat, in, out, y, n, s, m);
+            else launch_dslash<float, float, 1, false, true>(lat, in, out, y, n, s, m);
+        } else if (resid) {
+            if (r2) launch_dslash<float, float, 2, true, false>(lat, in, out, y, n, s, m);
+            else launch_dslash<float, float, 1, true, false>(lat, in, out, y, n, s, m);
+        } else {
+            if (r2) launch_dslash<float, float, 2, false, false>(lat, in, out, y, n, s, m);
+            else launch_dslash<float, float, 1, false, false>(lat, in, out, y, n, s, m);
+        }
+    } else if (compute == MRHS_FP64) {
+        if (general) {
+            if (in_prec != MRHS_FP64) fail(MRHS_ERR_INVALID, "masked FP64 operator needs FP64 input");
+            launch_dslash<double, double, 1, false, true>(lat, in, out, y, n, s, m);
+        } else if (in_prec == MRHS_FP64) {
+            if (resid) launch_dslash<double, double, 1, true, false>(lat, in, out, y, n, s, m);
+            else launch_dslash<double, double, 1, false, false>(lat, in, out, y, n, s, m);
+        } else if (in_prec == MRHS_FP32) {
+            if (resid) launch_dslash<double, float, 1, true, false>(lat, in, out, y, n, s, m);
+            else launch_dslash<double, float, 1, false, false>(lat, in, out, y, n, s, m);
+        } else {
+            fail(MRHS_ERR_INVALID, "unsupported input precision");
+        }
+    } else {
+        fail(MRHS_ERR_INVALID, "fine operator computes in FP32 or FP64");
+    }
+}
+
+// ------------------------------------------------------------ gauge layout
+__global__ void k_gauge_to_soa(const double2 *__restrict__ aos, double2 *__restrict__ u64,
+                               float2 *__restrict__ u32, int64_t V) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V * 36) return;
+    const int64_t site = i / 36;
+    const int e = (int)(i - site * 36);  // mu*9 + a*3 + b
+    const double2 v = aos[i];
+    u64[(int64_t)e * V + site] = v;
+    u32[(int64_t)e * V + site] = make_float2((float)v.x, (float)v.y);
+}
+
+void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s) {
+    const int64_t V = lat.g.V;
+    const int64_t n = V * 36;
+    k_gauge_to_soa<<<ceil_div(n, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(aos_dev),
+                                                     lat.U64.as<double2>(), lat.U32.as<float2>(), V);
+    MRHS_LAUNCHED("k_gauge_to_soa");
+}
+
+// ------------------------------------------------------------ clover build
+// 3x3 complex matrices in registers
+struct M3 { cplx<double> a[3][3]; };
+
+__device__ __forceinline__ M3 mat_mul(const M3 &x, const M3 &y) {
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            cplx<double> s = {0, 0};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cmac(s, x.a[i][k], y.a[k][j]);
+            r.a[i][j] = s;
+        }
+    return r;
+}
+__device__ __forceinline__ M3 mat_dag(const M3 &x) {
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) r.a[i][j] = conj(x.a[j][i]);
+    return r;
+}
+__device__ __forceinline__ M3 load_link(const double2 *U, int64_t V, int mu, int64_t site) {
+    M3 r;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const double2 v = U[(int64_t)(mu * 9 + i * 3 + j) * V + site];
+            r.a[i][j] = {v.x, v.y};
+        }
+    return r;
+}
+
+__device__ __forceinline__ int64_t nbr(const int c[4], const int L[4], int mu, int step) {
+    int d[4] = {c[0], c[1], c[2], c[3]};
+    d[mu] = (d[mu] + step + L[mu]) % L[mu];
+    return coords_to_site(d, L);
+}
+
+// G_{mu nu} = i F_{mu nu} = i (Q - Q^+)/8 (Hermitian), Q the clover-leaf sum at x
+__device__ M3 clover_G(const double2 *U, const Geom &g, const int c[4], int64_t site, int mu, int nu) {
+    const int64_t V = g.V;
+    int cm[4] = {c[0], c[1], c[2], c[3]};
+    cm[mu] = (cm[mu] - 1 + g.L[mu]) % g.L[mu];          // x - mu
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[nu] = (cn[nu] - 1 + g.L[nu]) % g.L[nu];          // x - nu
+    int cmn[4] = {cm[0], cm[1], cm[2], cm[3]};
+    cmn[nu] = (cmn[nu] - 1 + g.L[nu]) % g.L[nu];        // x - mu - nu
+    const int64_t s_pm = nbr(c, g.L, mu, 1), s_pn = nbr(c, g.L, nu, 1);
+    const int64_t s_m = coords_to_site(cm, g.L), s_n = coords_to_site(cn, g.L), s_mn = coords_to_site(cmn, g.L);
+    const int64_t s_m_pn = nbr(cm, g.L, nu, 1), s_n_pm = nbr(cn, g.L, mu, 1);
+    // leaf 1: U_mu(x) U_nu(x+mu) U_mu(x+nu)^+ U_nu(x)^+
+    M3 Q = mat_mul(mat_mul(load_link(U, V, mu, site), load_link(U, V, nu, s_pm)),
+                   mat_mul(mat_dag(load_link(U, V, mu, s_pn)), mat_dag(load_link(U, V, nu, site))));
+    // leaf 2: U_nu(x) U_mu(x-mu+nu)^+ U_nu(x-mu)^+ U_mu(x-mu)
+    M3 t = mat_mul(mat_mul(load_link(U, V, nu, site), mat_dag(load_link(U, V, mu, s_m_pn))),
+                   mat_mul(mat_dag(load_link(U, V, nu, s_m)), load_link(U, V, mu, s_m)));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q.a[i][j] = Q.a[i][j] + t.a[i][j];
+    // leaf 3: U_mu(x-mu)^+ U_nu(x-mu-nu)^+ U_mu(x-mu-nu) U_nu(x-nu)
+    t = mat_mul(mat_mul(mat_dag(load_link(U, V, mu, s_m)), mat_dag(load_link(U, V, nu, s_mn))),
+                mat_mul(load_link(U, V, mu, s_mn), load_link(U, V, nu, s_n)));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q.a[i][j] = Q.a[i][j] + t.a[i][j];
+    // leaf 4: U_nu(x-nu)^+ U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^+
+    t = mat_mul(mat_mul(mat_dag(load_link(U, V, nu, s_n)), load_link(U, V, mu, s_n)),
+                mat_mul(load_link(U, V, nu, s_n_pm), mat_dag(load_link(U, V, mu, site))));
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q.a[i][j] = Q.a[i][j] + t.a[i][j];
+    M3 G;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const cplx<double> d = Q.a[i][j] - conj(Q.a[j][i]);  // Q - Q^+
+            G.a[i][j] = ti(d);                                  // times i
+            G.a[i][j].re *= 0.125;
+            G.a[i][j].im *= 0.125;
+        }
+    return G;
+}
+
+// In the chiral basis sigma_{mu nu} is block diagonal; per chirality block
+// (c_sw/2) sum_{mu<nu} sigma^chi_{mu nu} (x) G_{mu nu}
+//   = (c_sw/2) (sigma_x (x) X + sigma_y (x) Y + sigma_z (x) Z)
+// with, for the upper block,  X = G03 - G12, Y = G02 + G13, Z = G23 - G01,
+// and for the lower block     X = -G03 - G12, Y = G02 - G13, Z = -G23 - G01.
+// As a 6x6 matrix (index s*3 + c): [[Z, X - iY], [X + iY, -Z]].
+__global__ void k_build_clover(const double2 *__restrict__ U, Geom g, double mass, double csw,
+                               double2 *__restrict__ C64, float2 *__restrict__ C32) {
+    const int64_t site = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (site >= g.V) return;
+    int c[4];
+    site_to_coords(site, g.L, c);
+    const M3 G01 = clover_G(U, g, c, site, 0, 1), G02 = clover_G(U, g, c, site, 0, 2),
+             G03 = clover_G(U, g, c, site, 0, 3), G12 = clover_G(U, g, c, site, 1, 2),
+             G13 = clover_G(U, g, c, site, 1, 3), G23 = clover_G(U, g, c, site, 2, 3);
+    const double h = 0.5 * csw;
+    for (int chi = 0; chi < 2; ++chi) {
+        const double s = chi == 0 ? 1.0 : -1.0;
+        cplx<double> B[6][6];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const cplx<double> X = s * G03.a[a][b] - G12.a[a][b];
+                const cplx<double> Y = G02.a[a][b] + s * G13.a[a][b];
+                const cplx<double> Z = s * G23.a[a][b] - G01.a[a][b];
+                B[a][b] = h * Z;
+                B[3 + a][3 + b] = (-h) * Z;
+                B[a][3 + b] = h * (X - ti(Y));
+                B[3 + a][b] = h * (X + ti(Y));
+            }
+        for (int i = 0; i < 6; ++i) B[i][i].re += 4.0 + mass;
+        const int64_t V = g.V;
+        for (int q = 0; q < 3; ++q) {
+            const double2 d = make_double2(B[2 * q][2 * q].re, B[2 * q + 1][2 * q + 1].re);
+            C64[(int64_t)(chi * 18 + q) * V + site] = d;
+            C32[(int64_t)(chi * 18 + q) * V + site] = make_float2((float)d.x, (float)d.y);
+        }
+        int q = 3;
+        for (int i = 1; i < 6; ++i)
+            for (int j = 0; j < i; ++j, ++q) {
+                const double2 l = make_double2(B[i][j].re, B[i][j].im);
+                C64[(int64_t)(chi * 18 + q) * V + site] = l;
+                C32[(int64_t)(chi * 18 + q) * V + site] = make_float2((float)l.x, (float)l.y);
+            }
+    }
+}
+
+void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s) {
+    const int64_t V = lat.g.V;
+    k_build_clover<<<ceil_div(V, 128), 128, 0, s>>>(lat.U64.as<double2>(), lat.g, mass, csw,
+                                                     lat.C64.as<double2>(), lat.C32.as<float2>());
+    MRHS_LAUNCHED("k_build_clover");
+}
+
+}  // namespace mrhs

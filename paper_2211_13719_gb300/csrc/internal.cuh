@@ -1,0 +1,98 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+// ----------------------------------------------------------------- lattice
+struct mrhs_lattice {
+    mrhs::Geom g;
+    int device = 0;
+    // links, link-major SoA: element (mu*9 + a*3 + b) of site x at [(mu*9+a*3+b)*V + x]
+    mrhs::DeviceBuffer U64, U32;
+    // compact clover + mass, SoA: [(chi*18 + q)*V + x], q < 3 packs diagonal
+    // pairs (d_{2q}, d_{2q+1}); q >= 3 is lower-triangle entry q - 3
+    mrhs::DeviceBuffer C64, C32;
+    bool has_gauge = false, has_clover = false;
+    double mass = 0.0, csw = 0.0;
+};
+
+namespace mrhs {
+
+// --------------------------------------------------------- fine operator
+// Selection of terms for the Galerkin construction (setup only).
+struct HopMask {
+    int diag;   // include the clover + mass diagonal
+    int dir;    // -1: all hops; else only stencil direction d in 1..8 (1+mu: +mu, 5+mu: -mu)
+    int cross;  // 0: all selected hops; 1: only hops leaving the aggregate; 2: only hops staying in
+    int B[4];   // aggregate extents
+};
+
+void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s);
+void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s);
+// out = D in (y == nullptr) or out = y - D in; compute in `compute` precision,
+// input in `in_prec` (FP32 input allowed with FP64 compute); out and y in `compute`.
+void dslash(const mrhs_lattice &lat, mrhs_precision compute, mrhs_precision in_prec,
+            const void *in, void *out, const void *y, int n, cudaStream_t s,
+            const HopMask *mask = nullptr);
+
+// ------------------------------------------------------------------ BLAS
+// Reduction scratch: per-block partial sums and a completion counter.
+struct Scratch {
+    DeviceBuffer partials;   // double2 [max_blocks][kchunk][n]
+    DeviceBuffer counter;    // unsigned int
+    int max_blocks = 0;
+    int max_cols = 0;        // kchunk * n capacity per block
+    void ensure(int blocks, int cols);
+};
+
+constexpr int KCHUNK = 8;  // basis vectors per multi-dot pass
+
+void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w,
+               int64_t rows, int n, double2 *out, Scratch &sc, cudaStream_t s, bool accumulate = false);
+void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s);
+// w += alpha * sum_j coef[j][r] basis_j ; basis may be FP32 while w is FP64.
+// If norm_out != nullptr, also writes ||w_new||^2 per RHS (needs sc).
+void lincomb(mrhs_precision pw, void *w, mrhs_precision pb, const void *basis, int64_t stride, int k,
+             const double2 *coef, double alpha, int64_t rows, int n, cudaStream_t s,
+             double *norm_out = nullptr, Scratch *sc = nullptr);
+// dst = src / sqrt(nrm2[r]) (0 where nrm2 == 0); dst may equal src
+void scale_inv_sqrt(mrhs_precision p, void *dst, const void *src, const double *nrm2, int64_t rows, int n,
+                    cudaStream_t s);
+// dst (pd) = src (ps) elementwise conversion
+void cast(mrhs_precision pd, void *dst, mrhs_precision ps, const void *src, int64_t count, cudaStream_t s);
+// y = a*x + y with real a, same precision
+void axpy(mrhs_precision p, double a, const void *x, void *y, int64_t count, cudaStream_t s);
+
+// ----------------------------------------------- per-RHS small Krylov state
+// Hessenberg / Givens state for n RHS and restart length m (device arrays).
+struct KrylovState {
+    int m = 0, n = 0;
+    DeviceBuffer R;      // double2 [n][m+1][m] rotated Hessenberg (upper triangular part)
+    DeviceBuffer cs;     // double  [n][m]
+    DeviceBuffer sn;     // double2 [n][m]
+    DeviceBuffer g;      // double2 [n][m+1]
+    DeviceBuffer y;      // double2 [m][n]  (layout of lincomb coefficients)
+    DeviceBuffer hcol;   // double2 [m+1][n] current Arnoldi column (pass 1 + pass 2)
+    DeviceBuffer h2;     // double2 [m+1][n] second-pass coefficients
+    DeviceBuffer hn2;    // double  [n]      ||w||^2 after orthogonalisation
+    DeviceBuffer beta2;  // double  [n]      ||r0||^2
+    DeviceBuffer res;    // double  [n]      current residual estimate |g_{j+1}|
+    void init(int m_, int n_);
+};
+// g = (sqrt(beta2), 0, ...), clears rotations
+void krylov_start(KrylovState &ks, int n, cudaStream_t s);
+// fold column j (hcol[0..j], hn2) into R with Givens rotations; updates g, res
+void krylov_givens(KrylovState &ks, int j, int n, cudaStream_t s);
+// y = R^{-1} g for the first `j` columns
+void krylov_solve(KrylovState &ks, int j, int n, cudaStream_t s);
+
+// -------------------------------------------------------------- RNG
+// Gaussian complex numbers from splitmix64 (Steele, Lea, Flood, OOPSLA 2014)
+// + Box-Muller; deterministic in (seed, index).
+void fill_gaussian(mrhs_precision p, void *dst, int64_t count, uint64_t seed, cudaStream_t s);
+
+}  // namespace mrhs
