@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark: MRHS multigrid solves per second to a true residual of 1e-10.
+
+Workload (one step = one MRHS solve of the whole RHS block):
+  24^3 x 64 lattice, antiperiodic t, U = exp(i 0.25 H) with seeded Gaussian
+  traceless Hermitian H, c_sw = 1, mass below, three-level MG (4^4 then 2^4
+  aggregates, 32 chirally split null vectors each), nRHS = 48 Gaussian
+  sources, outer FP64 FGMRES, FP32 inner FGMRES + V-cycle, BF16 tensor-core
+  coarse stencil, V-cycle replayed as a CUDA graph, tol 1e-10.
+Setup (null vectors, Galerkin) runs before the timed region and is reported
+separately.  The line also carries the plain one-RHS-at-a-time solver (FP32
+coarse stencil on CUDA cores, no graphs) on the same GPU, the fine-stencil
+roofline, the end-to-end number with host buffers, and the oracle timed on the
+host cores as the CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(dims=(24, 24, 24, 64), eps=0.25, gauge_seed=1301, source_seed=2301, mass=-0.1, csw=1.0,
+                nrhs=48, tol=1e-10, n_levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[32, 32])
+MG_PARAMS = dict(setup_sweeps=6, setup_m=8, smooth_m=4, coarse_m=16, coarse_cycles=2, inter_m=8, inner_m=8,
+                 inner_max_iters=200, inner_tol=1e-5, outer_m=4, max_outer_iters=30)
+WORKLOAD_NAME = ("wilson-clover MG solve 24^3x64 antiperiodic, U=exp(i0.25H), c_sw=1, 3 levels "
+                 "(4^4, 2^4 aggregates, 32 null vectors), nRHS=48, tol 1e-10")
+# the CPU baseline / reference arm: the oracle's FP64 MG-FGMRES on a smaller
+# lattice of the same recipe, scaled to the workload by the volume ratio
+ORACLE_SAMPLE = dict(dims=(8, 8, 8, 16), blocks=[(4, 4, 4, 4)], nvec=[8], setup_sweeps=3, setup_m=8,
+                     smooth_m=4, coarse_m=16, coarse_cycles=2, outer_m=8)
+
+
+def volume(d):
+    return d[0] * d[1] * d[2] * d[3]
+
+
+# ------------------------------------------------------------------ helpers
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash(*names):
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2211_13719_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_file):
+    """dram bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", "dslash_fp32_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("source_hash") == source_hash(kernel_file):
+            return rec
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------- oracle arm
+def oracle_sample_solve(steps: int, warmup: int):
+    """Time the oracle's FP64 MG-FGMRES on the sample lattice (one RHS per step)."""
+    import numpy as np
+
+    import synth
+    from oracle import mg as omg
+    s = ORACLE_SAMPLE
+    w = WORKLOAD
+    dims = s["dims"]
+    U = synth.gauge_exp(dims, w["eps"], w["gauge_seed"])
+    p = omg.MGParams(blocks=s["blocks"], nvec=s["nvec"], setup_sweeps=s["setup_sweeps"], setup_m=s["setup_m"],
+                     smooth_m=s["smooth_m"], coarse_m=s["coarse_m"], coarse_cycles=s["coarse_cycles"],
+                     outer_m=s["outer_m"], tol=w["tol"])
+    V = volume(dims)
+    levels = omg.build_hierarchy(U, dims, w["mass"], w["csw"], p,
+                                 [synth.gaussian_field(V, 12, s["nvec"][0], 7)])
+    times = []
+    for i in range(warmup + steps):
+        b = synth.gaussian_field(V, 12, 1, w["source_seed"] + i)
+        t0 = time.perf_counter()
+        x, hist = omg.solve(levels, b, p)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+        assert np.all(hist[-1] <= w["tol"])
+    mean = sum(times) / len(times)
+    scale = V / volume(w["dims"])
+    return {"value": scale / mean, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle FP64 MG-FGMRES, 1 RHS per step on {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]} "
+                       f"(same gauge recipe, 2 levels, 4^4 aggregates, {s['nvec'][0]} null vectors), "
+                       f"{mean:.2f} s per solve, scaled by the volume ratio {V}/{volume(w['dims'])}"),
+            "seconds_per_sample_solve": mean}
+
+
+def oracle_in_subprocess(steps=1, warmup=0):
+    """Run the oracle timing on one host thread in a fresh process (spawned after CUDA use)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample_solve(%d, %d)))" % (ROOT, steps, warmup))
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if p.returncode != 0:
+        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": "failed: " +
+                p.stderr.strip().splitlines()[-1] if p.stderr.strip() else "failed"}
+    return json.loads(p.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    res = oracle_in_subprocess(args.steps, args.warmup)
+    wall = time.perf_counter() - t0
+    line = {
+        "impl": "reference", "metric": "MG solves/s at 1e-10", "value": res["value"], "unit": "solves/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": (res.get("seconds_per_sample_solve") or 0) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "sample": ORACLE_SAMPLE["dims"]},
+        "cpu_baseline": {"value": res["value"], "unit": "solves/s", "cores": res["cores"], "kind": "oracle",
+                         "sample": res["sample"]},
+        "e2e": {"value": res["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def make_params(mrhs, n_max, coarse_precision, use_graph, **over):
+    p = mrhs.mrhs_mg_default_params()
+    w = WORKLOAD
+    p.n_levels = w["n_levels"]
+    for l, b in enumerate(w["blocks"]):
+        for mu in range(4):
+            p.block[l][mu] = b[mu]
+    for l, nv in enumerate(w["nvec"]):
+        p.n_vec[l] = nv
+    for k, v in dict(MG_PARAMS, **over).items():
+        setattr(p, k, v)
+    p.max_rhs = n_max
+    p.coarse_precision = coarse_precision
+    p.use_graph = use_graph
+    p.seed = 4242
+    return p
+
+
+def gauge_field(w):
+    import numpy as np
+
+    import synth
+    cache = f"/tmp/mrhs_bench_gauge_{w['dims']}_{w['eps']}_{w['gauge_seed']}.npy".replace(" ", "")
+    if os.path.exists(cache):
+        try:
+            return np.load(cache)
+        except Exception:
+            pass
+    U = synth.gauge_exp(w["dims"], w["eps"], w["gauge_seed"])
+    try:
+        np.save(cache, U)
+    except Exception:
+        pass
+    return U
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_2211_13719_gb300 import build as _build
+    from paper_2211_13719_gb300 import mrhs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        _build.build()
+    w = dict(WORKLOAD)
+    if args.nrhs:
+        w["nrhs"] = args.nrhs
+    n = w["nrhs"]
+    dims = w["dims"]
+    V = volume(dims)
+    U = gauge_field(w)
+    lat = mrhs.mrhs_create_lattice(dims, -1, dev)
+    mrhs.mrhs_load_gauge(lat, U)
+    mrhs.mrhs_build_clover(lat, w["mass"], w["csw"])
+    del U
+    t0 = time.perf_counter()
+    mg = mrhs.mrhs_setup_mg(lat, make_params(mrhs, n, mrhs.MRHS_BF16, 1))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w["source_seed"] + 1000 * rank)
+    b = torch.randn((V, 12, n), dtype=torch.complex128, device="cuda", generator=gen)
+    x = torch.zeros_like(b)
+    rel = np.zeros(n)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        x.zero_()
+        status, st = mrhs.mrhs_solve(mg, b, x, n, w["tol"], rel, stream=stream)
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = mrhs.mrhs_kernel_launch_count()
+    stats = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(step())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = mrhs.mrhs_kernel_launch_count() - launches0
+    t_dev = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_dev], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+        dist.barrier()
+    max_rel = float(max(s.max_rel_residual for s in stats))
+    value = n * args.steps * world / t_dev
+
+    extra = {}
+    if rank == 0:
+        # --- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+        bh = b.cpu().pin_memory()
+        xh = torch.empty_like(bh).pin_memory()
+        ke = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        te0 = time.perf_counter()
+        for _ in range(ke):
+            b.copy_(bh, non_blocking=True)
+            x.zero_()
+            mrhs.mrhs_solve(mg, b, x, n, w["tol"], rel, stream=stream)
+            xh.copy_(x, non_blocking=True)
+            torch.cuda.synchronize()
+        te = time.perf_counter() - te0
+        bytes_io = V * 12 * n * 16
+        extra["e2e"] = {"value": n * ke / te, "unit": "solves/s", "h2d_bytes_per_step": bytes_io,
+                        "d2h_bytes_per_step": bytes_io}
+        # --- component breakdown (one profiled solve, eager V-cycle): the paper's Sec. 8 table
+        # (reported from the solve stats of the timed steps)
+        s0 = stats[-1]
+        extra["per_solve"] = {"outer_iters": s0.outer_iters, "inner_iters": s0.inner_iters, "vcycles": s0.vcycles,
+                              "seconds": s0.seconds, "max_rel_residual": max_rel}
+        extra["setup_s"] = setup_s
+        # --- roofline of the fine stencil (FP32, RHS innermost), timed alone on the launching stream
+        peak, peak_kind = read_peaks()
+        a = torch.randn((V, 12, n), dtype=torch.complex64, device="cuda", generator=gen)
+        o = torch.empty_like(a)
+        for _ in range(3):
+            mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream)
+        reps = 20
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_k = ev0.elapsed_time(ev1) * 1e-3 / reps
+        alg = V * (576 + 192 * n)
+        achieved = alg / t_k / 1e9
+        tr = profiled_traffic("dirac.cu")
+        extra["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+                             "kernel": f"k_dslash fp32, {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}, nRHS={n}",
+                             "algorithmic_bytes_per_launch": alg, "ms_per_launch": t_k * 1e3,
+                             "peak_source": f"{peak_kind} HBM copy bandwidth"}
+        del a, o
+        # --- plain solver: one RHS at a time, FP32 coarse stencil on CUDA cores, no graphs
+        if not args.no_plain:
+            mgp = mrhs.mrhs_setup_mg(lat, make_params(mrhs, 1, mrhs.MRHS_FP32, 0))
+            b1 = b[:, :, :1].contiguous()
+            x1 = torch.zeros_like(b1)
+            rel1 = np.zeros(1)
+            mrhs.mrhs_solve(mgp, b1, x1, 1, w["tol"], rel1, stream=stream)  # warm-up
+            kp = args.plain_solves
+            tp0 = time.perf_counter()
+            for i in range(kp):
+                b1.copy_(b[:, :, i:i + 1])
+                x1.zero_()
+                mrhs.mrhs_solve(mgp, b1, x1, 1, w["tol"], rel1, stream=stream)
+            torch.cuda.synchronize()
+            tp = time.perf_counter() - tp0
+            plain = kp / tp
+            extra["plain"] = {"value": plain, "unit": "solves/s", "solves_timed": kp,
+                              "ratio_mixed_batched_over_plain": value / world / plain,
+                              "desc": "same MG, nRHS=1, FP32 coarse stencil on CUDA cores, no CUDA graphs, FP64 outer"}
+            mrhs.mrhs_destroy_mg(mgp)
+        # --- CPU baseline: the oracle on one host thread, bounded sample
+        if not args.no_cpu:
+            extra["cpu_baseline"] = oracle_in_subprocess(1, 0)
+        extra["clocks"] = clk.summary()
+        extra["gpu_launches"] = launches
+        line = {
+            "metric": "MG solves/s at 1e-10", "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+bf16",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME, "nrhs_per_gpu": n, "lattice": "x".join(map(str, dims)),
+                       "mass": w["mass"], "csw": w["csw"], "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (FP64 fields of 8 GB)"},
+        }
+        line.update(extra)
+        print(json.dumps(line), flush=True)
+    mrhs.mrhs_destroy_mg(mg)
+    mrhs.mrhs_destroy_lattice(lat)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=0)
+    ap.add_argument("--plain-solves", type=int, default=2)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

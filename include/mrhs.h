@@ -65,7 +65,8 @@ typedef enum {
 typedef enum {
     MRHS_FP32 = 0,
     MRHS_FP64 = 1,
-    MRHS_BF16 = 2
+    MRHS_BF16 = 2,
+    MRHS_FP16 = 3
 } mrhs_precision;
 
 typedef struct mrhs_lattice mrhs_lattice;
@@ -76,6 +77,10 @@ typedef struct mrhs_server mrhs_server;
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *mrhs_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a replayed CUDA graph counts its kernel nodes).  Diagnostic only. */
+uint64_t mrhs_kernel_launch_count(void);
 
 /* ------------------------------------------------------------------ */
 /* Lattice, gauge field, clover term                                   */
@@ -155,7 +160,7 @@ typedef struct {
     double inner_tol;                      /* FP32 inner relative tolerance       */
     int outer_m;                           /* FP64 outer FGMRES restart length    */
     int max_outer_iters;                   /* FP64 outer iteration cap            */
-    int coarse_precision;                  /* MRHS_FP32 or MRHS_BF16 coarse links */
+    int coarse_precision;                  /* MRHS_FP32, MRHS_FP16 or MRHS_BF16   */
     int max_rhs;                           /* largest nrhs a solve may use        */
     int use_graph;                         /* replay the V-cycle as a CUDA graph  */
     uint64_t seed;                         /* start vectors when none supplied    */
@@ -198,8 +203,11 @@ mrhs_status mrhs_prolong(mrhs_mg *mg, int level, const void *coarse_dev,
                          void *fine_dev, int nrhs, void *stream);
 
 /* Coarse 9-point stencil out = D_c in on level `level` >= 1 (Sec. 6), FP32
- * fields; links_prec MRHS_FP32 (CUDA cores) or MRHS_BF16 (tensor cores,
- * FP32 accumulation; requires nc = 64). */
+ * fields; links_prec MRHS_FP32 (CUDA cores) or the level's 16-bit tensor-core
+ * format MRHS_FP16 / MRHS_BF16 (FP32 accumulation; requires nc = 64 and the
+ * hierarchy built with that coarse_precision).  The 16-bit path stores each
+ * site's links scaled by their largest component and packs the input with
+ * one scale per RHS column, so FP16 neither overflows nor underflows. */
 mrhs_status mrhs_coarse_apply(mrhs_mg *mg, int level, const void *in_dev, void *out_dev,
                               int nrhs, mrhs_precision links_prec, void *stream);
 

@@ -85,9 +85,11 @@ template <typename T> __device__ __forceinline__ void stv(T *p, int64_t i, cplx<
 // Block-level fixed-order reduction of `cols` complex values per thread
 // (vals[c] for c < cols), then the cross-block finish by the last block.
 // smem: double2 [rpb][cols][n] laid out as [(rsub*cols + c)*n + col].
+// With real_only the single column goes to out_real; with real_tail the
+// first cols-1 columns go to out and the last column's real part to out_real.
 __device__ void block_finish(double2 *smem, const double2 *vals, int cols, int n, int rpb, int col, int rsub,
                              double2 *partials, unsigned int *counter, double2 *out, bool accumulate,
-                             bool real_only, double *out_real) {
+                             bool real_only, double *out_real, bool real_tail = false) {
     for (int c = 0; c < cols; ++c) smem[((int64_t)rsub * cols + c) * n + col] = vals[c];
     __syncthreads();
     const int tid = threadIdx.x;
@@ -120,6 +122,8 @@ __device__ void block_finish(double2 *smem, const double2 *vals, int cols, int n
         }
         if (real_only) {
             out_real[o] = s.x;
+        } else if (real_tail && o >= (cols - 1) * n) {
+            out_real[o - (cols - 1) * n] = s.x;
         } else if (accumulate) {
             double2 prev = out[o];
             out[o] = make_double2(prev.x + s.x, prev.y + s.y);
@@ -248,6 +252,98 @@ __global__ void k_axpy(T a, const T *x, T *y, int64_t count) {
     stv(y, i, v);
 }
 
+// out[j][r] = <b_j, w>_r for j < k (k < KCHUNK) and nrm2[r] = ||w_r||^2, one pass over w
+template <typename T>
+__global__ void k_dots_norm(const T *__restrict__ basis, int64_t stride, int k, const T *__restrict__ w,
+                            int64_t rows, int n, int rpb, double2 *partials, unsigned int *counter, double2 *out,
+                            double *nrm2) {
+    extern __shared__ double2 smem[];
+    const int col = threadIdx.x % n;
+    const int rsub = threadIdx.x / n;
+    cplx<T> acc[KCHUNK];
+#pragma unroll
+    for (int j = 0; j < KCHUNK; ++j) acc[j] = {0, 0};
+    T nacc = 0;
+    const int64_t step = (int64_t)gridDim.x * rpb;
+    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
+        const int64_t e = row * n + col;
+        const cplx<T> x = ldv(w, e);
+        nacc = fmadd(x.re, x.re, nacc);
+        nacc = fmadd(x.im, x.im, nacc);
+#pragma unroll
+        for (int j = 0; j < KCHUNK - 1; ++j)
+            if (j < k) cmac_conj(acc[j], ldv(basis, e + j * stride), x);
+    }
+    double2 vals[KCHUNK];
+#pragma unroll
+    for (int j = 0; j < KCHUNK; ++j) vals[j] = make_double2((double)acc[j].re, (double)acc[j].im);
+    vals[k] = make_double2((double)nacc, 0.0);
+    block_finish(smem, vals, k + 1, n, rpb, col, rsub, partials, counter, out, false, false, nrm2, true);
+}
+
+// w <- (w - sum_{j<k} h_j b_j) / beta with beta^2 = max(||w||^2 - sum_{all j<kall} |h_j|^2, 1e-6 ||w||^2)
+// (Pythagoras for an orthonormal basis); writes beta^2 to hn2 and ||w_new||^2 to nn.
+// `coef` points at the first of the k coefficients handled here, `hall` at all kall of them.
+template <typename T>
+__global__ void k_lincomb_scale(T *__restrict__ w, const T *__restrict__ basis, int64_t stride, int k,
+                                const double2 *__restrict__ coef, const double2 *__restrict__ hall, int kall,
+                                const double *__restrict__ nrm2, double *__restrict__ hn2, int64_t rows, int n,
+                                int rpb, double2 *partials, unsigned int *counter, double *nn) {
+    extern __shared__ double2 smem[];
+    const int col = threadIdx.x % n;
+    const int rsub = threadIdx.x / n;
+    double hh = 0.0;
+    for (int j = 0; j < kall; ++j) {
+        const double2 c = hall[(int64_t)j * n + col];
+        hh += c.x * c.x + c.y * c.y;
+    }
+    const double w2 = nrm2[col];
+    const double b2 = fmax(w2 - hh, 1e-6 * w2);
+    const double inv = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
+    if (blockIdx.x == 0 && rsub == 0) hn2[col] = b2;
+    cplx<T> cf[KCHUNK];
+#pragma unroll
+    for (int j = 0; j < KCHUNK; ++j) {
+        if (j < k) {
+            const double2 c = coef[(int64_t)j * n + col];
+            cf[j] = {(T)(-c.x), (T)(-c.y)};
+        } else {
+            cf[j] = {0, 0};
+        }
+    }
+    const T f = (T)inv;
+    T nacc = 0;
+    const int64_t step = (int64_t)gridDim.x * rpb;
+    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
+        const int64_t e = row * n + col;
+        cplx<T> x = ldv(w, e);
+#pragma unroll
+        for (int j = 0; j < KCHUNK; ++j)
+            if (j < k) cmac(x, cf[j], ldv(basis, e + j * stride));
+        x.re *= f;
+        x.im *= f;
+        stv(w, e, x);
+        nacc = fmadd(x.re, x.re, nacc);
+        nacc = fmadd(x.im, x.im, nacc);
+    }
+    double2 v = make_double2((double)nacc, 0.0);
+    block_finish(smem, &v, 1, n, rpb, col, rsub, partials, counter, nullptr, false, true, nn);
+}
+
+// columns whose new basis vector is not unit length (cancellation in the
+// Pythagorean norm) are rescaled; the Givens step applies the same factor to beta
+template <typename T>
+__global__ void k_norm_fixup(T *__restrict__ w, const double *__restrict__ nn, int64_t count, int n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const double f = nn[i % n];
+    if (f > 0.0 && fabs(f - 1.0) > 1e-2) {
+        const T s = (T)(1.0 / sqrt(f));
+        cplx<T> x = ldv(w, i);
+        stv(w, i, cplx<T>{x.re * s, x.im * s});
+    }
+}
+
 // ------------------------------------------------------------- launchers
 static void check_n(int n) {
     if (n < 1 || n > 256) fail(MRHS_ERR_INVALID, "batched BLAS supports 1 <= nrhs <= 256");
@@ -275,6 +371,67 @@ void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const
         }
         MRHS_LAUNCHED("k_multi_dot");
     }
+}
+
+void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, int k, void *w, int64_t rows, int n,
+                         double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s) {
+    check_n(n);
+    const RedGeom g = red_geom(rows, n);
+    const bool f32 = p == MRHS_FP32;
+    if (!f32 && p != MRHS_FP64) fail(MRHS_ERR_INVALID, "orthonormalize: FP32 or FP64 fields");
+    // dots (and ||w||^2 with the last chunk)
+    for (int j0 = 0; j0 < k || j0 == 0; j0 += KCHUNK - 1) {
+        const int kk = std::min(KCHUNK - 1, k - j0);
+        const bool last = j0 + kk >= k;
+        const size_t esz = f32 ? 8 : 16;
+        if (last) {
+            sc.ensure(g.blocks, (kk + 1) * n);
+            const size_t smem = sizeof(double2) * (size_t)g.rpb * (kk + 1) * n;
+            if (f32)
+                k_dots_norm<float><<<g.blocks, g.threads, smem, s>>>(
+                    static_cast<const float *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const float *>(w),
+                    rows, n, g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), h + (int64_t)j0 * n, nrm2);
+            else
+                k_dots_norm<double><<<g.blocks, g.threads, smem, s>>>(
+                    static_cast<const double *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const double *>(w),
+                    rows, n, g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), h + (int64_t)j0 * n, nrm2);
+            MRHS_LAUNCHED("k_dots_norm");
+            break;
+        }
+        multi_dot(p, static_cast<const char *>(basis) + esz * j0 * stride, stride, kk, w, rows, n,
+                  h + (int64_t)j0 * n, sc, s);
+    }
+    // subtract, normalise
+    for (int j0 = 0; j0 < k || j0 == 0; j0 += KCHUNK) {
+        const int kk = std::min(KCHUNK, k - j0);
+        const bool last = j0 + kk >= k;
+        const size_t esz = f32 ? 8 : 16;
+        if (!last) {
+            lincomb(p, w, p, static_cast<const char *>(basis) + esz * j0 * stride, stride, kk, h + (int64_t)j0 * n,
+                    -1.0, rows, n, s);
+            continue;
+        }
+        sc.ensure(g.blocks, n);
+        const size_t smem = sizeof(double2) * (size_t)g.rpb * n;
+        if (f32)
+            k_lincomb_scale<float><<<g.blocks, g.threads, smem, s>>>(
+                static_cast<float *>(w), static_cast<const float *>(basis) + 2 * j0 * stride, stride, kk,
+                h + (int64_t)j0 * n, h, k, nrm2, hn2, rows, n, g.rpb, sc.partials.as<double2>(),
+                sc.counter.as<unsigned int>(), nn);
+        else
+            k_lincomb_scale<double><<<g.blocks, g.threads, smem, s>>>(
+                static_cast<double *>(w), static_cast<const double *>(basis) + 2 * j0 * stride, stride, kk,
+                h + (int64_t)j0 * n, h, k, nrm2, hn2, rows, n, g.rpb, sc.partials.as<double2>(),
+                sc.counter.as<unsigned int>(), nn);
+        MRHS_LAUNCHED("k_lincomb_scale");
+        break;
+    }
+    const int64_t count = rows * n;
+    if (f32)
+        k_norm_fixup<float><<<ceil_div(count, 256), 256, 0, s>>>(static_cast<float *>(w), nn, count, n);
+    else
+        k_norm_fixup<double><<<ceil_div(count, 256), 256, 0, s>>>(static_cast<double *>(w), nn, count, n);
+    MRHS_LAUNCHED("k_norm_fixup");
 }
 
 void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s) {
@@ -364,6 +521,23 @@ void axpy(mrhs_precision p, double a, const void *x, void *y, int64_t count, cud
     MRHS_LAUNCHED("k_axpy");
 }
 
+template <typename T>
+__global__ void k_scale_real(T a, T *x, int64_t count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    cplx<T> v = ldv(x, i);
+    stv(x, i, cplx<T>{a * v.re, a * v.im});
+}
+
+void scale_real(mrhs_precision p, double a, void *x, int64_t count, cudaStream_t s) {
+    const int nb = ceil_div(count, 256);
+    if (p == MRHS_FP32)
+        k_scale_real<float><<<nb, 256, 0, s>>>((float)a, static_cast<float *>(x), count);
+    else
+        k_scale_real<double><<<nb, 256, 0, s>>>(a, static_cast<double *>(x), count);
+    MRHS_LAUNCHED("k_scale_real");
+}
+
 // ------------------------------------------------- per-RHS Givens / solve
 void KrylovState::init(int m_, int n_) {
     m = m_;
@@ -376,6 +550,8 @@ void KrylovState::init(int m_, int n_) {
     hcol.alloc(sizeof(double2) * (size_t)(m + 1) * n);
     h2.alloc(sizeof(double2) * (size_t)(m + 1) * n);
     hn2.alloc(sizeof(double) * (size_t)n);
+    nrm2w.alloc(sizeof(double) * (size_t)n);
+    nn.alloc(sizeof(double) * (size_t)n);
     beta2.alloc(sizeof(double) * (size_t)n);
     res.alloc(sizeof(double) * (size_t)n);
 }
@@ -393,15 +569,23 @@ __global__ void k_krylov_start(double2 *g, const double *beta2, double *res, int
 // G [a; b] = [rho; 0]: c = |a|/t, s = (a/|a|) conj(b)/t, t = sqrt(|a|^2+|b|^2);
 // for a = 0: c = 0, s = conj(b)/|b|.
 __global__ void k_krylov_givens(double2 *R, double *cs, double2 *sn, double2 *g, const double2 *hcol,
-                                const double2 *h2, const double *hn2, double *res, int j, int n, int m) {
+                                const double2 *h2, const double *hn2, const double *nn, double *res, int j, int n,
+                                int m) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     double2 col[65];
     for (int i = 0; i <= j; ++i) {
-        const double2 a = hcol[(int64_t)i * n + r], b = h2[(int64_t)i * n + r];
+        const double2 a = hcol[(int64_t)i * n + r];
+        const double2 b = h2 ? h2[(int64_t)i * n + r] : make_double2(0.0, 0.0);
         col[i] = make_double2(a.x + b.x, a.y + b.y);
     }
-    col[j + 1] = make_double2(sqrt(fmax(hn2[r], 0.0)), 0.0);
+    double beta = sqrt(fmax(hn2[r], 0.0));
+    if (nn) {  // basis vector rescaled by the fix-up (same test as k_norm_fixup)
+        const double f = nn[r];
+        if (f > 0.0 && fabs(f - 1.0) > 1e-2) beta *= sqrt(f);
+        if (f == 0.0) beta = 0.0;
+    }
+    col[j + 1] = make_double2(beta, 0.0);
     for (int i = 0; i < j; ++i) {
         const double c = cs[(int64_t)r * m + i];
         const double2 s = sn[(int64_t)r * m + i];
@@ -466,11 +650,12 @@ void krylov_start(KrylovState &ks, int n, cudaStream_t s) {
     MRHS_LAUNCHED("k_krylov_start");
 }
 
-void krylov_givens(KrylovState &ks, int j, int n, cudaStream_t s) {
+void krylov_givens(KrylovState &ks, int j, int n, cudaStream_t s, bool single_pass) {
     if (ks.m > 64) fail(MRHS_ERR_INVALID, "Krylov restart length above 64");
-    k_krylov_givens<<<ceil_div(n, 64), 64, 0, s>>>(ks.R.as<double2>(), ks.cs.as<double>(), ks.sn.as<double2>(),
-                                                   ks.g.as<double2>(), ks.hcol.as<double2>(), ks.h2.as<double2>(),
-                                                   ks.hn2.as<double>(), ks.res.as<double>(), j, n, ks.m);
+    k_krylov_givens<<<ceil_div(n, 64), 64, 0, s>>>(
+        ks.R.as<double2>(), ks.cs.as<double>(), ks.sn.as<double2>(), ks.g.as<double2>(), ks.hcol.as<double2>(),
+        single_pass ? nullptr : ks.h2.as<double2>(), ks.hn2.as<double>(), single_pass ? ks.nn.as<double>() : nullptr,
+        ks.res.as<double>(), j, n, ks.m);
     MRHS_LAUNCHED("k_krylov_givens");
 }
 

@@ -1,6 +1,7 @@
 // C ABI entry points (include/mrhs.h): argument validation, device
 // selection, error translation.  Every call catches the library's internal
 // exceptions and returns an mrhs_status; nothing aborts the host process.
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -61,11 +62,15 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 namespace mrhs {
 mrhs_status api_record(mrhs_status code, const std::string &msg) { return record(code, msg); }
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 }
 
 extern "C" {
 
 const char *mrhs_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t mrhs_kernel_launch_count(void) { return mrhs::g_launches.load(); }
 
 mrhs_status mrhs_create_lattice(const int dims[4], int t_boundary, int device, mrhs_lattice **out) {
     MRHS_API_BEGIN

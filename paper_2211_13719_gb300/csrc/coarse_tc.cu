@@ -1,0 +1,411 @@
+// Coarse 9-point stencil on the 5th-generation tensor cores (paper Sec. 6):
+// FP16 or BF16 operands, FP32 accumulation in tensor memory, nc = 64 coarse dof.
+//
+// Scaling: each site's 9 link blocks are stored divided by their largest
+// real or imaginary component (one FP32 scale per site) and the input field
+// is packed divided by its largest component per RHS column (one scale per
+// column, found by a max-reduction before packing); both scales factor out
+// of the site's sum and are applied to the FP32 result.  FP16 (11-bit
+// significand) therefore neither overflows nor loses small magnitudes.
+//
+// Per coarse site x the stencil is one complex GEMM over the RHS block,
+//   out[K][r] = sum_{d=0..8} sum_L A_d(x)[K][L] phi(x + delta_d)[L][r],
+// computed as one real GEMM without duplicating the links: with
+//   A'_d = [Re A_d ; Im A_d]        (128 x 64, rows K and 64 + K)
+//   B_d  = [Re phi_d | Im phi_d]    (64 x 2n)
+// D = sum_d A'_d B_d (128 x 2n) holds Re A Re phi, Re A Im phi, Im A Re phi
+// and Im A Im phi, so
+//   Re out[K][r] = D[K][r] - D[64+K][n+r],   Im out[K][r] = D[64+K][r] + D[K][n+r].
+// M = 128, N = 2n rounded up to a multiple of 16, K = 9 * 64 (36 MMAs of K = 16).
+//
+// Operands sit in shared memory in the 128-byte-swizzled K-major layout the
+// MMA descriptors describe (8-row atoms of 1024 bytes, 16-byte chunk c of
+// row r stored at chunk c ^ (r % 8)).  Links are converted once into that
+// image in global memory, so each (site, direction) tile is one contiguous
+// 16 KB bulk copy; the neighbour fields are packed into the same image form
+// by a small kernel before each apply.  One CTA per coarse site: a single
+// thread issues the bulk copies through a 3-stage mbarrier ring and the
+// MMAs; all four warps then read the accumulator out of tensor memory,
+// recombine real and imaginary parts and store the FP32 result.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records an
+// error flag, drains its outstanding copies (bounded), frees its tensor
+// memory and returns.  The host reads the flag at the end of a solve.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "mg.cuh"
+
+namespace mrhs {
+
+namespace {
+
+constexpr int NC = 64;                 // coarse dof handled by this kernel
+constexpr int MROWS = 128;             // 2 * NC real rows
+constexpr int STAGES = 3;
+constexpr int A_TILE = MROWS * NC * 2; // bytes of one BF16 link tile (16 KB)
+constexpr uint32_t SPIN_LIMIT = 1u << 20;
+
+__host__ __device__ __forceinline__ int npad_of(int n) { return ((2 * n + 15) / 16) * 16; }
+
+// byte offset of element (row, k) in a swizzled K-major tile of 64 BF16 columns
+__host__ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
+    const int atom = row >> 3, r = row & 7, chunk = k >> 3, within = k & 7;
+    return (uint32_t)(atom * 1024 + r * 128 + ((chunk ^ r) << 4) + within * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred P1;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, P1;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait; false on expiry
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (uint32_t i = 0; i < SPIN_LIMIT; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// shared-memory matrix descriptor: 128B swizzle, K-major, 8-row atoms 1024 B apart
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);      // start address
+    // leading byte offset: unused for a swizzled K-major tile one atom wide (left 0)
+    d |= (uint64_t)(1024u >> 4) << 32;             // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                        // descriptor version
+    d |= (uint64_t)2 << 61;                        // 128-byte swizzle
+    return d;
+}
+
+// instruction descriptor: 16-bit A, B (fmt 0 = F16, 1 = BF16) -> FP32, both K-major, M x N
+__host__ __device__ __forceinline__ uint32_t idesc_16bit(int M, int N, uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int FMT> __device__ __forceinline__ uint16_t to16(float v);
+template <> __device__ __forceinline__ uint16_t to16<0>(float v) { return __half_as_ushort(__float2half_rn(v)); }
+template <> __device__ __forceinline__ uint16_t to16<1>(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+    int L[4];
+    int64_t V;
+    int n, npad;
+    uint32_t idesc;
+    uint32_t tmem_cols;
+};
+
+__device__ __forceinline__ int64_t nb_site(int64_t site, const int L[4], int d) {
+    if (d == 0) return site;
+    int c[4];
+    site_to_coords(site, L, c);
+    const int mu = d <= 4 ? d - 1 : d - 5;
+    const int step = d <= 4 ? 1 : -1;
+    c[mu] = (c[mu] + step + L[mu]) % L[mu];
+    return coords_to_site(c, L);
+}
+
+__global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ Abf, const uint8_t *__restrict__ Phi,
+                                                   float2 *__restrict__ out, const float2 *__restrict__ y, TcArgs a,
+                                                   const float *__restrict__ link_scale,
+                                                   const float *__restrict__ col_scale, int *__restrict__ err) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ uint64_t bars[2 * STAGES + 1];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t site = blockIdx.x;
+    const uint32_t b_tile = (uint32_t)a.npad * 128u;
+    const uint32_t stage_bytes = A_TILE + ((b_tile + 1023u) & ~1023u);
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(base);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[STAGES]), done = smem_u32(&bars[2 * STAGES]);
+
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(a.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    if (tid == 0) {
+        // producer + MMA issuer: loads run STAGES - 1 directions ahead of the MMAs
+        bool ok = true;
+        int issued = 0;
+        for (int step = 0; step < 9 + STAGES - 1 && ok; ++step) {
+            if (step < 9) {
+                const int d = step, s = d % STAGES;
+                if (d >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((d / STAGES) - 1) & 1);
+                if (!ok) break;
+                const int64_t nb = nb_site(site, a.L, d);
+                const uint32_t sa = sbase + s * stage_bytes;
+                mbar_expect_tx(full0 + 8 * s, A_TILE + b_tile);
+                bulk_g2s(sa, Abf + ((size_t)site * 9 + d) * A_TILE, A_TILE, full0 + 8 * s);
+                bulk_g2s(sa + A_TILE, Phi + (size_t)nb * b_tile, b_tile, full0 + 8 * s);
+                ++issued;
+            }
+            const int e = step - (STAGES - 1);
+            if (e >= 0 && e < 9) {
+                const int s = e % STAGES;
+                ok = mbar_wait(full0 + 8 * s, (e / STAGES) & 1);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = sbase + s * stage_bytes, sb = sa + A_TILE;
+#pragma unroll
+                for (int kk = 0; kk < NC / 16; ++kk)
+                    mma_bf16(tmem, sdesc(sa + kk * 32), sdesc(sb + kk * 32), a.idesc, (e > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(empty0 + 8 * s);
+            }
+        }
+        if (ok) {
+            mma_commit(done);
+        } else {
+            atomicExch(err, 1);
+            abort_sh = 1;
+            // drain: every issued stage's copies must land, and every issued MMA
+            // finish, before the CTA frees its tensor memory and exits
+            for (int d = 0; d < issued; ++d) mbar_wait(full0 + 8 * (d % STAGES), (d / STAGES) & 1);
+            mma_commit(done);
+            mbar_wait(done, 0);
+        }
+    }
+    __syncthreads();
+    bool ok = abort_sh == 0;
+    if (ok) ok = mbar_wait(done, 0);
+    if (!ok && tid == 0) atomicExch(err, 1);
+    __syncthreads();
+    if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // TMEM rows 32*warp .. 32*warp+31 -> shared staging D[row][col] (stage buffers are free now)
+        float *Ds = reinterpret_cast<float *>(base);
+        const int ld = a.npad + 1;
+        const int row = 32 * warp + (tid & 31);
+        for (int c0 = 0; c0 < a.npad; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) Ds[row * ld + c0 + i] = v[i];
+        }
+        __syncthreads();
+        const int n = a.n;
+        const float ls = link_scale[site];
+        for (int idx = tid; idx < NC * n; idx += blockDim.x) {
+            const int K = idx / n, r = idx - K * n;
+            const float sc = ls * col_scale[r];
+            float re = sc * (Ds[K * ld + r] - Ds[(NC + K) * ld + n + r]);
+            float im = sc * (Ds[(NC + K) * ld + r] + Ds[K * ld + n + r]);
+            const int64_t o = site * (int64_t)(NC * n) + idx;
+            if (y) {
+                const float2 yy = y[o];
+                re = yy.x - re;
+                im = yy.y - im;
+            }
+            out[o] = make_float2(re, im);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols));
+}
+
+// per-RHS scale of the input: col_scale[r] = max over sites and components of
+// max(|Re|, |Im|) (float bits compared as unsigned: valid for non-negative floats)
+__global__ void k_col_absmax(const float2 *__restrict__ phi, int64_t count, int n, unsigned *__restrict__ col_max) {
+    __shared__ unsigned sm[64];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = 0u;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = phi[i];
+        const float m = fmaxf(fabsf(v.x), fabsf(v.y));
+        atomicMax(&sm[(int)(i % n)], __float_as_uint(m));
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicMax(&col_max[i], sm[i]);
+}
+
+// coarse field [V][64][n] FP32 -> per-site swizzled 16-bit image of [Re phi | Im phi]^T / col_scale
+template <int FMT>
+__global__ void k_pack_phi(const float2 *__restrict__ phi, uint8_t *__restrict__ img, int64_t V, int n, int npad,
+                           const float *__restrict__ col_scale) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V * npad * NC) return;
+    const int64_t site = i / (npad * NC);
+    const int rem = (int)(i - site * npad * NC);
+    const int j = rem / NC, k = rem - j * NC;
+    float v = 0.f;
+    if (j < 2 * n) {
+        const int r = j < n ? j : j - n;
+        const float c = col_scale[r];
+        const float2 p = phi[(site * NC + k) * n + r];
+        v = c > 0.f ? (j < n ? p.x : p.y) / c : 0.f;
+    }
+    *reinterpret_cast<uint16_t *>(img + site * (int64_t)npad * 128 + sw128_offset(j, k)) = to16<FMT>(v);
+}
+
+// per-site scale of the links: max over the 9 blocks of max(|Re|, |Im|)
+__global__ void k_link_scale(const float2 *__restrict__ A, float *__restrict__ scale) {
+    __shared__ float red[32];
+    const int64_t site = blockIdx.x;
+    const float2 *a = A + site * 9 * NC * NC;
+    float m = 0.f;
+    for (int i = threadIdx.x; i < 9 * NC * NC; i += blockDim.x) {
+        const float2 v = a[i];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+        scale[site] = t > 0.f ? t : 1.f;
+    }
+}
+
+// links [V][9][64][64] complex FP32 -> [V][9] swizzled 16-bit tiles of [Re A ; Im A] / scale (128 x 64)
+template <int FMT>
+__global__ void k_pack_links(const float2 *__restrict__ A, uint8_t *__restrict__ img, int64_t V,
+                             const float *__restrict__ scale) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V * 9 * MROWS * NC) return;
+    const int64_t tile = i / (MROWS * NC);
+    const int rem = (int)(i - tile * MROWS * NC);
+    const int m = rem / NC, k = rem - m * NC;
+    const float2 v = A[(tile * NC + (m % NC)) * NC + k];
+    const float s = scale[tile / 9];
+    *reinterpret_cast<uint16_t *>(img + tile * (int64_t)A_TILE + sw128_offset(m, k)) = to16<FMT>((m < NC ? v.x : v.y) / s);
+}
+
+size_t tc_smem_bytes(int npad) {
+    const size_t b_tile = (size_t)npad * 128;
+    const size_t stage = A_TILE + ((b_tile + 1023) & ~size_t(1023));
+    const size_t epi = (size_t)MROWS * (npad + 1) * sizeof(float);
+    return std::max(stage * STAGES, epi) + 1024;
+}
+
+}  // namespace
+
+bool coarse_bf16_supported(const Level &c) { return c.dof == NC; }
+
+void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s) {
+    if (!coarse_bf16_supported(c)) fail(MRHS_ERR_INVALID, "16-bit tensor-core stencil needs 64 coarse dof");
+    if (fmt != MRHS_FP16 && fmt != MRHS_BF16) fail(MRHS_ERR_INVALID, "16-bit format must be FP16 or BF16");
+    c.tc_fmt = fmt;
+    c.Abf.alloc((size_t)c.V * 9 * A_TILE);
+    c.PhiBf.alloc((size_t)c.V * npad_of(64) * 128);
+    c.TcErr.alloc(sizeof(int));
+    c.LinkScale.alloc(sizeof(float) * (size_t)c.V);
+    c.ColScale.alloc(sizeof(float) * 64);
+    MRHS_CUDA(cudaMemsetAsync(c.TcErr.ptr, 0, sizeof(int), s));
+    k_link_scale<<<(unsigned)c.V, 256, 0, s>>>(c.A32.as<float2>(), c.LinkScale.as<float>());
+    MRHS_LAUNCHED("k_link_scale");
+    const int64_t count = c.V * 9 * MROWS * NC;
+    if (fmt == MRHS_FP16)
+        k_pack_links<0><<<ceil_div(count, 256), 256, 0, s>>>(c.A32.as<float2>(), c.Abf.as<uint8_t>(), c.V,
+                                                             c.LinkScale.as<float>());
+    else
+        k_pack_links<1><<<ceil_div(count, 256), 256, 0, s>>>(c.A32.as<float2>(), c.Abf.as<uint8_t>(), c.V,
+                                                             c.LinkScale.as<float>());
+    MRHS_LAUNCHED("k_pack_links");
+}
+
+void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const float2 *y, int n, cudaStream_t s) {
+    if (!c.Abf.ptr) fail(MRHS_ERR_INVALID, "16-bit links not prepared");
+    if (n < 1 || n > 64) fail(MRHS_ERR_INVALID, "tensor-core coarse stencil supports 1..64 RHS");
+    const int npad = npad_of(n);
+    MRHS_CUDA(cudaMemsetAsync(c.ColScale.ptr, 0, sizeof(float) * 64, s));
+    const int64_t fcount = c.V * NC * n;
+    const int gmax = sm_count(0) * 4;
+    k_col_absmax<<<std::max(1, std::min(gmax, ceil_div(fcount, 256))), 256, 0, s>>>(in, fcount, n,
+                                                                                  c.ColScale.as<unsigned>());
+    MRHS_LAUNCHED("k_col_absmax");
+    const int64_t count = c.V * npad * NC;
+    if (c.tc_fmt == MRHS_FP16)
+        k_pack_phi<0><<<ceil_div(count, 256), 256, 0, s>>>(in, c.PhiBf.as<uint8_t>(), c.V, n, npad,
+                                                           c.ColScale.as<float>());
+    else
+        k_pack_phi<1><<<ceil_div(count, 256), 256, 0, s>>>(in, c.PhiBf.as<uint8_t>(), c.V, n, npad,
+                                                           c.ColScale.as<float>());
+    MRHS_LAUNCHED("k_pack_phi");
+    TcArgs a;
+    for (int mu = 0; mu < 4; ++mu) a.L[mu] = c.L[mu];
+    a.V = c.V;
+    a.n = n;
+    a.npad = npad;
+    a.idesc = idesc_16bit(MROWS, npad, c.tc_fmt == MRHS_FP16 ? 0u : 1u);
+    a.tmem_cols = npad <= 32 ? 32 : (npad <= 64 ? 64 : 128);
+    const size_t smem = tc_smem_bytes(npad);
+    static bool attr = false;
+    if (!attr) {
+        MRHS_CUDA(cudaFuncSetAttribute(k_coarse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(128)));
+        attr = true;
+    }
+    k_coarse_tc<<<(unsigned)c.V, 128, smem, s>>>(c.Abf.as<uint8_t>(), c.PhiBf.as<uint8_t>(), out, y, a,
+                                                  c.LinkScale.as<float>(), c.ColScale.as<float>(), c.TcErr.as<int>());
+    MRHS_LAUNCHED("k_coarse_tc");
+}
+
+int coarse_tc_error(const Level &c) {
+    if (!c.TcErr.ptr) return 0;
+    int e = 0;
+    MRHS_CUDA(cudaMemcpy(&e, c.TcErr.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    return e;
+}
+
+}  // namespace mrhs

@@ -29,7 +29,9 @@ inline void cuda_check(cudaError_t e, const char *what) {
     }
 }
 #define MRHS_CUDA(call) ::mrhs::cuda_check((call), #call)
-#define MRHS_LAUNCHED(name) ::mrhs::cuda_check(cudaGetLastError(), name)
+// counts kernel launches (diagnostic) and checks the launch
+void count_launches(uint64_t k);
+#define MRHS_LAUNCHED(name) (::mrhs::count_launches(1), ::mrhs::cuda_check(cudaGetLastError(), name))
 
 // -------------------------------------------------------- device buffers
 struct DeviceBuffer {

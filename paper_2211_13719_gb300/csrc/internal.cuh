@@ -66,6 +66,8 @@ void scale_inv_sqrt(mrhs_precision p, void *dst, const void *src, const double *
 void cast(mrhs_precision pd, void *dst, mrhs_precision ps, const void *src, int64_t count, cudaStream_t s);
 // y = a*x + y with real a, same precision
 void axpy(mrhs_precision p, double a, const void *x, void *y, int64_t count, cudaStream_t s);
+// x *= a (real a)
+void scale_real(mrhs_precision p, double a, void *x, int64_t count, cudaStream_t s);
 
 // ----------------------------------------------- per-RHS small Krylov state
 // Hessenberg / Givens state for n RHS and restart length m (device arrays).
@@ -79,14 +81,23 @@ struct KrylovState {
     DeviceBuffer hcol;   // double2 [m+1][n] current Arnoldi column (pass 1 + pass 2)
     DeviceBuffer h2;     // double2 [m+1][n] second-pass coefficients
     DeviceBuffer hn2;    // double  [n]      ||w||^2 after orthogonalisation
+    DeviceBuffer nrm2w;  // double  [n]      ||w||^2 before orthogonalisation (single-pass scheme)
+    DeviceBuffer nn;     // double  [n]      ||v_{j+1}||^2 after normalisation (single-pass scheme)
     DeviceBuffer beta2;  // double  [n]      ||r0||^2
     DeviceBuffer res;    // double  [n]      current residual estimate |g_{j+1}|
     void init(int m_, int n_);
 };
 // g = (sqrt(beta2), 0, ...), clears rotations
 void krylov_start(KrylovState &ks, int n, cudaStream_t s);
-// fold column j (hcol[0..j], hn2) into R with Givens rotations; updates g, res
-void krylov_givens(KrylovState &ks, int j, int n, cudaStream_t s);
+// fold column j (hcol[0..j] (+ h2 for two-pass Gram-Schmidt), hn2) into R with
+// Givens rotations; updates g, res.  single_pass: h2 unused, beta corrected by nn.
+void krylov_givens(KrylovState &ks, int j, int n, cudaStream_t s, bool single_pass = false);
+// One Gram-Schmidt step against an orthonormal basis in two passes over the data:
+// h = V^H w and ||w||^2 together, then w <- (w - V h) / beta with
+// beta^2 = ||w||^2 - |h|^2 (hn2 <- beta^2), nn <- ||w_new||^2, and a fix-up that
+// rescales columns whose new norm is off by more than 1% (cancellation).
+void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, int k, void *w, int64_t rows, int n,
+                         double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s);
 // y = R^{-1} g for the first `j` columns
 void krylov_solve(KrylovState &ks, int j, int n, cudaStream_t s);
 

@@ -1,0 +1,71 @@
+// Multigrid hierarchy: levels, intergrid kernels, coarse stencil, setup.
+#pragma once
+
+#include <functional>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace mrhs {
+
+// Transfer from one level to the next and the operator of coarse levels.
+struct Level {
+    int L[4] = {1, 1, 1, 1};
+    int64_t V = 0;
+    int dof = 12;          // components per site (12 on the fine level, nc on coarse levels)
+    // transfer to the next level (l < n_levels - 1)
+    int B[4] = {1, 1, 1, 1};
+    int N = 0;             // null vectors; the next level has nc = 2N
+    int64_t asize = 0;     // sites per aggregate
+    DeviceBuffer P32;      // [V][dof][N] chirally split, block-orthonormal vectors (FP32)
+    DeviceBuffer P64;      // same in FP64 (kept for export)
+    // coarse operator (l >= 1): 9-point stencil
+    DeviceBuffer A32;      // [V][9][dof][dof] complex FP32
+    DeviceBuffer Abf;      // tensor-core layout in BF16 (dof == 64), see coarse_tc.cu
+    DeviceBuffer PhiBf;    // packed 16-bit input field of the tensor-core stencil
+    DeviceBuffer TcErr;    // int: set by the tensor-core stencil when a bounded wait expired
+    DeviceBuffer LinkScale;  // float [V]: per-site scale of the 16-bit links
+    DeviceBuffer ColScale;   // float [64]: per-RHS scale of the packed input (max |component|)
+    int tc_fmt = 0;          // MRHS_FP16 or MRHS_BF16 when the 16-bit links exist
+    int64_t rows() const { return V * dof; }
+};
+
+// Term selection of the coarse stencil for the Galerkin construction.
+struct StencilMask {
+    int diag;   // include the d = 0 (self) block
+    int dir;    // -1 all, else only direction d in 1..8
+    int cross;  // 0 all; 1 only hops leaving the aggregate; 2 only hops staying inside
+    int B[4];
+};
+
+// c = P^dagger psi: fine [V][dof][n] -> coarse [Vc][2N][n] (coarse site stride `ostride` complex)
+void restrict_fields(const Level &f, const Level &c, const float2 *fine, float2 *coarse, int n,
+                     int64_t ostride, cudaStream_t s);
+// psi = P c
+void prolong_fields(const Level &f, const Level &c, const float2 *coarse, float2 *fine, int n, cudaStream_t s);
+// out = A in (or y - A in) with FP32 links; optional mask (setup)
+void coarse_apply_fp32(const Level &c, const float2 *in, float2 *out, const float2 *y, int n, cudaStream_t s,
+                       const StencilMask *mask = nullptr);
+// BF16 tensor-core stencil (dof == 64): out = A in (or y - A in)
+void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const float2 *y, int n, cudaStream_t s);
+bool coarse_bf16_supported(const Level &c);
+// nonzero if a tensor-core stencil launch on this level gave up waiting (reads device memory)
+int coarse_tc_error(const Level &c);
+void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s);
+// FP64 modified Gram-Schmidt (twice) of the chiral halves of `vecs` per aggregate, in place
+void block_orthonormalize(const Level &f, double2 *vecs, cudaStream_t s);
+// P [V][dof][N] -> Pexp [V][dof][2N] with column K = chi*N + k nonzero only on chirality chi
+void expand_chiral(const Level &f, const float2 *P, float2 *Pexp, cudaStream_t s);
+
+// Solver entry used by the C ABI and the server (solver.cu).
+bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *tols, double *rel_out,
+              mrhs_solve_stats *st, cudaStream_t s, int max_outer,
+              const std::function<bool(const double *, int)> &stop);
+int mg_max_rhs(const mrhs_mg *mg);
+int64_t mg_fine_rows(const mrhs_mg *mg);
+int mg_device(const mrhs_mg *mg);
+int mg_outer_m(const mrhs_mg *mg);
+
+}  // namespace mrhs

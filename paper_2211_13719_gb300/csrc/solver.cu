@@ -1,0 +1,833 @@
+// Multigrid setup, V-cycle and the mixed-precision MRHS solve (paper Sec. 5-8).
+//
+// Every RHS keeps its own Krylov space: operator applications and inner
+// products are batched over the RHS index, while the small Hessenberg /
+// Givens / least-squares work runs per RHS on the device (blas.cu).  The
+// V-cycle therefore contains no host synchronisation and is replayed as a
+// CUDA graph.
+//
+// Solve structure (FGMRES preconditioned by MG, Sec. 8; precision split):
+//   outer  FGMRES(outer_m) in FP64: true residual b - D x, its inner
+//          products and norms in FP64;
+//   inner  preconditioner of each outer step = FP32 FGMRES(inner_m) on D,
+//          preconditioned by the V-cycle, to relative tolerance inner_tol;
+//   V-cycle on level l: restrict, approximate coarse solve (GMRES on the
+//          coarsest level, FGMRES preconditioned by the next V-cycle on an
+//          intermediate level), prolong, post-smooth with smooth_m GMRES
+//          iterations (FP32; coarse stencil FP32 or BF16 tensor cores).
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "mg.cuh"
+
+namespace mrhs {
+mrhs_status api_record(mrhs_status code, const std::string &msg);
+}
+
+using namespace mrhs;
+
+namespace {
+
+int current_sm_count() {
+    int dev = 0;
+    MRHS_CUDA(cudaGetDevice(&dev));
+    return sm_count(dev);
+}
+
+// ------------------------------------------------------------ operators
+struct Op {
+    int64_t rows = 0;
+    virtual ~Op() = default;
+    virtual void apply(const float2 *in, float2 *out, int n, cudaStream_t s) = 0;
+    // r = b - A x
+    virtual void residual(const float2 *x, const float2 *b, float2 *r, int n, cudaStream_t s) = 0;
+};
+
+struct FineOp : Op {
+    const mrhs_lattice *lat;
+    explicit FineOp(const mrhs_lattice *l) : lat(l) { rows = l->g.V * 12; }
+    void apply(const float2 *in, float2 *out, int n, cudaStream_t s) override {
+        dslash(*lat, MRHS_FP32, MRHS_FP32, in, out, nullptr, n, s);
+    }
+    void residual(const float2 *x, const float2 *b, float2 *r, int n, cudaStream_t s) override {
+        dslash(*lat, MRHS_FP32, MRHS_FP32, x, r, b, n, s);
+    }
+};
+
+struct CoarseOp : Op {
+    const Level *lev;
+    bool bf16;
+    CoarseOp(const Level *l, bool use_bf16) : lev(l), bf16(use_bf16) { rows = l->rows(); }
+    void apply(const float2 *in, float2 *out, int n, cudaStream_t s) override {
+        if (bf16) coarse_apply_bf16(*lev, in, out, nullptr, n, s);
+        else coarse_apply_fp32(*lev, in, out, nullptr, n, s);
+    }
+    void residual(const float2 *x, const float2 *b, float2 *r, int n, cudaStream_t s) override {
+        if (bf16) coarse_apply_bf16(*lev, x, r, b, n, s);
+        else coarse_apply_fp32(*lev, x, r, b, n, s);
+    }
+};
+
+struct Precond {
+    virtual ~Precond() = default;
+    virtual void apply(const float2 *v, float2 *z, int n, cudaStream_t s) = 0;
+};
+
+// ------------------------------------------------------- Krylov workspace
+struct KWork {
+    int m = 0, nmax = 0;
+    int64_t rows = 0;
+    bool flexible = false;
+    DeviceBuffer V, Z;
+    KrylovState ks;
+    Scratch sc;
+    void init(int m_, int64_t rows_, int nmax_, bool flex) {
+        m = m_;
+        rows = rows_;
+        nmax = nmax_;
+        flexible = flex;
+        V.alloc(sizeof(float2) * (size_t)(m + 1) * rows * nmax);
+        if (flex) Z.alloc(sizeof(float2) * (size_t)m * rows * nmax);
+        ks.init(m, nmax);
+        sc.ensure(current_sm_count() * 8, KCHUNK * nmax);
+    }
+    float2 *Vj(int j, int n) const { return V.as<float2>() + (size_t)j * rows * n; }
+    float2 *Zj(int j, int n) const { return Z.as<float2>() + (size_t)j * rows * n; }
+};
+
+// Per-iteration convergence test on the host (outer / inner solves only).
+struct HostCheck {
+    const double *target;  // host, [n] absolute residual targets
+    double *res_host;      // pinned, [n]
+    bool done = false;
+    bool test(KrylovState &ks, int n, cudaStream_t s) {
+        MRHS_CUDA(cudaMemcpyAsync(res_host, ks.res.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        MRHS_CUDA(cudaStreamSynchronize(s));
+        for (int r = 0; r < n; ++r)
+            if (!(res_host[r] <= target[r])) return false;
+        done = true;
+        return true;
+    }
+};
+
+// One cycle of GMRES(m) (FGMRES(m) if M is given) for A x = b, updating x.
+// b == nullptr stands for b = 0; x_zero: x is zero on entry.
+// Returns the number of Arnoldi steps taken.
+int krylov_cycle(Op &A, Precond *M, const float2 *b, float2 *x, int n, int m, KWork &w, cudaStream_t s, bool x_zero,
+                 HostCheck *chk) {
+    const int64_t rows = A.rows;
+    const int64_t F = rows * n;
+    float2 *V0 = w.Vj(0, n);
+    if (x_zero) {
+        MRHS_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * F, s));
+        if (b) MRHS_CUDA(cudaMemcpyAsync(V0, b, sizeof(float2) * F, cudaMemcpyDeviceToDevice, s));
+        else MRHS_CUDA(cudaMemsetAsync(V0, 0, sizeof(float2) * F, s));
+    } else if (b) {
+        A.residual(x, b, V0, n, s);
+    } else {
+        A.apply(x, V0, n, s);
+        scale_real(MRHS_FP32, -1.0, V0, F, s);
+    }
+    KrylovState &ks = w.ks;
+    norm2(MRHS_FP32, V0, rows, n, ks.beta2.as<double>(), w.sc, s);
+    krylov_start(ks, n, s);
+    scale_inv_sqrt(MRHS_FP32, V0, V0, ks.beta2.as<double>(), rows, n, s);
+    int steps = m;
+    for (int j = 0; j < m; ++j) {
+        const float2 *vj = w.Vj(j, n);
+        const float2 *zj = vj;
+        if (M) {
+            float2 *z = w.Zj(j, n);
+            M->apply(vj, z, n, s);
+            zj = z;
+        }
+        float2 *wj = w.Vj(j + 1, n);
+        A.apply(zj, wj, n, s);
+        orthonormalize_step(MRHS_FP32, V0, F, j + 1, wj, rows, n, ks.hcol.as<double2>(), ks.nrm2w.as<double>(),
+                            ks.hn2.as<double>(), ks.nn.as<double>(), w.sc, s);
+        krylov_givens(ks, j, n, s, true);
+        if (chk && chk->test(ks, n, s)) {
+            steps = j + 1;
+            break;
+        }
+    }
+    krylov_solve(ks, steps, n, s);
+    lincomb(MRHS_FP32, x, MRHS_FP32, M ? w.Zj(0, n) : V0, F, steps, ks.y.as<double2>(), 1.0, rows, n, s);
+    return steps;
+}
+
+// ------------------------------------------------------- level workspace
+struct LevelWork {
+    DeviceBuffer rhs, sol;  // coarse levels: restricted residual and coarse solution
+    KWork solve;            // coarse levels: GMRES (coarsest) or FGMRES (intermediate)
+    KWork smooth;           // levels with a coarser level: post-smoother GMRES
+};
+
+struct GraphKey {
+    int n;
+    const void *in;
+    void *out;
+    bool operator<(const GraphKey &o) const {
+        if (n != o.n) return n < o.n;
+        if (in != o.in) return in < o.in;
+        return out < o.out;
+    }
+};
+
+}  // namespace
+
+// --------------------------------------------------------------- handle
+struct mrhs_mg {
+    mrhs_lattice *lat = nullptr;
+    mrhs_mg_params p{};
+    int nlev = 0;
+    int nmax = 0;
+    std::vector<Level> lev;
+    std::vector<LevelWork> work;
+    std::vector<std::unique_ptr<Op>> ops;
+    bool bf16 = false;
+    // inner FP32 MG-FGMRES on the fine level
+    KWork inner;
+    DeviceBuffer inner_b;
+    // outer FP64 FGMRES
+    int om = 0;
+    DeviceBuffer oV, oZ;  // FP64 [(om+1)][rows][nmax], FP32 [om][rows][nmax]
+    KrylovState oks;
+    Scratch osc;
+    DeviceBuffer obn2;    // double [nmax]
+    double *pinned = nullptr;  // host staging, 4*nmax doubles
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<GraphKey, uint64_t> graph_kernels;  // kernel nodes per graph
+    // component timing (profiled, non-graph solves only)
+    bool profile = false;
+    double t_fine = 0, t_restrict = 0, t_prolong = 0, t_coarse = 0;
+    int vcycles = 0;
+    // the solver's own stream: graphs cannot be captured on the legacy default stream
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    ~mrhs_mg() {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+        if (pinned) cudaFreeHost(pinned);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (own) cudaStreamDestroy(own);
+    }
+};
+
+namespace {
+
+struct EventTimer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaStream_t s;
+    double *acc;
+    bool on;
+    EventTimer(bool enabled, cudaStream_t st, double *accum) : s(st), acc(accum), on(enabled) {
+        if (!on) return;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s);
+    }
+    ~EventTimer() {
+        if (!on) return;
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        *acc += ms * 1e-3;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t s);
+
+struct VcyclePrecond : Precond {
+    mrhs_mg *mg;
+    int level;
+    VcyclePrecond(mrhs_mg *g, int l) : mg(g), level(l) {}
+    void apply(const float2 *v, float2 *z, int n, cudaStream_t s) override { vcycle(*mg, level, v, z, n, s); }
+};
+
+void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t s) {
+    Level &F = mg.lev[l];
+    Level &Cl = mg.lev[l + 1];
+    LevelWork &WC = mg.work[l + 1];
+    const bool prof = mg.profile && l == 0;
+    {
+        EventTimer t(prof, s, &mg.t_restrict);
+        restrict_fields(F, Cl, v, WC.rhs.as<float2>(), n, (int64_t)Cl.dof * n, s);
+    }
+    {
+        EventTimer t(prof, s, &mg.t_coarse);
+        Op &Ac = *mg.ops[l + 1];
+        float2 *sol = WC.sol.as<float2>();
+        if (l + 1 == mg.nlev - 1) {
+            for (int c = 0; c < mg.p.coarse_cycles; ++c)
+                krylov_cycle(Ac, nullptr, WC.rhs.as<float2>(), sol, n, mg.p.coarse_m, WC.solve, s, c == 0, nullptr);
+        } else {
+            VcyclePrecond M(&mg, l + 1);
+            krylov_cycle(Ac, &M, WC.rhs.as<float2>(), sol, n, mg.p.inter_m, WC.solve, s, true, nullptr);
+        }
+    }
+    {
+        EventTimer t(prof, s, &mg.t_prolong);
+        prolong_fields(F, Cl, WC.sol.as<float2>(), z, n, s);
+    }
+    {
+        EventTimer t(prof, s, &mg.t_fine);
+        krylov_cycle(*mg.ops[l], nullptr, v, z, n, mg.p.smooth_m, mg.work[l].smooth, s, false, nullptr);
+    }
+    if (l == 0) mg.vcycles++;
+}
+
+// V-cycle on the fine level, replayed from a CUDA graph per (n, in, out).
+struct FinePrecond : Precond {
+    mrhs_mg *mg;
+    explicit FinePrecond(mrhs_mg *g) : mg(g) {}
+    void apply(const float2 *v, float2 *z, int n, cudaStream_t s) override {
+        if (!mg->p.use_graph || mg->profile) {
+            vcycle(*mg, 0, v, z, n, s);
+            return;
+        }
+        GraphKey key{n, v, z};
+        auto it = mg->graphs.find(key);
+        if (it == mg->graphs.end()) {
+            // first use: run once eagerly (sizes every lazily configured kernel), then capture
+            vcycle(*mg, 0, v, z, n, s);
+            cudaGraph_t g = nullptr;
+            MRHS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            try {
+                vcycle(*mg, 0, v, z, n, s);
+            } catch (...) {
+                cudaStreamEndCapture(s, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            MRHS_CUDA(cudaStreamEndCapture(s, &g));
+            cudaGraphExec_t ex = nullptr;
+            MRHS_CUDA(cudaGraphInstantiate(&ex, g, 0));
+            size_t nn = 0;
+            MRHS_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (nn) MRHS_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+            uint64_t kern = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+            }
+            cudaGraphDestroy(g);
+            mg->graph_kernels[key] = kern;
+            it = mg->graphs.emplace(key, ex).first;
+            return;  // the eager run already produced z
+        }
+        MRHS_CUDA(cudaGraphLaunch(it->second, s));
+        count_launches(mg->graph_kernels[key]);
+        mg->vcycles++;
+    }
+};
+
+// FP32 MG-preconditioned FGMRES on the fine level: x = approx D^{-1} b.
+int inner_solve(mrhs_mg &mg, const float2 *b, float2 *x, int n, cudaStream_t s) {
+    Op &A = *mg.ops[0];
+    FinePrecond M(&mg);
+    const int64_t F = A.rows * n;
+    MRHS_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * F, s));
+    double *bn = mg.pinned + 2 * mg.nmax;
+    double *target = mg.pinned + 3 * mg.nmax;
+    norm2(MRHS_FP32, b, A.rows, n, mg.inner.ks.beta2.as<double>(), mg.inner.sc, s);
+    MRHS_CUDA(cudaMemcpyAsync(bn, mg.inner.ks.beta2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < n; ++r) target[r] = mg.p.inner_tol * std::sqrt(bn[r]);
+    HostCheck chk{target, mg.pinned + mg.nmax};
+    int total = 0;
+    bool first = true;
+    while (total < mg.p.inner_max_iters && !chk.done) {
+        const int m = std::min(mg.p.inner_m, mg.p.inner_max_iters - total);
+        total += krylov_cycle(A, &M, b, x, n, m, mg.inner, s, first, &chk);
+        first = false;
+    }
+    return total;
+}
+
+void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
+    if (p.n_levels < 2 || p.n_levels > MRHS_MAX_LEVELS) fail(MRHS_ERR_INVALID, "n_levels must be 2 or 3");
+    int L[4] = {lat->g.L[0], lat->g.L[1], lat->g.L[2], lat->g.L[3]};
+    int dof = 12;
+    for (int l = 0; l < p.n_levels - 1; ++l) {
+        for (int mu = 0; mu < 4; ++mu) {
+            if (p.block[l][mu] < 1 || L[mu] % p.block[l][mu])
+                fail(MRHS_ERR_INVALID, "aggregate extents must divide the level's lattice extents");
+            L[mu] /= p.block[l][mu];
+        }
+        const int N = p.n_vec[l];
+        if (N < 1 || N > 32) fail(MRHS_ERR_INVALID, "n_vec must be in 1..32");
+        int64_t asize = (int64_t)p.block[l][0] * p.block[l][1] * p.block[l][2] * p.block[l][3];
+        if (asize * (dof / 2) < N) fail(MRHS_ERR_INVALID, "aggregate too small for n_vec vectors per chirality");
+        dof = 2 * N;
+    }
+    if (p.smooth_m < 1 || p.smooth_m > 64 || p.coarse_m < 1 || p.coarse_m > 64 || p.inner_m < 1 || p.inner_m > 64 ||
+        p.outer_m < 1 || p.outer_m > 64 || p.setup_m < 1 || p.setup_m > 64 || p.inter_m < 1 || p.inter_m > 64)
+        fail(MRHS_ERR_INVALID, "Krylov lengths must be in 1..64");
+    if (p.coarse_cycles < 1 || p.setup_sweeps < 0 || p.inner_max_iters < 1 || p.max_outer_iters < 1)
+        fail(MRHS_ERR_INVALID, "iteration counts must be positive");
+    if (p.max_rhs < 1 || p.max_rhs > 64) fail(MRHS_ERR_INVALID, "max_rhs must be in 1..64");
+    if (p.coarse_precision != MRHS_FP32 && p.coarse_precision != MRHS_BF16 && p.coarse_precision != MRHS_FP16)
+        fail(MRHS_ERR_INVALID, "coarse_precision must be FP32, FP16 or BF16");
+    if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
+}
+
+void setup_level(mrhs_mg &mg, int l, cudaStream_t s) {
+    Level &F = mg.lev[l];
+    Level &Cl = mg.lev[l + 1];
+    const int N = F.N;
+    const int64_t count = F.V * F.dof * N;
+    // start vectors
+    DeviceBuffer v64(sizeof(double2) * count);
+    DeviceBuffer v32(sizeof(float2) * count);
+    if (mg.p.init_vecs[l]) {
+        MRHS_CUDA(cudaMemcpyAsync(v64.ptr, mg.p.init_vecs[l], sizeof(double2) * count, cudaMemcpyHostToDevice, s));
+        cast(MRHS_FP32, v32.ptr, MRHS_FP64, v64.ptr, count, s);
+    } else {
+        fill_gaussian(MRHS_FP32, v32.ptr, count, mg.p.seed * 0x9E3779B9ull + (uint64_t)l, s);
+    }
+    // relaxation of A v = 0, the N vectors as N right-hand sides
+    if (mg.p.setup_sweeps > 0) {
+        KWork rw;
+        rw.init(mg.p.setup_m, F.rows(), N, false);
+        for (int sweep = 0; sweep < mg.p.setup_sweeps; ++sweep) {
+            krylov_cycle(*mg.ops[l], nullptr, nullptr, v32.as<float2>(), N, mg.p.setup_m, rw, s, false, nullptr);
+            norm2(MRHS_FP32, v32.ptr, F.rows(), N, rw.ks.beta2.as<double>(), rw.sc, s);
+            scale_inv_sqrt(MRHS_FP32, v32.ptr, v32.ptr, rw.ks.beta2.as<double>(), F.rows(), N, s);
+        }
+        cast(MRHS_FP64, v64.ptr, MRHS_FP32, v32.ptr, count, s);
+    } else if (!mg.p.init_vecs[l]) {
+        cast(MRHS_FP64, v64.ptr, MRHS_FP32, v32.ptr, count, s);
+    }
+    // chiral split + FP64 block orthonormalisation
+    block_orthonormalize(F, v64.as<double2>(), s);
+    F.P64 = std::move(v64);
+    F.P32.alloc(sizeof(float2) * count);
+    cast(MRHS_FP32, F.P32.ptr, MRHS_FP64, F.P64.ptr, count, s);
+    v32.release();
+    // Galerkin coarse operator R A P, stencil block by stencil block
+    const int nc = 2 * N;
+    Cl.A32.alloc(sizeof(float2) * (size_t)Cl.V * 9 * nc * nc);
+    DeviceBuffer Pe(sizeof(float2) * (size_t)F.V * F.dof * nc);
+    DeviceBuffer H(sizeof(float2) * (size_t)F.V * F.dof * nc);
+    expand_chiral(F, F.P32.as<float2>(), Pe.as<float2>(), s);
+    const int64_t ostride = (int64_t)9 * nc * nc;
+    for (int d = 0; d < 9; ++d) {
+        if (l == 0) {
+            HopMask m{d == 0 ? 1 : 0, d == 0 ? -1 : d, d == 0 ? 2 : 1, {F.B[0], F.B[1], F.B[2], F.B[3]}};
+            dslash(*mg.lat, MRHS_FP32, MRHS_FP32, Pe.ptr, H.ptr, nullptr, nc, s, &m);
+        } else {
+            StencilMask m{d == 0 ? 1 : 0, d == 0 ? -1 : d, d == 0 ? 2 : 1, {F.B[0], F.B[1], F.B[2], F.B[3]}};
+            coarse_apply_fp32(F, Pe.as<float2>(), H.as<float2>(), nullptr, nc, s, &m);
+        }
+        restrict_fields(F, Cl, H.as<float2>(), Cl.A32.as<float2>() + (size_t)d * nc * nc, nc, ostride, s);
+    }
+    MRHS_CUDA(cudaStreamSynchronize(s));
+}
+
+void alloc_workspace(mrhs_mg &mg) {
+    const int nmax = mg.nmax;
+    mg.work.resize(mg.nlev);
+    for (int l = 0; l < mg.nlev; ++l) {
+        Level &L = mg.lev[l];
+        LevelWork &W = mg.work[l];
+        if (l >= 1) {
+            W.rhs.alloc(sizeof(float2) * (size_t)L.rows() * nmax);
+            W.sol.alloc(sizeof(float2) * (size_t)L.rows() * nmax);
+            if (l == mg.nlev - 1) W.solve.init(mg.p.coarse_m, L.rows(), nmax, false);
+            else W.solve.init(mg.p.inter_m, L.rows(), nmax, true);
+        }
+        if (l < mg.nlev - 1) W.smooth.init(mg.p.smooth_m, L.rows(), nmax, false);
+    }
+    const int64_t rows = mg.lev[0].rows();
+    mg.inner.init(mg.p.inner_m, rows, nmax, true);
+    mg.inner_b.alloc(sizeof(float2) * (size_t)rows * nmax);
+    mg.om = mg.p.outer_m;
+    mg.oV.alloc(sizeof(double2) * (size_t)(mg.om + 1) * rows * nmax);
+    mg.oZ.alloc(sizeof(float2) * (size_t)mg.om * rows * nmax);
+    mg.oks.init(mg.om, nmax);
+    mg.osc.ensure(current_sm_count() * 8, KCHUNK * nmax);
+    mg.obn2.alloc(sizeof(double) * nmax);
+    MRHS_CUDA(cudaMallocHost(&mg.pinned, sizeof(double) * 4 * nmax));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- solve
+namespace mrhs {
+
+// Outer FP64 FGMRES; returns true if every RHS r reached tols[r].
+// max_outer > 0 caps the outer iterations of this call (else the params' cap);
+// stop(res, n) is asked after every outer iteration with the per-RHS residual
+// estimates and may end the cycle early (used by the server to free slots).
+bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *tols, double *rel_out,
+              mrhs_solve_stats *st, cudaStream_t s, int max_outer, const std::function<bool(const double *, int)> &stop) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const mrhs_lattice &lat = *mg.lat;
+    const int64_t rows = mg.lev[0].rows();
+    const int64_t F = rows * n;
+    double2 *V0 = mg.oV.as<double2>();
+    float2 *Z0 = mg.oZ.as<float2>();
+    double *hbn2 = mg.pinned;          // ||b||^2
+    double *hres = mg.pinned + mg.nmax;
+    std::vector<double> target(n), rel(n, 0.0), relest(n, 0.0);
+    mg.vcycles = 0;
+    int outer = 0, inner_total = 0;
+    norm2(MRHS_FP64, b, rows, n, mg.obn2.as<double>(), mg.osc, s);
+    MRHS_CUDA(cudaMemcpyAsync(hbn2, mg.obn2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> bn2(hbn2, hbn2 + n);
+    for (int r = 0; r < n; ++r) target[r] = 0.5 * tols[r] * std::sqrt(bn2[r]);
+    const int cap = max_outer > 0 ? max_outer : mg.p.max_outer_iters;
+    bool converged = false;
+    while (true) {
+        // true residual in FP64
+        dslash(lat, MRHS_FP64, MRHS_FP64, x, V0, b, n, s);
+        norm2(MRHS_FP64, V0, rows, n, mg.oks.beta2.as<double>(), mg.osc, s);
+        MRHS_CUDA(cudaMemcpyAsync(hres, mg.oks.beta2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        MRHS_CUDA(cudaStreamSynchronize(s));
+        converged = true;
+        for (int r = 0; r < n; ++r) {
+            rel[r] = bn2[r] > 0 ? std::sqrt(hres[r] / bn2[r]) : std::sqrt(hres[r]);
+            if (!(rel[r] <= tols[r])) converged = false;
+        }
+        if (converged || outer >= cap) break;
+        krylov_start(mg.oks, n, s);
+        scale_inv_sqrt(MRHS_FP64, V0, V0, mg.oks.beta2.as<double>(), rows, n, s);
+        int steps = mg.om;
+        for (int j = 0; j < mg.om; ++j) {
+            float2 *zj = Z0 + (size_t)j * F;
+            double2 *vj = V0 + (size_t)j * F;
+            double2 *wj = V0 + (size_t)(j + 1) * F;
+            cast(MRHS_FP32, mg.inner_b.ptr, MRHS_FP64, vj, F, s);
+            inner_total += inner_solve(mg, mg.inner_b.as<float2>(), zj, n, s);
+            dslash(lat, MRHS_FP64, MRHS_FP32, zj, wj, nullptr, n, s);
+            double2 *hcol = mg.oks.hcol.as<double2>();
+            double2 *h2 = mg.oks.h2.as<double2>();
+            multi_dot(MRHS_FP64, V0, F, j + 1, wj, rows, n, hcol, mg.osc, s);
+            lincomb(MRHS_FP64, wj, MRHS_FP64, V0, F, j + 1, hcol, -1.0, rows, n, s);
+            multi_dot(MRHS_FP64, V0, F, j + 1, wj, rows, n, h2, mg.osc, s);
+            lincomb(MRHS_FP64, wj, MRHS_FP64, V0, F, j + 1, h2, -1.0, rows, n, s, mg.oks.hn2.as<double>(), &mg.osc);
+            scale_inv_sqrt(MRHS_FP64, wj, wj, mg.oks.hn2.as<double>(), rows, n, s);
+            krylov_givens(mg.oks, j, n, s);
+            ++outer;
+            HostCheck chk{target.data(), hres};
+            bool halt = chk.test(mg.oks, n, s) || outer >= cap;
+            if (!halt && stop) {
+                for (int r = 0; r < n; ++r) relest[r] = bn2[r] > 0 ? hres[r] / std::sqrt(bn2[r]) : 0.0;
+                halt = stop(relest.data(), n);
+            }
+            if (halt) {
+                steps = j + 1;
+                break;
+            }
+        }
+        krylov_solve(mg.oks, steps, n, s);
+        lincomb(MRHS_FP64, x, MRHS_FP32, Z0, F, steps, mg.oks.y.as<double2>(), 1.0, rows, n, s);
+    }
+    for (int l = 1; l < mg.nlev; ++l) {
+        if (coarse_tc_error(mg.lev[l])) {
+            MRHS_CUDA(cudaMemsetAsync(mg.lev[l].TcErr.ptr, 0, sizeof(int), s));
+            MRHS_CUDA(cudaStreamSynchronize(s));
+            fail(MRHS_ERR_TIMEOUT, "tensor-core coarse stencil gave up waiting for its operands");
+        }
+    }
+    if (rel_out)
+        for (int r = 0; r < n; ++r) rel_out[r] = rel[r];
+    if (st) {
+        st->outer_iters = outer;
+        st->inner_iters = inner_total;
+        st->vcycles = mg.vcycles;
+        st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        double mx = 0;
+        for (int r = 0; r < n; ++r) mx = std::max(mx, rel[r]);
+        st->max_rel_residual = mx;
+    }
+    return converged;
+}
+
+int mg_max_rhs(const mrhs_mg *mg) { return mg->nmax; }
+int64_t mg_fine_rows(const mrhs_mg *mg) { return mg->lev[0].rows(); }
+int mg_device(const mrhs_mg *mg) { return mg->lat->device; }
+int mg_outer_m(const mrhs_mg *mg) { return mg->p.outer_m; }
+
+}  // namespace mrhs
+
+// ------------------------------------------------------------- C ABI
+namespace {
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int d) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            prev = -1;
+        }
+        if (prev != d) MRHS_CUDA(cudaSetDevice(d));
+    }
+    ~DevGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+mrhs_status ok() {
+    api_record(MRHS_OK, "");
+    return MRHS_OK;
+}
+
+#define API_TRY try {
+#define API_CATCH                                                                   \
+    }                                                                               \
+    catch (const mrhs::Error &e) { return api_record(e.code, e.what()); }           \
+    catch (const std::bad_alloc &) { return api_record(MRHS_ERR_OOM, "host allocation failed"); } \
+    catch (const std::exception &e) { return api_record(MRHS_ERR_CUDA, e.what()); }
+
+void check_level(mrhs_mg *mg, int level, int min_level, int max_level) {
+    if (!mg) fail(MRHS_ERR_INVALID, "mg must be non-null");
+    if (level < min_level || level > max_level) fail(MRHS_ERR_INVALID, "level out of range");
+}
+
+void check_n(mrhs_mg *mg, int nrhs) {
+    if (nrhs < 1 || nrhs > mg->nmax) fail(MRHS_ERR_INVALID, "nrhs must be in 1..max_rhs");
+}
+
+}  // namespace
+
+extern "C" {
+
+void mrhs_mg_default_params(mrhs_mg_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->n_levels = 3;
+    for (int mu = 0; mu < 4; ++mu) {
+        p->block[0][mu] = 4;
+        p->block[1][mu] = 2;
+    }
+    p->n_vec[0] = 32;
+    p->n_vec[1] = 32;
+    p->setup_sweeps = 6;
+    p->setup_m = 8;
+    p->smooth_m = 4;
+    p->coarse_m = 16;
+    p->coarse_cycles = 2;
+    p->inter_m = 8;
+    p->inner_m = 8;
+    p->inner_max_iters = 200;
+    p->inner_tol = 1e-5;
+    p->outer_m = 4;
+    p->max_outer_iters = 30;
+    p->coarse_precision = MRHS_FP32;
+    p->max_rhs = 48;
+    p->use_graph = 1;
+    p->seed = 1234;
+}
+
+mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_mg **out) {
+    API_TRY
+    if (!lat || !params || !out) fail(MRHS_ERR_INVALID, "lattice, params and out must be non-null");
+    *out = nullptr;
+    if (!lat->has_clover) fail(MRHS_ERR_INVALID, "clover term not built");
+    validate_params(lat, *params);
+    DevGuard dg(lat->device);
+    auto mg = std::make_unique<mrhs_mg>();
+    mg->lat = lat;
+    mg->p = *params;
+    mg->nlev = params->n_levels;
+    mg->nmax = params->max_rhs;
+    mg->profile = std::getenv("MRHS_PROFILE") && std::atoi(std::getenv("MRHS_PROFILE")) != 0;
+    mg->lev.resize(mg->nlev);
+    // geometry
+    Level &f = mg->lev[0];
+    for (int mu = 0; mu < 4; ++mu) f.L[mu] = lat->g.L[mu];
+    f.V = lat->g.V;
+    f.dof = 12;
+    for (int l = 0; l < mg->nlev - 1; ++l) {
+        Level &F = mg->lev[l];
+        Level &C = mg->lev[l + 1];
+        for (int mu = 0; mu < 4; ++mu) {
+            F.B[mu] = params->block[l][mu];
+            C.L[mu] = F.L[mu] / F.B[mu];
+        }
+        F.N = params->n_vec[l];
+        F.asize = (int64_t)F.B[0] * F.B[1] * F.B[2] * F.B[3];
+        C.V = (int64_t)C.L[0] * C.L[1] * C.L[2] * C.L[3];
+        C.dof = 2 * F.N;
+    }
+    mg->ops.emplace_back(new FineOp(lat));
+    cudaStream_t s = nullptr;
+    MRHS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    try {
+        for (int l = 0; l < mg->nlev - 1; ++l) {
+            setup_level(*mg, l, s);
+            Level &C = mg->lev[l + 1];
+            const bool use_tc = (params->coarse_precision == MRHS_BF16 || params->coarse_precision == MRHS_FP16) &&
+                                coarse_bf16_supported(C);
+            if (use_tc) coarse_links_to_16bit(C, (mrhs_precision)params->coarse_precision, s);
+            mg->ops.emplace_back(new CoarseOp(&C, use_tc));
+        }
+        MRHS_CUDA(cudaStreamSynchronize(s));
+        alloc_workspace(*mg);
+        MRHS_CUDA(cudaStreamCreateWithFlags(&mg->own, cudaStreamNonBlocking));
+        MRHS_CUDA(cudaEventCreateWithFlags(&mg->ev_in, cudaEventDisableTiming));
+        MRHS_CUDA(cudaEventCreateWithFlags(&mg->ev_out, cudaEventDisableTiming));
+    } catch (...) {
+        cudaStreamDestroy(s);
+        throw;
+    }
+    cudaStreamDestroy(s);
+    *out = mg.release();
+    return ok();
+    API_CATCH
+}
+
+void mrhs_destroy_mg(mrhs_mg *mg) {
+    if (!mg) return;
+    try {
+        DevGuard dg(mg->lat->device);
+        cudaDeviceSynchronize();
+        delete mg;
+    } catch (...) {
+        delete mg;
+    }
+}
+
+mrhs_status mrhs_mg_level_info(mrhs_mg *mg, int level, int dims[4], int *dof) {
+    API_TRY
+    check_level(mg, level, 0, mg ? mg->nlev - 1 : 0);
+    if (!dims || !dof) fail(MRHS_ERR_INVALID, "outputs must be non-null");
+    for (int mu = 0; mu < 4; ++mu) dims[mu] = mg->lev[level].L[mu];
+    *dof = mg->lev[level].dof;
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_mg_get_prolongator(mrhs_mg *mg, int level, double *host_out) {
+    API_TRY
+    check_level(mg, level, 0, mg ? mg->nlev - 2 : 0);
+    if (!host_out) fail(MRHS_ERR_INVALID, "output must be non-null");
+    DevGuard dg(mg->lat->device);
+    const Level &F = mg->lev[level];
+    MRHS_CUDA(cudaMemcpy(host_out, F.P64.ptr, sizeof(double2) * F.V * F.dof * F.N, cudaMemcpyDeviceToHost));
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_mg_get_coarse_links(mrhs_mg *mg, int level, double *host_out) {
+    API_TRY
+    check_level(mg, level, 1, mg ? mg->nlev - 1 : 1);
+    if (!host_out) fail(MRHS_ERR_INVALID, "output must be non-null");
+    DevGuard dg(mg->lat->device);
+    const Level &C = mg->lev[level];
+    const size_t count = (size_t)C.V * 9 * C.dof * C.dof;
+    std::vector<float2> tmp(count);
+    MRHS_CUDA(cudaMemcpy(tmp.data(), C.A32.ptr, sizeof(float2) * count, cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < count; ++i) {
+        host_out[2 * i] = tmp[i].x;
+        host_out[2 * i + 1] = tmp[i].y;
+    }
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_restrict(mrhs_mg *mg, int level, const void *fine_dev, void *coarse_dev, int nrhs, void *stream) {
+    API_TRY
+    check_level(mg, level, 0, mg ? mg->nlev - 2 : 0);
+    check_n(mg, nrhs);
+    if (!fine_dev || !coarse_dev) fail(MRHS_ERR_INVALID, "fields must be non-null");
+    DevGuard dg(mg->lat->device);
+    const Level &C = mg->lev[level + 1];
+    restrict_fields(mg->lev[level], C, static_cast<const float2 *>(fine_dev), static_cast<float2 *>(coarse_dev), nrhs,
+                    (int64_t)C.dof * nrhs, static_cast<cudaStream_t>(stream));
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_prolong(mrhs_mg *mg, int level, const void *coarse_dev, void *fine_dev, int nrhs, void *stream) {
+    API_TRY
+    check_level(mg, level, 0, mg ? mg->nlev - 2 : 0);
+    check_n(mg, nrhs);
+    if (!fine_dev || !coarse_dev) fail(MRHS_ERR_INVALID, "fields must be non-null");
+    DevGuard dg(mg->lat->device);
+    prolong_fields(mg->lev[level], mg->lev[level + 1], static_cast<const float2 *>(coarse_dev),
+                   static_cast<float2 *>(fine_dev), nrhs, static_cast<cudaStream_t>(stream));
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_coarse_apply(mrhs_mg *mg, int level, const void *in_dev, void *out_dev, int nrhs,
+                              mrhs_precision links_prec, void *stream) {
+    API_TRY
+    check_level(mg, level, 1, mg ? mg->nlev - 1 : 1);
+    if (nrhs < 1 || nrhs > 64) fail(MRHS_ERR_INVALID, "nrhs must be in 1..64");
+    if (!in_dev || !out_dev || in_dev == out_dev) fail(MRHS_ERR_INVALID, "distinct non-null fields required");
+    DevGuard dg(mg->lat->device);
+    const Level &C = mg->lev[level];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (links_prec == MRHS_FP32) {
+        coarse_apply_fp32(C, static_cast<const float2 *>(in_dev), static_cast<float2 *>(out_dev), nullptr, nrhs, s);
+    } else if (links_prec == MRHS_BF16 || links_prec == MRHS_FP16) {
+        if (!C.Abf.ptr || C.tc_fmt != links_prec)
+            fail(MRHS_ERR_INVALID, "no 16-bit links of this format on this level (needs nc = 64 and that coarse_precision)");
+        coarse_apply_bf16(C, static_cast<const float2 *>(in_dev), static_cast<float2 *>(out_dev), nullptr, nrhs, s);
+    } else {
+        fail(MRHS_ERR_INVALID, "links precision must be FP32 or BF16");
+    }
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_vcycle(mrhs_mg *mg, const void *v_dev, void *z_dev, int nrhs, void *stream) {
+    API_TRY
+    check_level(mg, 0, 0, 0);
+    check_n(mg, nrhs);
+    if (!v_dev || !z_dev || v_dev == z_dev) fail(MRHS_ERR_INVALID, "distinct non-null fields required");
+    DevGuard dg(mg->lat->device);
+    vcycle(*mg, 0, static_cast<const float2 *>(v_dev), static_cast<float2 *>(z_dev), nrhs,
+           static_cast<cudaStream_t>(stream));
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, double tol, double *rel_res_host,
+                       mrhs_solve_stats *stats, void *stream) {
+    API_TRY
+    if (!mg) fail(MRHS_ERR_INVALID, "mg must be non-null");
+    check_n(mg, nrhs);
+    if (!b_dev || !x_dev || b_dev == x_dev) fail(MRHS_ERR_INVALID, "distinct non-null b and x required");
+    if (!(tol > 0 && tol < 1)) fail(MRHS_ERR_INVALID, "tol must be in (0, 1)");
+    DevGuard dg(mg->lat->device);
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    mg->t_fine = mg->t_restrict = mg->t_prolong = mg->t_coarse = 0;
+    std::vector<double> tols(nrhs, tol);
+    // order the solve after the caller's prior work on `stream`, run it on the
+    // solver's own stream, and order the caller's later work after it
+    MRHS_CUDA(cudaEventRecord(mg->ev_in, user));
+    MRHS_CUDA(cudaStreamWaitEvent(mg->own, mg->ev_in, 0));
+    const bool conv = mg_solve(*mg, static_cast<const double2 *>(b_dev), static_cast<double2 *>(x_dev), nrhs,
+                               tols.data(), rel_res_host, stats, mg->own, 0, nullptr);
+    MRHS_CUDA(cudaEventRecord(mg->ev_out, mg->own));
+    MRHS_CUDA(cudaStreamWaitEvent(user, mg->ev_out, 0));
+    MRHS_CUDA(cudaStreamSynchronize(mg->own));
+    if (stats) {
+        stats->t_fine = mg->t_fine;
+        stats->t_restrict = mg->t_restrict;
+        stats->t_prolong = mg->t_prolong;
+        stats->t_coarse = mg->t_coarse;
+    }
+    if (!conv) return api_record(MRHS_ERR_NOT_CONVERGED, "outer iteration cap reached before tol");
+    return ok();
+    API_CATCH
+}
+
+}  // extern "C"

@@ -29,6 +29,7 @@ MRHS_ERR_NOT_FOUND = -7
 MRHS_FP32 = 0
 MRHS_FP64 = 1
 MRHS_BF16 = 2
+MRHS_FP16 = 3
 
 MAX_LEVELS = 3
 
@@ -103,6 +104,7 @@ _D = C.c_double
 # name -> (restype, argtypes); restype None means a void function
 PROTOTYPES = {
     "mrhs_last_error": (C.c_char_p, []),
+    "mrhs_kernel_launch_count": (C.c_uint64, []),
     "mrhs_create_lattice": (_I, [C.POINTER(C.c_int), _I, _I, C.POINTER(_P)]),
     "mrhs_destroy_lattice": (None, [_P]),
     "mrhs_load_gauge": (_I, [_P, _P]),
@@ -174,6 +176,10 @@ def _stream(s):
     if isinstance(s, int):
         return s
     return s.cuda_stream
+
+
+def mrhs_kernel_launch_count() -> int:
+    return int(lib().mrhs_kernel_launch_count())
 
 
 # ------------------------------------------------------------------ lattice

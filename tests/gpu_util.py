@@ -43,3 +43,30 @@ def site_rel_err(a: np.ndarray, b: np.ndarray) -> float:
     num = np.sqrt(np.sum(np.abs(a - b) ** 2, axis=1))
     den = np.sqrt(np.sum(np.abs(b) ** 2, axis=1))
     return float(np.max(num / np.maximum(den, 1e-300)))
+
+
+def make_mg(lat, params: dict, init_vecs=None):
+    """mrhs_setup_mg with the defaults overridden by `params` (a dict of MgParams fields).
+
+    `init_vecs[l]` (optional) are host FP64 start vectors (V_l, dof_l, N_l); the
+    arrays must stay alive during the call."""
+    p = mrhs.mrhs_mg_default_params()
+    for k, v in params.items():
+        if k == "blocks":
+            for l, b in enumerate(v):
+                for mu in range(4):
+                    p.block[l][mu] = int(b[mu])
+        elif k == "nvec":
+            for l, nv in enumerate(v):
+                p.n_vec[l] = int(nv)
+        else:
+            setattr(p, k, v)
+    keep = []
+    if init_vecs is not None:
+        for l, a in enumerate(init_vecs):
+            a = np.ascontiguousarray(a, dtype=np.complex128)
+            keep.append(a)
+            p.init_vecs[l] = a.ctypes.data
+    mg = mrhs.mrhs_setup_mg(lat, p)
+    del keep
+    return mg
