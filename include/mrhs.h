@@ -141,6 +141,20 @@ mrhs_status mrhs_blas_lincomb(void *w_dev, const void *basis_dev, int k,
                               const void *coef_dev, double alpha, int64_t rows,
                               int nrhs, mrhs_precision prec, void *stream);
 
+/* The paper has no counterpart to this entry point.  It computes exactly
+ * what mrhs_blas_multi_dot computes, for callers that must not allocate
+ * device memory while they run (code being recorded into a CUDA graph,
+ * hosts that reserve all device memory up front, programs whose memory
+ * belongs to another allocator): it never calls cudaMalloc or cudaFree.
+ * Its reduction scratch is a statically allocated 4 MiB device array shared
+ * by all calls; nrhs is limited to 1..64 (MRHS_ERR_INVALID beyond).  The
+ * first call on a device looks the array up (cudaGetSymbolAddress) with that
+ * device current: make it before any stream capture.  Calls that overlap on
+ * the GPU race on the shared scratch; order them on one stream. */
+mrhs_status mrhs_blas_multi_dot_noalloc(const void *basis_dev, int k, const void *w_dev,
+                                        int64_t rows, int nrhs, mrhs_precision prec,
+                                        void *out_dev, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Multigrid hierarchy                                                  */
 /* ------------------------------------------------------------------ */

@@ -434,6 +434,27 @@ void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, in
     MRHS_LAUNCHED("k_norm_fixup");
 }
 
+void multi_dot_fixed_scratch(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w, int64_t rows,
+                             int n, double2 *out, double2 *partials, unsigned int *counter, int max_blocks,
+                             cudaStream_t s) {
+    check_n(n);
+    RedGeom g = red_geom(rows, n);
+    g.blocks = std::min(g.blocks, max_blocks);
+    for (int j0 = 0; j0 < k; j0 += KCHUNK) {
+        const int kk = std::min(KCHUNK, k - j0);
+        const size_t smem = sizeof(double2) * (size_t)g.rpb * kk * n;
+        if (p == MRHS_FP32)
+            k_multi_dot<float><<<g.blocks, g.threads, smem, s>>>(
+                static_cast<const float *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const float *>(w), rows, n,
+                g.rpb, partials, counter, out + (int64_t)j0 * n, 0);
+        else
+            k_multi_dot<double><<<g.blocks, g.threads, smem, s>>>(
+                static_cast<const double *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const double *>(w), rows,
+                n, g.rpb, partials, counter, out + (int64_t)j0 * n, 0);
+        MRHS_LAUNCHED("k_multi_dot");
+    }
+}
+
 void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s) {
     check_n(n);
     const RedGeom g = red_geom(rows, n);

@@ -54,6 +54,12 @@ constexpr int KCHUNK = 8;  // basis vectors per multi-dot pass
 void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w,
                int64_t rows, int n, double2 *out, Scratch &sc, cudaStream_t s, bool accumulate = false);
 void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s);
+// multi_dot with caller-provided reduction scratch: `partials` holds at least
+// max_blocks * KCHUNK * n double2, `counter` must be zero on entry (the kernel
+// leaves it zero); the grid is capped at max_blocks.
+void multi_dot_fixed_scratch(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w, int64_t rows,
+                             int n, double2 *out, double2 *partials, unsigned int *counter, int max_blocks,
+                             cudaStream_t s);
 // w += alpha * sum_j coef[j][r] basis_j ; basis may be FP32 while w is FP64.
 // If norm_out != nullptr, also writes ||w_new||^2 per RHS (needs sc).
 void lincomb(mrhs_precision pw, void *w, mrhs_precision pb, const void *basis, int64_t stride, int k,

@@ -113,6 +113,7 @@ PROTOTYPES = {
     "mrhs_apply_D": (_I, [_P, _P, _P, _I, _I, _P]),
     "mrhs_residual_D": (_I, [_P, _P, _P, _P, _I, _I, _P]),
     "mrhs_blas_multi_dot": (_I, [_P, _I, _P, _I64, _I, _I, _P, _P]),
+    "mrhs_blas_multi_dot_noalloc": (_I, [_P, _I, _P, _I64, _I, _I, _P, _P]),
     "mrhs_blas_norm2": (_I, [_P, _I64, _I, _I, _P, _P]),
     "mrhs_blas_lincomb": (_I, [_P, _P, _I, _P, _D, _I64, _I, _I, _P]),
     "mrhs_mg_default_params": (None, [C.POINTER(MgParams)]),
@@ -219,6 +220,11 @@ def mrhs_residual_D(lat, in_dev, y_dev, out_dev, nrhs, prec, stream=None):
 def mrhs_blas_multi_dot(basis_dev, k, w_dev, rows, nrhs, prec, out_dev, stream=None):
     _check(lib().mrhs_blas_multi_dot(_ptr(basis_dev), int(k), _ptr(w_dev), int(rows), int(nrhs), int(prec),
                                      _ptr(out_dev), _stream(stream)))
+
+
+def mrhs_blas_multi_dot_noalloc(basis_dev, k, w_dev, rows, nrhs, prec, out_dev, stream=None):
+    _check(lib().mrhs_blas_multi_dot_noalloc(_ptr(basis_dev), int(k), _ptr(w_dev), int(rows), int(nrhs), int(prec),
+                                             _ptr(out_dev), _stream(stream)))
 
 
 def mrhs_blas_norm2(w_dev, rows, nrhs, prec, out_dev, stream=None):
