@@ -61,8 +61,11 @@ static RedGeom red_geom(int64_t rows, int n) {
     RedGeom r;
     r.rpb = n >= 256 ? 1 : 256 / n;
     r.threads = n * r.rpb;
-    const int64_t need = (rows + r.rpb - 1) / r.rpb;
-    const int64_t cap = (int64_t)current_sms() * 8;
+    // at least 32 rows per thread, at most 4 blocks per SM: enough loads in
+    // flight for HBM on large fields, few partials for the last block to sum
+    // on the small coarse-level fields
+    const int64_t need = (rows + 32 * r.rpb - 1) / (32 * r.rpb);
+    const int64_t cap = (int64_t)current_sms() * 4;
     r.blocks = (int)std::max<int64_t>(1, std::min(need, cap));
     return r;
 }
@@ -114,12 +117,25 @@ __device__ void block_finish(double2 *smem, const double2 *vals, int cols, int n
     if (!last) return;
     __threadfence();
     for (int o = tid; o < nout; o += blockDim.x) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int b = 0; b < (int)gridDim.x; ++b) {
-            const double2 v = __ldcg(&partials[(int64_t)b * nout + o]);
-            s.x += v.x;
-            s.y += v.y;
+        // fixed order: four interleaved partial sums over the blocks, then combined
+        double2 q[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                        make_double2(0.0, 0.0)};
+        const int nb = (int)gridDim.x;
+        int b = 0;
+        for (; b + 4 <= nb; b += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double2 v = __ldcg(&partials[(int64_t)(b + u) * nout + o]);
+                q[u].x += v.x;
+                q[u].y += v.y;
+            }
         }
+        for (; b < nb; ++b) {
+            const double2 v = __ldcg(&partials[(int64_t)b * nout + o]);
+            q[0].x += v.x;
+            q[0].y += v.y;
+        }
+        double2 s = make_double2((q[0].x + q[1].x) + (q[2].x + q[3].x), (q[0].y + q[1].y) + (q[2].y + q[3].y));
         if (real_only) {
             out_real[o] = s.x;
         } else if (real_tail && o >= (cols - 1) * n) {
@@ -223,14 +239,19 @@ __global__ void k_lincomb(TW *__restrict__ w, const TB *__restrict__ basis, int6
     }
 }
 
+// dst = src / sqrt(nrm2[col]); one RHS column per thread, factor computed once
 template <typename T>
-__global__ void k_scale_inv_sqrt(T *dst, const T *src, const double *nrm2, int64_t count, int n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const double v = nrm2[i % n];
+__global__ void k_scale_inv_sqrt(T *dst, const T *src, const double *nrm2, int64_t rows, int n, int rpb) {
+    const int col = threadIdx.x % n;
+    const int rsub = threadIdx.x / n;
+    const double v = nrm2[col];
     const T f = v > 0.0 ? (T)(1.0 / sqrt(v)) : (T)0;
-    cplx<T> x = ldv(src, i);
-    stv(dst, i, cplx<T>{x.re * f, x.im * f});
+    const int64_t step = (int64_t)gridDim.x * rpb;
+    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
+        const int64_t e = row * n + col;
+        const cplx<T> x = ldv(src, e);
+        stv(dst, e, cplx<T>{x.re * f, x.im * f});
+    }
 }
 
 template <typename TD, typename TS>
@@ -332,15 +353,21 @@ __global__ void k_lincomb_scale(T *__restrict__ w, const T *__restrict__ basis, 
 
 // columns whose new basis vector is not unit length (cancellation in the
 // Pythagorean norm) are rescaled; the Givens step applies the same factor to beta
+// columns whose new basis vector is not unit length (cancellation in the
+// Pythagorean norm) are rescaled; the Givens step applies the same factor to
+// beta.  One column per thread: unflagged columns return without touching data.
 template <typename T>
-__global__ void k_norm_fixup(T *__restrict__ w, const double *__restrict__ nn, int64_t count, int n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
-    const double f = nn[i % n];
-    if (f > 0.0 && fabs(f - 1.0) > 1e-2) {
-        const T s = (T)(1.0 / sqrt(f));
-        cplx<T> x = ldv(w, i);
-        stv(w, i, cplx<T>{x.re * s, x.im * s});
+__global__ void k_norm_fixup(T *__restrict__ w, const double *__restrict__ nn, int64_t rows, int n, int rpb) {
+    const int col = threadIdx.x % n;
+    const int rsub = threadIdx.x / n;
+    const double f = nn[col];
+    if (!(f > 0.0 && fabs(f - 1.0) > 1e-2)) return;
+    const T sc = (T)(1.0 / sqrt(f));
+    const int64_t step = (int64_t)gridDim.x * rpb;
+    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
+        const int64_t e = row * n + col;
+        const cplx<T> x = ldv(w, e);
+        stv(w, e, cplx<T>{x.re * sc, x.im * sc});
     }
 }
 
@@ -426,11 +453,10 @@ void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, in
         MRHS_LAUNCHED("k_lincomb_scale");
         break;
     }
-    const int64_t count = rows * n;
     if (f32)
-        k_norm_fixup<float><<<ceil_div(count, 256), 256, 0, s>>>(static_cast<float *>(w), nn, count, n);
+        k_norm_fixup<float><<<g.blocks, g.threads, 0, s>>>(static_cast<float *>(w), nn, rows, n, g.rpb);
     else
-        k_norm_fixup<double><<<ceil_div(count, 256), 256, 0, s>>>(static_cast<double *>(w), nn, count, n);
+        k_norm_fixup<double><<<g.blocks, g.threads, 0, s>>>(static_cast<double *>(w), nn, rows, n, g.rpb);
     MRHS_LAUNCHED("k_norm_fixup");
 }
 
@@ -511,11 +537,14 @@ void lincomb(mrhs_precision pw, void *w, mrhs_precision pb, const void *basis, i
 
 void scale_inv_sqrt(mrhs_precision p, void *dst, const void *src, const double *nrm2, int64_t rows, int n,
                     cudaStream_t s) {
-    const int64_t count = rows * n;
+    check_n(n);
+    const RedGeom g = red_geom(rows, n);
     if (p == MRHS_FP32)
-        k_scale_inv_sqrt<float><<<ceil_div(count, 256), 256, 0, s>>>(static_cast<float *>(dst), static_cast<const float *>(src), nrm2, count, n);
+        k_scale_inv_sqrt<float><<<g.blocks, g.threads, 0, s>>>(static_cast<float *>(dst),
+                                                              static_cast<const float *>(src), nrm2, rows, n, g.rpb);
     else
-        k_scale_inv_sqrt<double><<<ceil_div(count, 256), 256, 0, s>>>(static_cast<double *>(dst), static_cast<const double *>(src), nrm2, count, n);
+        k_scale_inv_sqrt<double><<<g.blocks, g.threads, 0, s>>>(static_cast<double *>(dst),
+                                                               static_cast<const double *>(src), nrm2, rows, n, g.rpb);
     MRHS_LAUNCHED("k_scale_inv_sqrt");
 }
 

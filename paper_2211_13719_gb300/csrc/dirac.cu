@@ -255,6 +255,226 @@ __global__ void __launch_bounds__(128) k_dslash(const cplx<Real> *__restrict__ U
     }
 }
 
+// ------------------------------------------------- paired-FP32 variant
+// Two RHS per thread held as (Re r0, Re r1) / (Im r0, Im r1) pairs so that
+// every multiply-add runs as one paired FP32 instruction (FFMA2 / FADD2 /
+// FMUL2 on sm_100 and later); 32-bit index arithmetic.  Used for FP32 fields
+// with an even RHS count; same operator and reconstruction rules as above.
+struct P2 {
+    float2 re, im;
+};
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ P2 p2add(P2 a, P2 b) { return {__fadd2_rn(a.re, b.re), __fadd2_rn(a.im, b.im)}; }
+template <int F> __device__ __forceinline__ P2 p2f(P2 a) {
+    if constexpr (F == FP) return a;
+    else if constexpr (F == FM) return {neg2(a.re), neg2(a.im)};
+    else if constexpr (F == FI) return {neg2(a.im), a.re};
+    else return {a.im, neg2(a.re)};
+}
+__device__ __forceinline__ P2 ld_p2(const float2 *__restrict__ p, int64_t off) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p + off));
+    return {make_float2(v.x, v.z), make_float2(v.y, v.w)};
+}
+// streaming store: the result is not read again by this kernel, keep it from
+// displacing neighbour spinors in L2
+__device__ __forceinline__ void st_p2(float2 *p, int64_t off, P2 v) {
+    __stcs(reinterpret_cast<float4 *>(p + off), make_float4(v.re.x, v.im.x, v.re.y, v.im.y));
+}
+// acc += u * h  (u one complex number shared by both RHS)
+__device__ __forceinline__ void p2mac(P2 &acc, float2 u, P2 h) {
+    const float2 ur = make_float2(u.x, u.x), ui = make_float2(u.y, u.y), nui = make_float2(-u.y, -u.y);
+    acc.re = __ffma2_rn(ur, h.re, acc.re);
+    acc.re = __ffma2_rn(nui, h.im, acc.re);
+    acc.im = __ffma2_rn(ur, h.im, acc.im);
+    acc.im = __ffma2_rn(ui, h.re, acc.im);
+}
+// acc += conj(u) * h
+__device__ __forceinline__ void p2mac_conj(P2 &acc, float2 u, P2 h) {
+    const float2 ur = make_float2(u.x, u.x), ui = make_float2(u.y, u.y), nui = make_float2(-u.y, -u.y);
+    acc.re = __ffma2_rn(ur, h.re, acc.re);
+    acc.re = __ffma2_rn(ui, h.im, acc.re);
+    acc.im = __ffma2_rn(ur, h.im, acc.im);
+    acc.im = __ffma2_rn(nui, h.re, acc.im);
+}
+
+// Sites are visited brick by brick: a brick is Lx x Ly x bz x Lt, traversed
+// with x, y, z fastest and t slowest, so the +-t neighbour of a site is reused
+// Lx*Ly*bz sites later (instead of Lx*Ly*Lz) while it still sits in L2.
+struct KArgs32 {
+    int L[4];
+    int V;
+    int n, G;
+    int stride[4];
+    int tb;
+    int bz;          // brick extent in z
+    int brick;       // sites per brick: Lx * Ly * bz * Lt
+    int slab;        // Lx * Ly * bz
+};
+
+template <int MU, bool FWD>
+__device__ __forceinline__ void hop_x2(P2 (&acc)[12], const float2 *__restrict__ U, const float2 *__restrict__ in,
+                                      const KArgs32 &a, int nb, int link_site, bool flip, int r0) {
+    using P = Proj<MU>;
+    constexpr int F0 = FWD ? P::F0 : neg_f<P::F0>::v;
+    constexpr int F1 = FWD ? P::F1 : neg_f<P::F1>::v;
+    constexpr int G2 = FWD ? P::G2 : neg_f<P::G2>::v;
+    constexpr int G3 = FWD ? P::G3 : neg_f<P::G3>::v;
+    const int64_t base = (int64_t)nb * 12 * a.n + r0;
+    P2 h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const P2 p0 = ld_p2(in, base + (int64_t)(0 * 3 + c) * a.n);
+        const P2 p1 = ld_p2(in, base + (int64_t)(1 * 3 + c) * a.n);
+        const P2 pa = ld_p2(in, base + (int64_t)(P::P0 * 3 + c) * a.n);
+        const P2 pb = ld_p2(in, base + (int64_t)(P::P1 * 3 + c) * a.n);
+        h0[c] = p2add(p0, p2f<F0>(pa));
+        h1[c] = p2add(p1, p2f<F1>(pb));
+    }
+    if (flip) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            h0[c] = p2f<FM>(h0[c]);
+            h1[c] = p2f<FM>(h1[c]);
+        }
+    }
+    const int V = a.V;
+#pragma unroll
+    for (int row = 0; row < 3; ++row) {
+        P2 s0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, s1 = s0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (FWD) {
+                const float2 u = __ldg(U + (int64_t)(MU * 9 + row * 3 + b) * V + link_site);
+                p2mac(s0, u, h0[b]);
+                p2mac(s1, u, h1[b]);
+            } else {
+                const float2 u = __ldg(U + (int64_t)(MU * 9 + b * 3 + row) * V + link_site);
+                p2mac_conj(s0, u, h0[b]);
+                p2mac_conj(s1, u, h1[b]);
+            }
+        }
+        acc[0 * 3 + row] = p2add(acc[0 * 3 + row], s0);
+        acc[1 * 3 + row] = p2add(acc[1 * 3 + row], s1);
+        acc[2 * 3 + row] = p2add(acc[2 * 3 + row], p2f<G2>(P::Q2 == 0 ? s0 : s1));
+        acc[3 * 3 + row] = p2add(acc[3 * 3 + row], p2f<G3>(P::Q3 == 0 ? s0 : s1));
+    }
+}
+
+template <int MU>
+__device__ __forceinline__ void hop_pair_x2(P2 (&acc)[12], const float2 *__restrict__ U,
+                                           const float2 *__restrict__ in, const KArgs32 &a, int site,
+                                           const int c[4], int r0) {
+    const int L = a.L[MU];
+    const int st = a.stride[MU];
+    const bool wrapF = (c[MU] == L - 1), wrapB = (c[MU] == 0);
+    const int sf = wrapF ? site - st * (L - 1) : site + st;
+    const int sb = wrapB ? site + st * (L - 1) : site - st;
+    const bool flipF = MU == 3 && wrapF && a.tb < 0;
+    const bool flipB = MU == 3 && wrapB && a.tb < 0;
+    hop_x2<MU, true>(acc, U, in, a, sf, site, flipF, r0);
+    hop_x2<MU, false>(acc, U, in, a, sb, sb, flipB, r0);
+}
+
+template <bool RESID>
+__global__ void __launch_bounds__(128, 4) k_dslash_x2(const float2 *__restrict__ U, const float2 *__restrict__ C,
+                                                       const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                       const float2 *__restrict__ y, KArgs32 a) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const int visit = item / a.G;
+    if (visit >= a.V) return;
+    const int r0 = (item - visit * a.G) * 2;
+    int c[4];
+    {
+        const int b = visit / a.brick;
+        int q = visit - b * a.brick;
+        c[3] = q / a.slab;
+        q -= c[3] * a.slab;
+        c[0] = q % a.L[0];
+        q /= a.L[0];
+        c[1] = q % a.L[1];
+        c[2] = b * a.bz + q / a.L[1];
+    }
+    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+    P2 acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    hop_pair_x2<0>(acc, U, in, a, site, c, r0);
+    hop_pair_x2<1>(acc, U, in, a, site, c, r0);
+    hop_pair_x2<2>(acc, U, in, a, site, c, r0);
+    hop_pair_x2<3>(acc, U, in, a, site, c, r0);
+
+    const int V = a.V;
+    const int64_t base = (int64_t)site * 12 * a.n + r0;
+    const float2 mhalf = make_float2(-0.5f, -0.5f);
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        P2 v[6], o[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v[i] = ld_p2(in, base + (int64_t)(6 * chi + i) * a.n);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float2 d = __ldg(C + (int64_t)(chi * 18 + q) * V + site);
+            const float2 d0 = make_float2(d.x, d.x), d1 = make_float2(d.y, d.y);
+            o[2 * q] = {__fmul2_rn(d0, v[2 * q].re), __fmul2_rn(d0, v[2 * q].im)};
+            o[2 * q + 1] = {__fmul2_rn(d1, v[2 * q + 1].re), __fmul2_rn(d1, v[2 * q + 1].im)};
+        }
+        int q = 3;
+#pragma unroll
+        for (int i = 1; i < 6; ++i) {
+#pragma unroll
+            for (int j = 0; j < i; ++j, ++q) {
+                const float2 l = __ldg(C + (int64_t)(chi * 18 + q) * V + site);
+                p2mac(o[i], l, v[j]);
+                p2mac_conj(o[j], l, v[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const P2 acc_i = acc[6 * chi + i];
+            P2 res = {__ffma2_rn(mhalf, acc_i.re, o[i].re), __ffma2_rn(mhalf, acc_i.im, o[i].im)};
+            const int64_t off = base + (int64_t)(6 * chi + i) * a.n;
+            if constexpr (RESID) {
+                const P2 yy = ld_p2(y, off);
+                res = {__fadd2_rn(yy.re, neg2(res.re)), __fadd2_rn(yy.im, neg2(res.im))};
+            }
+            st_p2(out, off, res);
+        }
+    }
+}
+
+static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n,
+                             cudaStream_t s) {
+    if (n % 2 || lat.g.V * 12LL * n >= (1LL << 31) || lat.g.V * (int64_t)(n / 2) >= (1LL << 31)) return false;
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    if (!al(in) || !al(out) || (y && !al(y))) return false;
+    KArgs32 a;
+    for (int mu = 0; mu < 4; ++mu) a.L[mu] = lat.g.L[mu];
+    a.V = (int)lat.g.V;
+    a.n = n;
+    a.G = n / 2;
+    a.stride[0] = 1;
+    a.stride[1] = a.L[0];
+    a.stride[2] = a.L[0] * a.L[1];
+    a.stride[3] = a.L[0] * a.L[1] * a.L[2];
+    a.tb = lat.g.tb;
+    a.bz = (a.L[2] % 8 == 0) ? 8 : (a.L[2] % 4 == 0 ? 4 : (a.L[2] % 2 == 0 ? 2 : 1));
+    a.slab = a.L[0] * a.L[1] * a.bz;
+    a.brick = a.slab * a.L[3];
+    const int64_t items = (int64_t)a.V * a.G;
+    const int threads = 128;
+    const unsigned blocks = (unsigned)((items + threads - 1) / threads);
+    const float2 *U = lat.U32.as<float2>();
+    const float2 *C = lat.C32.as<float2>();
+    if (y)
+        k_dslash_x2<true><<<blocks, threads, 0, s>>>(U, C, static_cast<const float2 *>(in), static_cast<float2 *>(out),
+                                                     static_cast<const float2 *>(y), a);
+    else
+        k_dslash_x2<false><<<blocks, threads, 0, s>>>(U, C, static_cast<const float2 *>(in),
+                                                      static_cast<float2 *>(out), nullptr, a);
+    MRHS_LAUNCHED("k_dslash_x2");
+    return true;
+}
+
 template <typename Real, typename TIn, int R, bool RESID, bool GENERAL>
 static void launch_dslash(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n,
                           cudaStream_t s, const HopMask &mask) {
@@ -287,6 +507,7 @@ void dslash(const mrhs_lattice &lat, mrhs_precision compute, mrhs_precision in_p
     if (compute == MRHS_FP32) {
         if (in_prec != MRHS_FP32) fail(MRHS_ERR_INVALID, "FP32 operator needs FP32 input");
         const bool r2 = (n % 2) == 0;
+        if (!general && launch_dslash_x2(lat, in, out, y, n, s)) return;
         if (general) {
             if (r2) launch_dslash<float, float, 2, false, true>(lat, in, out, y, n, s, m);
             else launch_dslash<float, float, 1, false, true>(lat, in, out, y, n, s, m);

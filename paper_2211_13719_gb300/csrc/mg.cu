@@ -55,119 +55,184 @@ __device__ __forceinline__ cplx<float> ld2(const float2 *p, int64_t i) {
 }
 
 // ---------------------------------------------------------------- restrict
-// One block per coarse site; the block's threads own the 2N x n outputs.
-// Per round, SB fine sites of the aggregate are staged in shared memory
-// (their prolongator rows and field rows, both contiguous in global memory).
-constexpr int RESTRICT_MAXO = 16;
+// One block per coarse site (aggregate).  Each thread owns KG consecutive
+// basis vectors k of one chirality and one RHS column r (up to MAXI such
+// items); per round PSB fine sites of the aggregate are staged in shared
+// memory (their prolongator rows [dof][N] and field rows [dof][n], both
+// contiguous in global memory), and for every staged site and component of
+// the item's chirality the thread loads one field value and KG prolongator
+// values (shared-memory broadcasts) for KG complex multiply-adds.
+constexpr int RESTRICT_MAXI = 4;
 
-__global__ void k_restrict(const float2 *__restrict__ fine, const float2 *__restrict__ P, float2 *__restrict__ coarse,
-                           int64_t ostride, AggGeom a, int SB) {
+template <int KG>
+__global__ void __launch_bounds__(1024) k_restrict(const float2 *__restrict__ fine, const float2 *__restrict__ P,
+                                                  float2 *__restrict__ coarse, int64_t ostride, AggGeom a, int PSB) {
     extern __shared__ float2 sm[];
-    float2 *Ps = sm;
-    float2 *Fs = sm + (size_t)SB * a.dof * a.N;
+    float2 *Ps = sm;                                   // [PSB][dof][N]
+    float2 *Fs = sm + (size_t)PSB * a.dof * a.N;       // [PSB][dof][n]
     const int64_t xc = blockIdx.x;
-    const int nc = 2 * a.N, half = a.dof / 2;
-    const int nout = nc * a.n;
+    const int half = a.dof / 2;
+    const int kgroups = a.N / KG;
+    const int items = 2 * kgroups * a.n;               // (chi, kgroup, r)
     const int tid = threadIdx.x, T = blockDim.x;
-    cplx<float> acc[RESTRICT_MAXO];
+    cplx<float> acc[RESTRICT_MAXI][KG];
 #pragma unroll
-    for (int j = 0; j < RESTRICT_MAXO; ++j) acc[j] = {0.f, 0.f};
+    for (int i = 0; i < RESTRICT_MAXI; ++i)
+#pragma unroll
+        for (int j = 0; j < KG; ++j) acc[i][j] = {0.f, 0.f};
     const int pw = a.dof * a.N, fw = a.dof * a.n;
-    for (int64_t i0 = 0; i0 < a.asize; i0 += SB) {
-        const int nsb = (int)(a.asize - i0 < SB ? a.asize - i0 : SB);
+    for (int64_t i0 = 0; i0 < a.asize; i0 += PSB) {
+        const int nsb = (int)(a.asize - i0 < PSB ? a.asize - i0 : PSB);
         __syncthreads();
         for (int e = tid; e < nsb * pw; e += T) {
             const int sb = e / pw;
-            const int64_t x = agg_site(a, xc, i0 + sb);
-            Ps[e] = P[x * pw + (e - sb * pw)];
+            Ps[e] = P[agg_site(a, xc, i0 + sb) * pw + (e - sb * pw)];
         }
         for (int e = tid; e < nsb * fw; e += T) {
             const int sb = e / fw;
-            const int64_t x = agg_site(a, xc, i0 + sb);
-            Fs[e] = fine[x * fw + (e - sb * fw)];
+            Fs[e] = fine[agg_site(a, xc, i0 + sb) * fw + (e - sb * fw)];
         }
         __syncthreads();
 #pragma unroll
-        for (int j = 0; j < RESTRICT_MAXO; ++j) {
-            const int o = tid + j * T;
-            if (o < nout) {
-                const int K = o / a.n, r = o - K * a.n;
-                const int chi = K / a.N, k = K - chi * a.N;
-                cplx<float> s = acc[j];
+        for (int it = 0; it < RESTRICT_MAXI; ++it) {
+            const int item = tid + it * T;
+            if (item < items) {
+                const int r = item % a.n;
+                const int q = item / a.n;
+                const int chi = q / kgroups, k0 = (q - chi * kgroups) * KG;
                 for (int sb = 0; sb < nsb; ++sb) {
-                    const float2 *pp = Ps + (size_t)(sb * a.dof + chi * half) * a.N + k;
+                    const float2 *pp = Ps + (size_t)(sb * a.dof + chi * half) * a.N + k0;
                     const float2 *ff = Fs + (size_t)(sb * a.dof + chi * half) * a.n + r;
-                    for (int d = 0; d < half; ++d) cmac_conj(s, ld2(pp, (int64_t)d * a.N), ld2(ff, (int64_t)d * a.n));
+                    for (int d = 0; d < half; ++d) {
+                        const cplx<float> f = ld2(ff, (int64_t)d * a.n);
+#pragma unroll
+                        for (int j = 0; j < KG; ++j) cmac_conj(acc[it][j], ld2(pp, (int64_t)d * a.N + j), f);
+                    }
                 }
-                acc[j] = s;
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < RESTRICT_MAXO; ++j) {
-        const int o = tid + j * T;
-        if (o < nout) coarse[xc * ostride + o] = make_float2(acc[j].re, acc[j].im);
+    for (int it = 0; it < RESTRICT_MAXI; ++it) {
+        const int item = tid + it * T;
+        if (item < items) {
+            const int r = item % a.n;
+            const int q = item / a.n;
+            const int chi = q / kgroups, k0 = (q - chi * kgroups) * KG;
+#pragma unroll
+            for (int j = 0; j < KG; ++j)
+                coarse[xc * ostride + (int64_t)(chi * a.N + k0 + j) * a.n + r] = make_float2(acc[it][j].re, acc[it][j].im);
+        }
     }
+}
+
+template <int KG>
+static void launch_restrict(const AggGeom &a, int64_t Vc, const float2 *fine, const float2 *P, float2 *coarse,
+                            int64_t ostride, cudaStream_t s) {
+    const int items = 2 * (a.N / KG) * a.n;
+    int T = std::min(1024, std::max(64, ((items + RESTRICT_MAXI - 1) / RESTRICT_MAXI + 31) / 32 * 32));
+    if (T * RESTRICT_MAXI < items) fail(MRHS_ERR_INVALID, "restrict: nc * nrhs too large");
+    const size_t per_site = sizeof(float2) * (size_t)a.dof * (a.N + a.n);
+    int PSB = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_site));
+    PSB = (int)std::min<int64_t>(PSB, a.asize);
+    const size_t smem = per_site * PSB;
+    if (smem > 200 * 1024) fail(MRHS_ERR_INVALID, "restrict: per-site data too large for shared memory");
+    static bool attr = false;
+    if (!attr) {
+        MRHS_CUDA(cudaFuncSetAttribute(k_restrict<KG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    k_restrict<KG><<<(unsigned)Vc, T, smem, s>>>(fine, P, coarse, ostride, a, PSB);
+    MRHS_LAUNCHED("k_restrict");
 }
 
 void restrict_fields(const Level &f, const Level &c, const float2 *fine, float2 *coarse, int n, int64_t ostride,
                      cudaStream_t s) {
     const AggGeom a = agg_geom(f, c, n);
-    const int nout = 2 * f.N * n;
-    int T = ((nout + RESTRICT_MAXO - 1) / RESTRICT_MAXO + 31) / 32 * 32;
-    T = std::max(64, std::min(1024, T));
-    if ((int64_t)T * RESTRICT_MAXO < nout) fail(MRHS_ERR_INVALID, "restrict: nc * nrhs too large");
-    const size_t per_site = sizeof(float2) * (size_t)f.dof * (f.N + n);
-    int SB = (int)std::max<size_t>(1, std::min<size_t>(8, (96 * 1024) / per_site));
-    SB = (int)std::min<int64_t>(SB, f.asize);
-    const size_t smem = per_site * SB;
-    if (smem > 200 * 1024) fail(MRHS_ERR_INVALID, "restrict: per-site data too large for shared memory");
-    static bool attr = false;
-    if (!attr) {
-        MRHS_CUDA(cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
-    }
-    k_restrict<<<(unsigned)c.V, T, smem, s>>>(fine, f.P32.as<float2>(), coarse, ostride, a, SB);
-    MRHS_LAUNCHED("k_restrict");
+    const float2 *P = f.P32.as<float2>();
+    if (f.N % 4 == 0) launch_restrict<4>(a, c.V, fine, P, coarse, ostride, s);
+    else if (f.N % 2 == 0) launch_restrict<2>(a, c.V, fine, P, coarse, ostride, s);
+    else launch_restrict<1>(a, c.V, fine, P, coarse, ostride, s);
 }
 
 // ----------------------------------------------------------------- prolong
-// One thread per (fine site, RHS): psi[x][d][r] = sum_k P[x][d][k] c[xc][chi(d) N + k][r].
-__global__ void k_prolong(const float2 *__restrict__ coarse, const float2 *__restrict__ P, float2 *__restrict__ fine,
-                          AggGeom a, int64_t V) {
-    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t x = item / a.n;
-    if (x >= V) return;
-    const int r = (int)(item - x * a.n);
-    int c[4];
-    site_to_coords(x, a.L, c);
-    int cc[4];
-    for (int mu = 0; mu < 4; ++mu) cc[mu] = c[mu] / a.B[mu];
-    const int64_t xc = coords_to_site(cc, a.Lc);
-    const int nc = 2 * a.N, half = a.dof / 2;
-    const float2 *Px = P + x * a.dof * a.N;
-    for (int chi = 0; chi < 2; ++chi) {
-        cplx<float> cv[32];
+// One block per aggregate: the coarse block c[xc] ([nc][n]) is staged in
+// shared memory once, the prolongator rows of PSB fine sites per round.  A
+// thread item is (site, DG consecutive components of one chirality, RHS r):
+// per basis vector k one coarse value and DG prolongator values (broadcast)
+// feed DG complex multiply-adds; the DG outputs are stored contiguously in r.
+template <int DG>
+__global__ void __launch_bounds__(256) k_prolong(const float2 *__restrict__ coarse, const float2 *__restrict__ P,
+                                                 float2 *__restrict__ fine, AggGeom a, int PSB) {
+    extern __shared__ float2 sm[];
+    const int nc = 2 * a.N;
+    float2 *Cs = sm;                          // [nc][n]
+    float2 *Ps = sm + (size_t)nc * a.n;       // [PSB][dof][N]
+    const int64_t xc = blockIdx.x;
+    const int half = a.dof / 2;
+    const int tid = threadIdx.x, T = blockDim.x;
+    for (int e = tid; e < nc * a.n; e += T) Cs[e] = coarse[xc * nc * a.n + e];
+    const int dgroups = a.dof / DG;
+    const int pw = a.dof * a.N;
+    for (int64_t i0 = 0; i0 < a.asize; i0 += PSB) {
+        const int nsb = (int)(a.asize - i0 < PSB ? a.asize - i0 : PSB);
+        __syncthreads();
+        for (int e = tid; e < nsb * pw; e += T) {
+            const int sb = e / pw;
+            Ps[e] = P[agg_site(a, xc, i0 + sb) * pw + (e - sb * pw)];
+        }
+        __syncthreads();
+        const int items = nsb * dgroups * a.n;
+        for (int item = tid; item < items; item += T) {
+            const int r = item % a.n;
+            const int q = item / a.n;
+            const int sb = q / dgroups, g = q - sb * dgroups;
+            const int d0 = g * DG;
+            const int chi = d0 / half;
+            cplx<float> acc[DG];
 #pragma unroll
-        for (int k = 0; k < 32; ++k)
-            cv[k] = k < a.N ? ld2(coarse, (xc * nc + chi * a.N + k) * a.n + r) : cplx<float>{0.f, 0.f};
-        for (int d = chi * half; d < chi * half + half; ++d) {
-            cplx<float> s = {0.f, 0.f};
-            const float2 *pr = Px + (int64_t)d * a.N;
+            for (int j = 0; j < DG; ++j) acc[j] = {0.f, 0.f};
+            const float2 *pp = Ps + (size_t)(sb * a.dof + d0) * a.N;
+            const float2 *cc = Cs + (size_t)(chi * a.N) * a.n + r;
+            for (int k = 0; k < a.N; ++k) {
+                const cplx<float> cv = ld2(cc, (int64_t)k * a.n);
 #pragma unroll
-            for (int k = 0; k < 32; ++k)
-                if (k < a.N) cmac(s, ld2(pr, k), cv[k]);
-            fine[(x * a.dof + d) * a.n + r] = make_float2(s.re, s.im);
+                for (int j = 0; j < DG; ++j) cmac(acc[j], ld2(pp, (int64_t)j * a.N + k), cv);
+            }
+            const int64_t x = agg_site(a, xc, i0 + sb);
+#pragma unroll
+            for (int j = 0; j < DG; ++j)
+                fine[(x * a.dof + d0 + j) * a.n + r] = make_float2(acc[j].re, acc[j].im);
         }
     }
 }
 
-void prolong_fields(const Level &f, const Level &c, const float2 *coarse, float2 *fine, int n, cudaStream_t s) {
-    if (f.N > 32) fail(MRHS_ERR_INVALID, "prolong: at most 32 null vectors");
-    const AggGeom a = agg_geom(f, c, n);
-    const int64_t items = f.V * n;
-    k_prolong<<<ceil_div(items, 128), 128, 0, s>>>(coarse, f.P32.as<float2>(), fine, a, f.V);
+template <int DG>
+static void launch_prolong(const AggGeom &a, int64_t Vc, const float2 *coarse, const float2 *P, float2 *fine,
+                           cudaStream_t s) {
+    const size_t cbytes = sizeof(float2) * (size_t)2 * a.N * a.n;
+    const size_t per_site = sizeof(float2) * (size_t)a.dof * a.N;
+    int PSB = (int)std::max<size_t>(1, std::min<size_t>(16, (64 * 1024) / per_site));
+    PSB = (int)std::min<int64_t>(PSB, a.asize);
+    const size_t smem = cbytes + per_site * PSB;
+    if (smem > 200 * 1024) fail(MRHS_ERR_INVALID, "prolong: coarse block too large for shared memory");
+    static bool attr = false;
+    if (!attr) {
+        MRHS_CUDA(cudaFuncSetAttribute(k_prolong<DG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    k_prolong<DG><<<(unsigned)Vc, 256, smem, s>>>(coarse, P, fine, a, PSB);
     MRHS_LAUNCHED("k_prolong");
+}
+
+void prolong_fields(const Level &f, const Level &c, const float2 *coarse, float2 *fine, int n, cudaStream_t s) {
+    const AggGeom a = agg_geom(f, c, n);
+    const int half = f.dof / 2;
+    const float2 *P = f.P32.as<float2>();
+    if (half % 4 == 0) launch_prolong<4>(a, c.V, coarse, P, fine, s);
+    else if (half % 3 == 0) launch_prolong<3>(a, c.V, coarse, P, fine, s);
+    else if (half % 2 == 0) launch_prolong<2>(a, c.V, coarse, P, fine, s);
+    else launch_prolong<1>(a, c.V, coarse, P, fine, s);
 }
 
 // ---------------------------------------------------- coarse stencil, FP32
