@@ -5,15 +5,18 @@ Workload (one step = one MRHS solve of the whole RHS block):
   24^3 x 64 lattice, antiperiodic t, U = exp(i 0.25 H) with seeded Gaussian
   traceless Hermitian H, c_sw = 1, mass below, three-level MG (4^4 then 2^4
   aggregates, 32 chirally split null vectors each), nRHS = 48 Gaussian
-  sources, outer FP64 FGMRES, FP32 inner FGMRES + V-cycle, BF16 tensor-core
-  coarse stencil, V-cycle replayed as a CUDA graph, tol 1e-10.
+  sources, outer FP64 FGMRES, FP32 inner FGMRES + V-cycle, FP16 tensor-core
+  coarse stencil and intergrid transfers, V-cycle replayed as a CUDA graph,
+  tol 1e-10.
 Setup (null vectors, Galerkin) runs before the timed region and is reported
 separately.  The line also carries the plain one-RHS-at-a-time solver (FP32
 coarse stencil on CUDA cores, no graphs) on the same GPU, the fine-stencil
-roofline, the end-to-end number with host buffers, and the oracle timed on the
-host cores as the CPU baseline.
+roofline, the end-to-end number with host buffers, a continuous-batching
+serving run (p50 / p99 latency), and the oracle timed on the host cores as
+the CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --case stencil|intergrid|blas   (small cases for ncu captures)
 """
 from __future__ import annotations
 
@@ -31,9 +34,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(dims=(24, 24, 24, 64), eps=0.25, gauge_seed=1301, source_seed=2301, mass=-0.1, csw=1.0,
+WORKLOAD = dict(dims=(24, 24, 24, 64), eps=0.25, gauge_seed=1301, source_seed=2301, mass=-0.13, csw=1.0,
                 nrhs=48, tol=1e-10, n_levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[32, 32])
-MG_PARAMS = dict(setup_sweeps=6, setup_m=8, smooth_m=4, coarse_m=16, coarse_cycles=2, inter_m=8, inner_m=8,
+MG_PARAMS = dict(setup_sweeps=6, setup_m=8, smooth_m=4, coarse_m=12, coarse_cycles=1, inter_m=3, inner_m=8,
                  inner_max_iters=200, inner_tol=1e-5, outer_m=4, max_outer_iters=30)
 WORKLOAD_NAME = ("wilson-clover MG solve 24^3x64 antiperiodic, U=exp(i0.25H), c_sw=1, 3 levels "
                  "(4^4, 2^4 aggregates, 32 null vectors), nRHS=48, tol 1e-10")
@@ -239,6 +242,66 @@ def gauge_field(w):
     return U
 
 
+SERVE_SMALL = dict(dims=(16, 16, 16, 32), gauge_seed=1402)
+
+
+def run_serving(mrhs, mg_big, w, saturated, args, torch, np):
+    """Poisson arrivals of 1..12-source requests, 50/50 over two resident
+    hierarchies (the 24^3x64 one and a 16^3x32 one of the same recipe), at
+    `serve_load` times the measured saturated solves/s; p50 / p99 latency."""
+    import synth
+    dims_s = SERVE_SMALL["dims"]
+    Us = synth.gauge_exp(dims_s, w["eps"], SERVE_SMALL["gauge_seed"])
+    lat_s = mrhs.mrhs_create_lattice(dims_s, -1, torch.cuda.current_device())
+    mrhs.mrhs_load_gauge(lat_s, Us)
+    mrhs.mrhs_build_clover(lat_s, w["mass"], w["csw"])
+    mg_s = mrhs.mrhs_setup_mg(lat_s, make_params(mrhs, w["nrhs"], mrhs.MRHS_FP16, 1))
+    srv = mrhs.mrhs_server_create(max_queue=4096, hbm_reserve_gb=2.0)
+    try:
+        cids = [mrhs.mrhs_server_add_config(srv, mg_big, w["nrhs"]),
+                mrhs.mrhs_server_add_config(srv, mg_s, w["nrhs"])]
+        vols = [volume(w["dims"]), volume(dims_s)]
+        rng = np.random.default_rng(3001)
+        # sources drawn once per config and reused (values do not affect the schedule)
+        pool = [synth.gaussian_field(vols[c], 12, 12, 2401 + c) for c in range(2)]
+        # offered load in requests/s: fraction of the RHS throughput, mean 6.5 RHS per request,
+        # the small config costs about its volume ratio of a big solve
+        mean_cost = 0.5 * (1.0 + vols[1] / vols[0]) * 6.5
+        rate = args.serve_load * saturated / mean_cost
+        reqs = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(args.serve_requests):
+            t_next += rng.exponential(1.0 / rate)
+            while time.perf_counter() < t_next:
+                time.sleep(0.0005)
+            c = int(rng.integers(0, 2))
+            nr = int(rng.integers(1, 13))
+            b = np.ascontiguousarray(pool[c][:, :, :nr])
+            x = np.zeros_like(b)
+            rid = mrhs.mrhs_submit(srv, cids[c], b, x, nr, w["tol"])
+            reqs.append((rid, c, nr, x))
+        mrhs.mrhs_server_drain(srv)
+        wall = time.perf_counter() - t0
+        lat, ok, solves = [], 0, 0
+        for rid, c, nr, x in reqs:
+            st, rs = mrhs.mrhs_poll(srv, rid)
+            lat.append(rs.latency_s)
+            if st == mrhs.MRHS_OK:
+                ok += 1
+                solves += nr
+        lat_ms = np.array(lat) * 1e3
+        return {"requests": len(reqs), "completed_ok": ok, "solves": solves, "wall_s": wall,
+                "solves_per_s": solves / wall, "offered_load": args.serve_load,
+                "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "configs": [w["dims"], dims_s], "slots_per_config": w["nrhs"],
+                "arrivals": "Poisson, seed 3001, 1..12 sources per request, 50/50 configs"}
+    finally:
+        mrhs.mrhs_server_destroy(srv)
+        mrhs.mrhs_destroy_mg(mg_s)
+        mrhs.mrhs_destroy_lattice(lat_s)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -266,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
     mrhs.mrhs_build_clover(lat, w["mass"], w["csw"])
     del U
     t0 = time.perf_counter()
-    mg = mrhs.mrhs_setup_mg(lat, make_params(mrhs, n, mrhs.MRHS_BF16, 1))
+    mg = mrhs.mrhs_setup_mg(lat, make_params(mrhs, n, mrhs.MRHS_FP16, 1))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
 
@@ -294,11 +357,13 @@ def run_ours(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev) as clk:
+        torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
         for _ in range(args.steps):
             stats.append(step())
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     launches = mrhs.mrhs_kernel_launch_count() - launches0
     t_dev = e0.elapsed_time(e1) * 1e-3
     if world > 1:
@@ -378,6 +443,9 @@ def run_ours(args, rank, world, local_rank):
                               "ratio_mixed_batched_over_plain": value / world / plain,
                               "desc": "same MG, nRHS=1, FP32 coarse stencil on CUDA cores, no CUDA graphs, FP64 outer"}
             mrhs.mrhs_destroy_mg(mgp)
+        # --- serving: continuous batching over two resident configurations
+        if args.serve_requests > 0:
+            extra["serving"] = run_serving(mrhs, mg, w, value / world, args, torch, np)
         # --- CPU baseline: the oracle on one host thread, bounded sample
         if not args.no_cpu:
             extra["cpu_baseline"] = oracle_in_subprocess(1, 0)
@@ -386,7 +454,7 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": "MG solves/s at 1e-10", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+bf16",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32+f16",
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "nrhs_per_gpu": n, "lattice": "x".join(map(str, dims)),
                        "mass": w["mass"], "csw": w["csw"], "parallelism": f"replicas x{world}",
@@ -396,6 +464,86 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     mrhs.mrhs_destroy_mg(mg)
     mrhs.mrhs_destroy_lattice(lat)
+
+
+# ------------------------------------------------------- profiling cases
+def run_case(name, reps):
+    """Small launches of one kernel family, for ncu captures (a few GB on the device).
+
+    stencil:   FP32 fine operator, 24^4 lattice, 48 RHS
+    intergrid: tensor-core restriction + prolongation, 16^4 lattice, 4^4 aggregates, 32 vectors, 48 RHS
+    blas:      the FP32 batched multi-dot and linear combination, 16^4 x 12 rows, 48 RHS, 4 vectors
+    Prints one JSON line with the CUDA-event time per launch."""
+    import numpy as np
+    import torch
+
+    from paper_2211_13719_gb300 import build as _build
+    from paper_2211_13719_gb300 import mrhs
+    import synth
+
+    _build.build()
+    n = 48
+    stream = torch.cuda.current_stream()
+
+    def ev(fn):
+        for _ in range(2):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"case": name, "nrhs": n, "reps": reps}
+    if name == "blas":
+        rows = 16 ** 4 * 12
+        k = 4
+        basis = torch.randn((k + 1, rows, n), dtype=torch.complex64, device="cuda")
+        h = torch.empty((k + 1, n), dtype=torch.complex128, device="cuda")
+        out["rows"] = rows
+        out["ms_multi_dot_k4"] = ev(lambda: mrhs.mrhs_blas_multi_dot(basis, k, basis[k], rows, n, mrhs.MRHS_FP32, h))
+        out["GBs_multi_dot_k4"] = (k + 1) * rows * n * 8 / out["ms_multi_dot_k4"] / 1e6
+        coef = torch.full((k, n), 1e-3, dtype=torch.complex128, device="cuda")
+        out["ms_lincomb_k4"] = ev(lambda: mrhs.mrhs_blas_lincomb(basis[k], basis, k, coef, -1.0, rows, n,
+                                                                  mrhs.MRHS_FP32))
+        out["GBs_lincomb_k4"] = (k + 2) * rows * n * 8 / out["ms_lincomb_k4"] / 1e6
+        return print(json.dumps(out), flush=True)
+    dims = (24, 24, 24, 24) if name == "stencil" else (16, 16, 16, 16)
+    V = volume(dims)
+    U = synth.gauge_exp(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
+    lat = mrhs.mrhs_create_lattice(dims, -1, torch.cuda.current_device())
+    mrhs.mrhs_load_gauge(lat, U)
+    mrhs.mrhs_build_clover(lat, WORKLOAD["mass"], WORKLOAD["csw"])
+    out["dims"] = list(dims)
+    if name == "stencil":
+        a = torch.randn((V, 12, n), dtype=torch.complex64, device="cuda")
+        o = torch.empty_like(a)
+        out["ms_apply_fp32"] = ev(lambda: mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream))
+        out["alg_GBs"] = V * (576 + 192 * n) / out["ms_apply_fp32"] / 1e6
+    elif name == "intergrid":
+        p = mrhs.mrhs_mg_default_params()
+        p.n_levels = 2
+        for mu in range(4):
+            p.block[0][mu] = 4
+        p.n_vec[0] = 32
+        p.setup_sweeps = 0
+        p.max_rhs = n
+        p.coarse_m = p.smooth_m = p.inner_m = p.outer_m = 2
+        p.coarse_precision = mrhs.MRHS_FP16
+        p.use_graph = 0
+        mg = mrhs.mrhs_setup_mg(lat, p)
+        f = torch.randn((V, 12, n), dtype=torch.complex64, device="cuda")
+        c = torch.randn((V // 256, 64, n), dtype=torch.complex64, device="cuda")
+        out["ms_restrict_api"] = ev(lambda: mrhs.mrhs_restrict(mg, 0, f, c, n))
+        out["ms_prolong"] = ev(lambda: mrhs.mrhs_prolong(mg, 0, c, f, n))
+        mrhs.mrhs_destroy_mg(mg)
+    else:
+        raise SystemExit(f"unknown case {name}")
+    mrhs.mrhs_destroy_lattice(lat)
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -408,7 +556,15 @@ def main():
     ap.add_argument("--plain-solves", type=int, default=2)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--case", default=None, choices=["stencil", "intergrid", "blas"],
+                    help="run a small profiling case of one kernel family instead of the benchmark")
+    ap.add_argument("--case-reps", type=int, default=3)
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case, args.case_reps)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

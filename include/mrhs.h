@@ -82,6 +82,21 @@ const char *mrhs_last_error(void);
  * (a replayed CUDA graph counts its kernel nodes).  Diagnostic only. */
 uint64_t mrhs_kernel_launch_count(void);
 
+/* Event timing of one kernel, for measurement harnesses (no effect on any
+ * result).  After mrhs_kernel_timer_start(name), every launch of the kernel
+ * `name` ("k_dslash_x2", "k_dslash", "k_dots_norm", "k_lincomb_scale",
+ * "k_lincomb", "k_multi_dot", "k_norm2", "k_restrict_tc", "k_prolong_tc",
+ * "k_coarse_tc") that is not being captured into a CUDA graph is bracketed by
+ * two CUDA events recorded on its launching stream; launches captured into a
+ * graph are only counted.  mrhs_kernel_timer_stop waits for the recorded
+ * events, writes the summed event time of the timed launches (ms), their
+ * number and the number of captured launches (each pointer may be NULL), and
+ * ends the timing.  One timing at a time: start while one is active, or stop
+ * while none is, returns MRHS_ERR_INVALID.  The events are created on the
+ * device current at the launch. */
+mrhs_status mrhs_kernel_timer_start(const char *kernel_name);
+mrhs_status mrhs_kernel_timer_stop(double *total_ms, int64_t *timed_launches, int64_t *captured_launches);
+
 /* ------------------------------------------------------------------ */
 /* Lattice, gauge field, clover term                                   */
 /* ------------------------------------------------------------------ */
@@ -146,7 +161,7 @@ mrhs_status mrhs_blas_lincomb(void *w_dev, const void *basis_dev, int k,
  * device memory while they run (code being recorded into a CUDA graph,
  * hosts that reserve all device memory up front, programs whose memory
  * belongs to another allocator): it never calls cudaMalloc or cudaFree.
- * Its reduction scratch is a statically allocated 4 MiB device array shared
+ * Its reduction scratch is a statically allocated 4.1 MiB device array shared
  * by all calls; nrhs is limited to 1..64 (MRHS_ERR_INVALID beyond).  The
  * first call on a device looks the array up (cudaGetSymbolAddress) with that
  * device current: make it before any stream capture.  Calls that overlap on
@@ -208,11 +223,15 @@ mrhs_status mrhs_mg_get_prolongator(mrhs_mg *mg, int level, double *host_out);
 mrhs_status mrhs_mg_get_coarse_links(mrhs_mg *mg, int level, double *host_out);
 
 /* Restriction c = P^dagger psi from level `level` to level+1 (Sec. 5),
- * FP32 fields (level-l layout in, coarse layout out). */
+ * FP32 fields (level-l layout in, coarse layout out).  Hierarchies built
+ * with coarse_precision FP16 or BF16 compute it on the tensor cores (FP16
+ * operands scaled per RHS, FP32 accumulation, nrhs <= 64); FP32 hierarchies
+ * on CUDA cores. */
 mrhs_status mrhs_restrict(mrhs_mg *mg, int level, const void *fine_dev,
                           void *coarse_dev, int nrhs, void *stream);
 
-/* Prolongation psi = P c from level+1 to level `level` (Sec. 5), FP32. */
+/* Prolongation psi = P c from level+1 to level `level` (Sec. 5), FP32
+ * fields, on the tensor cores or CUDA cores as for mrhs_restrict. */
 mrhs_status mrhs_prolong(mrhs_mg *mg, int level, const void *coarse_dev,
                          void *fine_dev, int nrhs, void *stream);
 

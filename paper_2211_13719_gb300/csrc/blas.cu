@@ -2,17 +2,22 @@
 // RHS computed "simultaneously" in one pass instead of one after another).
 //
 // A field is `rows` rows of `n` complex values, RHS innermost.  A block of
-// n * rpb threads (rpb = rows per block pass) gives each thread one RHS
-// column and a strided set of rows, so every warp load is contiguous in
+// (n / W) * rpb threads (rpb = rows per block pass) gives each thread W
+// adjacent RHS columns (W = 2 for FP32 fields with even n: one 16-byte load
+// per row) and a strided set of rows, so every warp load is contiguous in
 // memory.  Each thread accumulates its rows; the block reduces over its
-// row-threads in a fixed order into a per-block partial; the last block to
-// finish (atomic ticket) sums the partials in block order.  The sum order of
+// row-threads in a fixed order into a per-block partial; the last block of
+// each group of 32 (atomic ticket) sums its group's partials in block order
+// and the last group sums the group totals in group order.  The sum order of
 // RHS r therefore depends only on (rows, n, grid), never on the values of
 // other RHS: batching does not change a result beyond that fixed order.
 //
 // FP32 fields are accumulated in FP32 per thread and in FP64 from the block
 // level up; FP64 fields in FP64 throughout.  Outputs are FP64.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "internal.cuh"
@@ -39,35 +44,74 @@ static int current_sms() {
 
 void Scratch::ensure(int blocks, int cols) {
     if (!counter.ptr) {
-        counter.alloc(sizeof(unsigned int) * 4);
-        MRHS_CUDA(cudaMemset(counter.ptr, 0, sizeof(unsigned int) * 4));
+        counter.alloc(sizeof(unsigned int) * 64);
+        MRHS_CUDA(cudaMemset(counter.ptr, 0, sizeof(unsigned int) * 64));
     }
     if (blocks > max_blocks || cols > max_cols) {
         const int b = std::max(blocks, max_blocks);
         const int c = std::max(cols, max_cols);
-        partials.alloc(sizeof(double2) * (size_t)b * (size_t)c);
+        // per-block partials, then one total per group of 32 blocks
+        partials.alloc(sizeof(double2) * (size_t)(b + (b + 31) / 32) * (size_t)c);
         max_blocks = b;
         max_cols = c;
     }
 }
 
 struct RedGeom {
+    int w;        // RHS columns per thread (2: FP32 pairs moved as float4)
     int rpb;      // rows per block pass
-    int threads;  // n * rpb
+    int threads;  // (n / w) * rpb
     int blocks;
 };
 
-static RedGeom red_geom(int64_t rows, int n) {
+constexpr int RED_GROUP = 32;  // blocks per first-level group of the cross-block sum
+
+static RedGeom red_geom(int64_t rows, int n, int w = 1) {
     RedGeom r;
-    r.rpb = n >= 256 ? 1 : 256 / n;
-    r.threads = n * r.rpb;
-    // at least 32 rows per thread, at most 4 blocks per SM: enough loads in
-    // flight for HBM on large fields, few partials for the last block to sum
-    // on the small coarse-level fields
+    r.w = w;
+    const int nw = n / w;
+    const int target = w == 2 ? 128 : 256;
+    r.rpb = nw >= target ? 1 : target / nw;
+    r.threads = nw * r.rpb;
+    // at least 32 rows per thread; at most 4 blocks of 256 (8 of 128) threads per
+    // SM: enough loads in flight for HBM on large fields, few partials on small ones
     const int64_t need = (rows + 32 * r.rpb - 1) / (32 * r.rpb);
-    const int64_t cap = (int64_t)current_sms() * 4;
+    const int64_t cap = (int64_t)current_sms() * (w == 2 ? 8 : 4);
     r.blocks = (int)std::max<int64_t>(1, std::min(need, cap));
     return r;
+}
+
+// Caps the grid at one full wave: the blocks of `kernel` (block size
+// g.threads, `smem` dynamic bytes) that are resident on all SMs at once.
+// Rows are split evenly over the blocks, so a partial second wave would
+// leave most SMs idle for its duration.
+template <typename K> static void fit_wave(RedGeom &g, K kernel, size_t smem) {
+    // resident blocks per SM for (kernel, block size, smem), computed once per key
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t>, int> cache;
+    const auto key = std::make_tuple(reinterpret_cast<const void *>(kernel), g.threads, smem);
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) per_sm = it->second;
+    }
+    if (per_sm == 0) {
+        MRHS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, g.threads, smem));
+        per_sm = std::max(1, per_sm);
+        std::lock_guard<std::mutex> lock(mu);
+        cache[key] = per_sm;
+    }
+    g.blocks = std::min(g.blocks, per_sm * current_sms());
+}
+
+// FP32 fields take the paired path when n is even and every field pointer
+// (and the basis stride) keeps the 16-byte alignment of a float4
+static int pair_width(mrhs_precision p, int n, std::initializer_list<const void *> ptrs, int64_t stride = 0) {
+    if (p != MRHS_FP32 || n % 2 != 0 || stride % 2 != 0) return 1;
+    for (const void *q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) & 15u) return 1;
+    return 2;
 }
 
 template <typename T> struct vec2;
@@ -84,19 +128,83 @@ template <typename T> __device__ __forceinline__ void stv(T *p, int64_t i, cplx<
     o.y = v.im;
     reinterpret_cast<typename vec2<T>::type *>(p)[i] = o;
 }
+// W consecutive complex values starting at element e (e even when W == 2)
+template <int W, typename T> __device__ __forceinline__ void ldw(const T *p, int64_t e, cplx<T> (&x)[W]) {
+    if constexpr (W == 2) {
+        static_assert(std::is_same<T, float>::value, "paired access is FP32");
+        const float4 v = *reinterpret_cast<const float4 *>(p + 2 * e);
+        x[0] = {v.x, v.y};
+        x[1] = {v.z, v.w};
+    } else {
+        x[0] = ldv(p, e);
+    }
+}
+template <int W, typename T> __device__ __forceinline__ void stw(T *p, int64_t e, const cplx<T> (&x)[W]) {
+    if constexpr (W == 2) {
+        *reinterpret_cast<float4 *>(p + 2 * e) = make_float4(x[0].re, x[0].im, x[1].re, x[1].im);
+    } else {
+        stv(p, e, x[0]);
+    }
+}
 
-// Block-level fixed-order reduction of `cols` complex values per thread
-// (vals[c] for c < cols), then the cross-block finish by the last block.
-// smem: double2 [rpb][cols][n] laid out as [(rsub*cols + c)*n + col].
-// With real_only the single column goes to out_real; with real_tail the
-// first cols-1 columns go to out and the last column's real part to out_real.
+// fixed-order sum of count values p[0], p[stride], ... (four interleaved partial sums)
+__device__ __forceinline__ double2 ordered_sum(const double2 *p, int count, int stride) {
+    double2 q[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    int b = 0;
+    for (; b + 4 <= count; b += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const double2 v = __ldcg(&p[(int64_t)(b + u) * stride]);
+            q[u].x += v.x;
+            q[u].y += v.y;
+        }
+    }
+    for (; b < count; ++b) {
+        const double2 v = __ldcg(&p[(int64_t)b * stride]);
+        q[0].x += v.x;
+        q[0].y += v.y;
+    }
+    return make_double2((q[0].x + q[1].x) + (q[2].x + q[3].x), (q[0].y + q[1].y) + (q[2].y + q[3].y));
+}
+
+struct FinishOut {
+    double2 *out;
+    bool accumulate;
+    bool real_only;   // the single column goes to out_real
+    double *out_real;
+    bool real_tail;   // the first cols - 1 columns go to out, the last column's real part to out_real
+};
+
+__device__ __forceinline__ void finish_emit(const FinishOut &f, int cols, int n, int o, double2 s) {
+    if (f.real_only) {
+        f.out_real[o] = s.x;
+    } else if (f.real_tail && o >= (cols - 1) * n) {
+        f.out_real[o - (cols - 1) * n] = s.x;
+    } else if (f.accumulate) {
+        const double2 prev = f.out[o];
+        f.out[o] = make_double2(prev.x + s.x, prev.y + s.y);
+    } else {
+        f.out[o] = s;
+    }
+}
+
+// Block-level fixed-order reduction of `cols` quantities for the thread's W
+// columns col..col+W-1 (vals[c * W + w]), then the cross-block finish: the last
+// block of each group of RED_GROUP consecutive blocks sums the group's partials
+// in block order, the last group sums the group totals in group order.  Every
+// sum has a fixed order, so no result depends on the order blocks finish in.
+// smem: double2 [rpb][cols][n] as [(rsub * cols + c) * n + col]; partials hold
+// (blocks + groups) * cols * n; counter[0..groups] is zero on entry and left zero.
+template <int W>
 __device__ void block_finish(double2 *smem, const double2 *vals, int cols, int n, int rpb, int col, int rsub,
-                             double2 *partials, unsigned int *counter, double2 *out, bool accumulate,
-                             bool real_only, double *out_real, bool real_tail = false) {
-    for (int c = 0; c < cols; ++c) smem[((int64_t)rsub * cols + c) * n + col] = vals[c];
+                             double2 *partials, unsigned int *counter, const FinishOut &f) {
+    for (int c = 0; c < cols; ++c)
+#pragma unroll
+        for (int w = 0; w < W; ++w) smem[((int64_t)rsub * cols + c) * n + col + w] = vals[c * W + w];
     __syncthreads();
     const int tid = threadIdx.x;
     const int nout = cols * n;
+    const int nb = (int)gridDim.x;
     for (int o = tid; o < nout; o += blockDim.x) {
         double2 s = make_double2(0.0, 0.0);
         for (int q = 0; q < rpb; ++q) {
@@ -106,151 +214,182 @@ __device__ void block_finish(double2 *smem, const double2 *vals, int cols, int n
         }
         partials[(int64_t)blockIdx.x * nout + o] = s;
     }
+    const int g = (int)blockIdx.x / RED_GROUP;
+    const int groups = (nb + RED_GROUP - 1) / RED_GROUP;
+    const int gb0 = g * RED_GROUP, gsize = min(RED_GROUP, nb - gb0);
     __shared__ bool last;
     __threadfence();
     __syncthreads();
+    if (tid == 0) last = atomicAdd(&counter[g], 1u) == (unsigned)(gsize - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double2 *gpart = partials + (int64_t)nb * nout;
+    for (int o = tid; o < nout; o += blockDim.x) {
+        const double2 s = ordered_sum(partials + (int64_t)gb0 * nout + o, gsize, nout);
+        if (groups == 1) finish_emit(f, cols, n, o, s);
+        else gpart[(int64_t)g * nout + o] = s;
+    }
+    if (groups == 1) {
+        if (tid == 0) counter[g] = 0u;
+        return;
+    }
+    __threadfence();
+    __syncthreads();
     if (tid == 0) {
-        const unsigned int ticket = atomicAdd(counter, 1u);
-        last = (ticket == gridDim.x - 1);
+        counter[g] = 0u;
+        last = atomicAdd(&counter[groups], 1u) == (unsigned)(groups - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int o = tid; o < nout; o += blockDim.x) {
-        // fixed order: four interleaved partial sums over the blocks, then combined
-        double2 q[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
-                        make_double2(0.0, 0.0)};
-        const int nb = (int)gridDim.x;
-        int b = 0;
-        for (; b + 4 <= nb; b += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double2 v = __ldcg(&partials[(int64_t)(b + u) * nout + o]);
-                q[u].x += v.x;
-                q[u].y += v.y;
-            }
-        }
-        for (; b < nb; ++b) {
-            const double2 v = __ldcg(&partials[(int64_t)b * nout + o]);
-            q[0].x += v.x;
-            q[0].y += v.y;
-        }
-        double2 s = make_double2((q[0].x + q[1].x) + (q[2].x + q[3].x), (q[0].y + q[1].y) + (q[2].y + q[3].y));
-        if (real_only) {
-            out_real[o] = s.x;
-        } else if (real_tail && o >= (cols - 1) * n) {
-            out_real[o - (cols - 1) * n] = s.x;
-        } else if (accumulate) {
-            double2 prev = out[o];
-            out[o] = make_double2(prev.x + s.x, prev.y + s.y);
-        } else {
-            out[o] = s;
-        }
-    }
-    if (tid == 0) *counter = 0u;
+    for (int o = tid; o < nout; o += blockDim.x) finish_emit(f, cols, n, o, ordered_sum(gpart + o, groups, nout));
+    if (tid == 0) counter[groups] = 0u;
 }
 
+// thread geometry shared by the reductions: W columns per thread, rpb row-threads per block
+#define RED_THREAD_GEOMETRY                    \
+    const int nw = n / W;                      \
+    const int col = (int)(threadIdx.x % nw) * W; \
+    const int rsub = (int)(threadIdx.x / nw);   \
+    const int64_t step = (int64_t)gridDim.x * rpb
+
 // out[j][r] = sum_i conj(b_j[i][r]) w[i][r], j < k <= KCHUNK
-template <typename T>
+template <typename T, int W>
 __global__ void k_multi_dot(const T *__restrict__ basis, int64_t stride, int k, const T *__restrict__ w,
                             int64_t rows, int n, int rpb, double2 *partials, unsigned int *counter,
                             double2 *out, int accumulate) {
     extern __shared__ double2 smem[];
-    const int col = threadIdx.x % n;
-    const int rsub = threadIdx.x / n;
-    cplx<T> acc[KCHUNK];
+    RED_THREAD_GEOMETRY;
+    cplx<T> acc[KCHUNK][W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j) acc[j] = {0, 0};
-    const int64_t step = (int64_t)gridDim.x * rpb;
+    for (int j = 0; j < KCHUNK; ++j)
+#pragma unroll
+        for (int v = 0; v < W; ++v) acc[j][v] = {0, 0};
     for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
         const int64_t e = row * n + col;
-        const cplx<T> x = ldv(w, e);
+        cplx<T> x[W];
+        ldw<W>(w, e, x);
 #pragma unroll
-        for (int j = 0; j < KCHUNK; ++j)
-            if (j < k) cmac_conj(acc[j], ldv(basis, e + j * stride), x);
+        for (int j = 0; j < KCHUNK; ++j) {
+            if (j < k) {
+                cplx<T> b[W];
+                ldw<W>(basis + 2 * j * stride, e, b);
+#pragma unroll
+                for (int v = 0; v < W; ++v) cmac_conj(acc[j][v], b[v], x[v]);
+            }
+        }
     }
-    double2 vals[KCHUNK];
+    double2 vals[KCHUNK * W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j) vals[j] = make_double2((double)acc[j].re, (double)acc[j].im);
-    block_finish(smem, vals, k, n, rpb, col, rsub, partials, counter, out, accumulate != 0, false, nullptr);
+    for (int j = 0; j < KCHUNK; ++j)
+#pragma unroll
+        for (int v = 0; v < W; ++v) vals[j * W + v] = make_double2((double)acc[j][v].re, (double)acc[j][v].im);
+    block_finish<W>(smem, vals, k, n, rpb, col, rsub, partials, counter,
+                    FinishOut{out, accumulate != 0, false, nullptr, false});
 }
 
-template <typename T>
+template <typename T, int W>
 __global__ void k_norm2(const T *__restrict__ w, int64_t rows, int n, int rpb, double2 *partials,
                         unsigned int *counter, double *out) {
     extern __shared__ double2 smem[];
-    const int col = threadIdx.x % n;
-    const int rsub = threadIdx.x / n;
-    T acc = 0;
-    const int64_t step = (int64_t)gridDim.x * rpb;
+    RED_THREAD_GEOMETRY;
+    T acc[W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) acc[v] = 0;
     for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
-        const cplx<T> x = ldv(w, row * n + col);
-        acc = fmadd(x.re, x.re, acc);
-        acc = fmadd(x.im, x.im, acc);
+        cplx<T> x[W];
+        ldw<W>(w, row * n + col, x);
+#pragma unroll
+        for (int v = 0; v < W; ++v) {
+            acc[v] = fmadd(x[v].re, x[v].re, acc[v]);
+            acc[v] = fmadd(x[v].im, x[v].im, acc[v]);
+        }
     }
-    double2 v = make_double2((double)acc, 0.0);
-    block_finish(smem, &v, 1, n, rpb, col, rsub, partials, counter, nullptr, false, true, out);
+    double2 vals[W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) vals[v] = make_double2((double)acc[v], 0.0);
+    block_finish<W>(smem, vals, 1, n, rpb, col, rsub, partials, counter, FinishOut{nullptr, false, true, out, false});
 }
 
 // w += alpha * sum_j coef[j][r] b_j ; optional ||w||^2 per RHS
-template <typename TW, typename TB, bool NORM>
+template <typename TW, typename TB, bool NORM, int W>
 __global__ void k_lincomb(TW *__restrict__ w, const TB *__restrict__ basis, int64_t stride, int k,
                           const double2 *__restrict__ coef, double alpha, int64_t rows, int n, int rpb,
                           double2 *partials, unsigned int *counter, double *norm_out) {
     extern __shared__ double2 smem[];
-    // coefficients of this thread's column, scaled by alpha, in the basis precision
+    // coefficients of this thread's columns, scaled by alpha, in the basis precision
     using TC = typename std::conditional<sizeof(TW) == 8 || sizeof(TB) == 8, double, float>::type;
-    const int col = threadIdx.x % n;
-    const int rsub = threadIdx.x / n;
-    cplx<TC> cf[KCHUNK];
+    RED_THREAD_GEOMETRY;
+    cplx<TC> cf[KCHUNK][W];
 #pragma unroll
     for (int j = 0; j < KCHUNK; ++j) {
-        if (j < k) {
-            const double2 c = coef[(int64_t)j * n + col];
-            cf[j] = {(TC)(alpha * c.x), (TC)(alpha * c.y)};
-        } else {
-            cf[j] = {0, 0};
+#pragma unroll
+        for (int v = 0; v < W; ++v) {
+            if (j < k) {
+                const double2 c = coef[(int64_t)j * n + col + v];
+                cf[j][v] = {(TC)(alpha * c.x), (TC)(alpha * c.y)};
+            } else {
+                cf[j][v] = {0, 0};
+            }
         }
     }
-    TW nacc = 0;
-    const int64_t step = (int64_t)gridDim.x * rpb;
+    TW nacc[W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) nacc[v] = 0;
     for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
         const int64_t e = row * n + col;
-        cplx<TC> s = {0, 0};
+        cplx<TC> s[W];
+#pragma unroll
+        for (int v = 0; v < W; ++v) s[v] = {0, 0};
 #pragma unroll
         for (int j = 0; j < KCHUNK; ++j) {
             if (j < k) {
-                const cplx<TB> b = ldv(basis, e + j * stride);
-                cmac(s, cf[j], cplx<TC>{(TC)b.re, (TC)b.im});
+                cplx<TB> b[W];
+                ldw<W>(basis + 2 * j * stride, e, b);
+#pragma unroll
+                for (int v = 0; v < W; ++v) cmac(s[v], cf[j][v], cplx<TC>{(TC)b[v].re, (TC)b[v].im});
             }
         }
-        cplx<TW> x = ldv(w, e);
-        x.re += (TW)s.re;
-        x.im += (TW)s.im;
-        stv(w, e, x);
-        if (NORM) {
-            nacc = fmadd(x.re, x.re, nacc);
-            nacc = fmadd(x.im, x.im, nacc);
+        cplx<TW> x[W];
+        ldw<W>(w, e, x);
+#pragma unroll
+        for (int v = 0; v < W; ++v) {
+            x[v].re += (TW)s[v].re;
+            x[v].im += (TW)s[v].im;
+            if (NORM) {
+                nacc[v] = fmadd(x[v].re, x[v].re, nacc[v]);
+                nacc[v] = fmadd(x[v].im, x[v].im, nacc[v]);
+            }
         }
+        stw<W>(w, e, x);
     }
     if (NORM) {
-        double2 v = make_double2((double)nacc, 0.0);
-        block_finish(smem, &v, 1, n, rpb, col, rsub, partials, counter, nullptr, false, true, norm_out);
+        double2 vals[W];
+#pragma unroll
+        for (int v = 0; v < W; ++v) vals[v] = make_double2((double)nacc[v], 0.0);
+        block_finish<W>(smem, vals, 1, n, rpb, col, rsub, partials, counter,
+                        FinishOut{nullptr, false, true, norm_out, false});
     }
 }
 
-// dst = src / sqrt(nrm2[col]); one RHS column per thread, factor computed once
-template <typename T>
+// dst = src / sqrt(nrm2[col]); factors computed once per thread
+template <typename T, int W>
 __global__ void k_scale_inv_sqrt(T *dst, const T *src, const double *nrm2, int64_t rows, int n, int rpb) {
-    const int col = threadIdx.x % n;
-    const int rsub = threadIdx.x / n;
-    const double v = nrm2[col];
-    const T f = v > 0.0 ? (T)(1.0 / sqrt(v)) : (T)0;
-    const int64_t step = (int64_t)gridDim.x * rpb;
+    RED_THREAD_GEOMETRY;
+    T f[W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) {
+        const double q = nrm2[col + v];
+        f[v] = q > 0.0 ? (T)(1.0 / sqrt(q)) : (T)0;
+    }
     for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
         const int64_t e = row * n + col;
-        const cplx<T> x = ldv(src, e);
-        stv(dst, e, cplx<T>{x.re * f, x.im * f});
+        cplx<T> x[W];
+        ldw<W>(src, e, x);
+#pragma unroll
+        for (int v = 0; v < W; ++v) x[v] = {x[v].re * f[v], x[v].im * f[v]};
+        stw<W>(dst, e, x);
     }
 }
 
@@ -274,100 +413,136 @@ __global__ void k_axpy(T a, const T *x, T *y, int64_t count) {
 }
 
 // out[j][r] = <b_j, w>_r for j < k (k < KCHUNK) and nrm2[r] = ||w_r||^2, one pass over w
-template <typename T>
+template <typename T, int W>
 __global__ void k_dots_norm(const T *__restrict__ basis, int64_t stride, int k, const T *__restrict__ w,
                             int64_t rows, int n, int rpb, double2 *partials, unsigned int *counter, double2 *out,
                             double *nrm2) {
     extern __shared__ double2 smem[];
-    const int col = threadIdx.x % n;
-    const int rsub = threadIdx.x / n;
-    cplx<T> acc[KCHUNK];
+    RED_THREAD_GEOMETRY;
+    cplx<T> acc[KCHUNK][W];
+    T nacc[W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j) acc[j] = {0, 0};
-    T nacc = 0;
-    const int64_t step = (int64_t)gridDim.x * rpb;
+    for (int v = 0; v < W; ++v) {
+        nacc[v] = 0;
+#pragma unroll
+        for (int j = 0; j < KCHUNK; ++j) acc[j][v] = {0, 0};
+    }
     for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
         const int64_t e = row * n + col;
-        const cplx<T> x = ldv(w, e);
-        nacc = fmadd(x.re, x.re, nacc);
-        nacc = fmadd(x.im, x.im, nacc);
+        cplx<T> x[W];
+        ldw<W>(w, e, x);
 #pragma unroll
-        for (int j = 0; j < KCHUNK - 1; ++j)
-            if (j < k) cmac_conj(acc[j], ldv(basis, e + j * stride), x);
+        for (int v = 0; v < W; ++v) {
+            nacc[v] = fmadd(x[v].re, x[v].re, nacc[v]);
+            nacc[v] = fmadd(x[v].im, x[v].im, nacc[v]);
+        }
+#pragma unroll
+        for (int j = 0; j < KCHUNK - 1; ++j) {
+            if (j < k) {
+                cplx<T> b[W];
+                ldw<W>(basis + 2 * j * stride, e, b);
+#pragma unroll
+                for (int v = 0; v < W; ++v) cmac_conj(acc[j][v], b[v], x[v]);
+            }
+        }
     }
-    double2 vals[KCHUNK];
+    double2 vals[KCHUNK * W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j) vals[j] = make_double2((double)acc[j].re, (double)acc[j].im);
-    vals[k] = make_double2((double)nacc, 0.0);
-    block_finish(smem, vals, k + 1, n, rpb, col, rsub, partials, counter, out, false, false, nrm2, true);
+    for (int j = 0; j < KCHUNK; ++j)
+#pragma unroll
+        for (int v = 0; v < W; ++v) vals[j * W + v] = make_double2((double)acc[j][v].re, (double)acc[j][v].im);
+#pragma unroll
+    for (int v = 0; v < W; ++v) vals[k * W + v] = make_double2((double)nacc[v], 0.0);
+    block_finish<W>(smem, vals, k + 1, n, rpb, col, rsub, partials, counter, FinishOut{out, false, false, nrm2, true});
 }
 
 // w <- (w - sum_{j<k} h_j b_j) / beta with beta^2 = max(||w||^2 - sum_{all j<kall} |h_j|^2, 1e-6 ||w||^2)
 // (Pythagoras for an orthonormal basis); writes beta^2 to hn2 and ||w_new||^2 to nn.
 // `coef` points at the first of the k coefficients handled here, `hall` at all kall of them.
-template <typename T>
+template <typename T, int W>
 __global__ void k_lincomb_scale(T *__restrict__ w, const T *__restrict__ basis, int64_t stride, int k,
                                 const double2 *__restrict__ coef, const double2 *__restrict__ hall, int kall,
                                 const double *__restrict__ nrm2, double *__restrict__ hn2, int64_t rows, int n,
                                 int rpb, double2 *partials, unsigned int *counter, double *nn) {
     extern __shared__ double2 smem[];
-    const int col = threadIdx.x % n;
-    const int rsub = threadIdx.x / n;
-    double hh = 0.0;
-    for (int j = 0; j < kall; ++j) {
-        const double2 c = hall[(int64_t)j * n + col];
-        hh += c.x * c.x + c.y * c.y;
-    }
-    const double w2 = nrm2[col];
-    const double b2 = fmax(w2 - hh, 1e-6 * w2);
-    const double inv = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
-    if (blockIdx.x == 0 && rsub == 0) hn2[col] = b2;
-    cplx<T> cf[KCHUNK];
+    RED_THREAD_GEOMETRY;
+    cplx<T> cf[KCHUNK][W];
+    T f[W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j) {
-        if (j < k) {
-            const double2 c = coef[(int64_t)j * n + col];
-            cf[j] = {(T)(-c.x), (T)(-c.y)};
-        } else {
-            cf[j] = {0, 0};
+    for (int v = 0; v < W; ++v) {
+        double hh = 0.0;
+        for (int j = 0; j < kall; ++j) {
+            const double2 c = hall[(int64_t)j * n + col + v];
+            hh += c.x * c.x + c.y * c.y;
+        }
+        const double w2 = nrm2[col + v];
+        const double b2 = fmax(w2 - hh, 1e-6 * w2);
+        f[v] = (T)(b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0);
+        if (blockIdx.x == 0 && rsub == 0) hn2[col + v] = b2;
+#pragma unroll
+        for (int j = 0; j < KCHUNK; ++j) {
+            if (j < k) {
+                const double2 c = coef[(int64_t)j * n + col + v];
+                cf[j][v] = {(T)(-c.x), (T)(-c.y)};
+            } else {
+                cf[j][v] = {0, 0};
+            }
         }
     }
-    const T f = (T)inv;
-    T nacc = 0;
-    const int64_t step = (int64_t)gridDim.x * rpb;
+    T nacc[W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) nacc[v] = 0;
     for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
         const int64_t e = row * n + col;
-        cplx<T> x = ldv(w, e);
+        cplx<T> x[W];
+        ldw<W>(w, e, x);
 #pragma unroll
-        for (int j = 0; j < KCHUNK; ++j)
-            if (j < k) cmac(x, cf[j], ldv(basis, e + j * stride));
-        x.re *= f;
-        x.im *= f;
-        stv(w, e, x);
-        nacc = fmadd(x.re, x.re, nacc);
-        nacc = fmadd(x.im, x.im, nacc);
+        for (int j = 0; j < KCHUNK; ++j) {
+            if (j < k) {
+                cplx<T> b[W];
+                ldw<W>(basis + 2 * j * stride, e, b);
+#pragma unroll
+                for (int v = 0; v < W; ++v) cmac(x[v], cf[j][v], b[v]);
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < W; ++v) {
+            x[v].re *= f[v];
+            x[v].im *= f[v];
+            nacc[v] = fmadd(x[v].re, x[v].re, nacc[v]);
+            nacc[v] = fmadd(x[v].im, x[v].im, nacc[v]);
+        }
+        stw<W>(w, e, x);
     }
-    double2 v = make_double2((double)nacc, 0.0);
-    block_finish(smem, &v, 1, n, rpb, col, rsub, partials, counter, nullptr, false, true, nn);
+    double2 vals[W];
+#pragma unroll
+    for (int v = 0; v < W; ++v) vals[v] = make_double2((double)nacc[v], 0.0);
+    block_finish<W>(smem, vals, 1, n, rpb, col, rsub, partials, counter, FinishOut{nullptr, false, true, nn, false});
 }
 
-// columns whose new basis vector is not unit length (cancellation in the
-// Pythagorean norm) are rescaled; the Givens step applies the same factor to beta
-// columns whose new basis vector is not unit length (cancellation in the
+// Columns whose new basis vector is not unit length (cancellation in the
 // Pythagorean norm) are rescaled; the Givens step applies the same factor to
-// beta.  One column per thread: unflagged columns return without touching data.
-template <typename T>
+// beta.  Threads whose columns are all unflagged return without touching data.
+template <typename T, int W>
 __global__ void k_norm_fixup(T *__restrict__ w, const double *__restrict__ nn, int64_t rows, int n, int rpb) {
-    const int col = threadIdx.x % n;
-    const int rsub = threadIdx.x / n;
-    const double f = nn[col];
-    if (!(f > 0.0 && fabs(f - 1.0) > 1e-2)) return;
-    const T sc = (T)(1.0 / sqrt(f));
-    const int64_t step = (int64_t)gridDim.x * rpb;
+    RED_THREAD_GEOMETRY;
+    T sc[W];
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < W; ++v) {
+        const double f = nn[col + v];
+        const bool flag = f > 0.0 && fabs(f - 1.0) > 1e-2;
+        sc[v] = flag ? (T)(1.0 / sqrt(f)) : (T)1;
+        any = any || flag;
+    }
+    if (!any) return;
     for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
         const int64_t e = row * n + col;
-        const cplx<T> x = ldv(w, e);
-        stv(w, e, cplx<T>{x.re * sc, x.im * sc});
+        cplx<T> x[W];
+        ldw<W>(w, e, x);
+#pragma unroll
+        for (int v = 0; v < W; ++v) x[v] = {x[v].re * sc[v], x[v].im * sc[v]};
+        stw<W>(w, e, x);
     }
 }
 
@@ -376,26 +551,40 @@ static void check_n(int n) {
     if (n < 1 || n > 256) fail(MRHS_ERR_INVALID, "batched BLAS supports 1 <= nrhs <= 256");
 }
 
+// calls f(T{}, integral_constant<W>) for the field precision and column width
+template <typename F> static void dispatch(mrhs_precision p, int w, const char *what, F &&f) {
+    if (p == MRHS_FP32) {
+        if (w == 2) f(float{}, std::integral_constant<int, 2>{});
+        else f(float{}, std::integral_constant<int, 1>{});
+    } else if (p == MRHS_FP64) {
+        f(double{}, std::integral_constant<int, 1>{});
+    } else {
+        fail(MRHS_ERR_INVALID, std::string(what) + ": FP32 or FP64 fields");
+    }
+}
+
+#define RED_TYPES(tT, tW)          \
+    using T = decltype(tT);        \
+    constexpr int W = decltype(tW)::value
+
 void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w, int64_t rows, int n,
                double2 *out, Scratch &sc, cudaStream_t s, bool accumulate) {
     check_n(n);
     if (k <= 0) return;
-    const RedGeom g = red_geom(rows, n);
+    const RedGeom g0 = red_geom(rows, n, pair_width(p, n, {basis, w}, stride));
     for (int j0 = 0; j0 < k; j0 += KCHUNK) {
         const int kk = std::min(KCHUNK, k - j0);
-        sc.ensure(g.blocks, kk * n);
-        const size_t smem = sizeof(double2) * (size_t)g.rpb * kk * n;
-        if (p == MRHS_FP32) {
-            k_multi_dot<float><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<const float *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const float *>(w), rows, n,
+        const size_t smem = sizeof(double2) * (size_t)g0.rpb * kk * n;
+        dispatch(p, g0.w, "multi_dot", [&](auto tT, auto tW) {
+            RED_TYPES(tT, tW);
+            RedGeom g = g0;
+            fit_wave(g, k_multi_dot<T, W>, smem);
+            sc.ensure(g.blocks, kk * n);
+            MRHS_TIMED("k_multi_dot", s);
+            k_multi_dot<T, W><<<g.blocks, g.threads, smem, s>>>(
+                static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const T *>(w), rows, n,
                 g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), out + (int64_t)j0 * n, accumulate);
-        } else if (p == MRHS_FP64) {
-            k_multi_dot<double><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<const double *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const double *>(w), rows,
-                n, g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), out + (int64_t)j0 * n, accumulate);
-        } else {
-            fail(MRHS_ERR_INVALID, "multi_dot: FP32 or FP64 fields");
-        }
+        });
         MRHS_LAUNCHED("k_multi_dot");
     }
 }
@@ -403,60 +592,60 @@ void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const
 void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, int k, void *w, int64_t rows, int n,
                          double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s) {
     check_n(n);
-    const RedGeom g = red_geom(rows, n);
+    const RedGeom g0 = red_geom(rows, n, pair_width(p, n, {basis, w}, stride));
     const bool f32 = p == MRHS_FP32;
     if (!f32 && p != MRHS_FP64) fail(MRHS_ERR_INVALID, "orthonormalize: FP32 or FP64 fields");
+    const size_t esz = f32 ? 8 : 16;
     // dots (and ||w||^2 with the last chunk)
     for (int j0 = 0; j0 < k || j0 == 0; j0 += KCHUNK - 1) {
         const int kk = std::min(KCHUNK - 1, k - j0);
-        const bool last = j0 + kk >= k;
-        const size_t esz = f32 ? 8 : 16;
-        if (last) {
-            sc.ensure(g.blocks, (kk + 1) * n);
-            const size_t smem = sizeof(double2) * (size_t)g.rpb * (kk + 1) * n;
-            if (f32)
-                k_dots_norm<float><<<g.blocks, g.threads, smem, s>>>(
-                    static_cast<const float *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const float *>(w),
-                    rows, n, g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), h + (int64_t)j0 * n, nrm2);
-            else
-                k_dots_norm<double><<<g.blocks, g.threads, smem, s>>>(
-                    static_cast<const double *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const double *>(w),
-                    rows, n, g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), h + (int64_t)j0 * n, nrm2);
-            MRHS_LAUNCHED("k_dots_norm");
-            break;
+        if (j0 + kk < k) {
+            multi_dot(p, static_cast<const char *>(basis) + esz * j0 * stride, stride, kk, w, rows, n,
+                      h + (int64_t)j0 * n, sc, s);
+            continue;
         }
-        multi_dot(p, static_cast<const char *>(basis) + esz * j0 * stride, stride, kk, w, rows, n,
-                  h + (int64_t)j0 * n, sc, s);
+        const size_t smem = sizeof(double2) * (size_t)g0.rpb * (kk + 1) * n;
+        dispatch(p, g0.w, "orthonormalize", [&](auto tT, auto tW) {
+            RED_TYPES(tT, tW);
+            RedGeom g = g0;
+            fit_wave(g, k_dots_norm<T, W>, smem);
+            sc.ensure(g.blocks, (kk + 1) * n);
+            MRHS_TIMED("k_dots_norm", s);
+            k_dots_norm<T, W><<<g.blocks, g.threads, smem, s>>>(
+                static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const T *>(w), rows, n,
+                g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), h + (int64_t)j0 * n, nrm2);
+        });
+        MRHS_LAUNCHED("k_dots_norm");
+        break;
     }
     // subtract, normalise
     for (int j0 = 0; j0 < k || j0 == 0; j0 += KCHUNK) {
         const int kk = std::min(KCHUNK, k - j0);
-        const bool last = j0 + kk >= k;
-        const size_t esz = f32 ? 8 : 16;
-        if (!last) {
+        if (j0 + kk < k) {
             lincomb(p, w, p, static_cast<const char *>(basis) + esz * j0 * stride, stride, kk, h + (int64_t)j0 * n,
                     -1.0, rows, n, s);
             continue;
         }
-        sc.ensure(g.blocks, n);
-        const size_t smem = sizeof(double2) * (size_t)g.rpb * n;
-        if (f32)
-            k_lincomb_scale<float><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<float *>(w), static_cast<const float *>(basis) + 2 * j0 * stride, stride, kk,
-                h + (int64_t)j0 * n, h, k, nrm2, hn2, rows, n, g.rpb, sc.partials.as<double2>(),
-                sc.counter.as<unsigned int>(), nn);
-        else
-            k_lincomb_scale<double><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<double *>(w), static_cast<const double *>(basis) + 2 * j0 * stride, stride, kk,
-                h + (int64_t)j0 * n, h, k, nrm2, hn2, rows, n, g.rpb, sc.partials.as<double2>(),
-                sc.counter.as<unsigned int>(), nn);
+        const size_t smem = sizeof(double2) * (size_t)g0.rpb * n;
+        dispatch(p, g0.w, "orthonormalize", [&](auto tT, auto tW) {
+            RED_TYPES(tT, tW);
+            RedGeom g = g0;
+            fit_wave(g, k_lincomb_scale<T, W>, smem);
+            sc.ensure(g.blocks, n);
+            MRHS_TIMED("k_lincomb_scale", s);
+            k_lincomb_scale<T, W><<<g.blocks, g.threads, smem, s>>>(
+                static_cast<T *>(w), static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk, h + (int64_t)j0 * n,
+                h, k, nrm2, hn2, rows, n, g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), nn);
+        });
         MRHS_LAUNCHED("k_lincomb_scale");
         break;
     }
-    if (f32)
-        k_norm_fixup<float><<<g.blocks, g.threads, 0, s>>>(static_cast<float *>(w), nn, rows, n, g.rpb);
-    else
-        k_norm_fixup<double><<<g.blocks, g.threads, 0, s>>>(static_cast<double *>(w), nn, rows, n, g.rpb);
+    dispatch(p, g0.w, "orthonormalize", [&](auto tT, auto tW) {
+        RED_TYPES(tT, tW);
+        RedGeom g = g0;
+        fit_wave(g, k_norm_fixup<T, W>, 0);
+        k_norm_fixup<T, W><<<g.blocks, g.threads, 0, s>>>(static_cast<T *>(w), nn, rows, n, g.rpb);
+    });
     MRHS_LAUNCHED("k_norm_fixup");
 }
 
@@ -464,59 +653,63 @@ void multi_dot_fixed_scratch(mrhs_precision p, const void *basis, int64_t stride
                              int n, double2 *out, double2 *partials, unsigned int *counter, int max_blocks,
                              cudaStream_t s) {
     check_n(n);
-    RedGeom g = red_geom(rows, n);
-    g.blocks = std::min(g.blocks, max_blocks);
+    RedGeom g0 = red_geom(rows, n, pair_width(p, n, {basis, w}, stride));
+    g0.blocks = std::min(g0.blocks, max_blocks);
     for (int j0 = 0; j0 < k; j0 += KCHUNK) {
         const int kk = std::min(KCHUNK, k - j0);
-        const size_t smem = sizeof(double2) * (size_t)g.rpb * kk * n;
-        if (p == MRHS_FP32)
-            k_multi_dot<float><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<const float *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const float *>(w), rows, n,
-                g.rpb, partials, counter, out + (int64_t)j0 * n, 0);
-        else
-            k_multi_dot<double><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<const double *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const double *>(w), rows,
-                n, g.rpb, partials, counter, out + (int64_t)j0 * n, 0);
+        const size_t smem = sizeof(double2) * (size_t)g0.rpb * kk * n;
+        dispatch(p, g0.w, "multi_dot", [&](auto tT, auto tW) {
+            RED_TYPES(tT, tW);
+            RedGeom g = g0;
+            fit_wave(g, k_multi_dot<T, W>, smem);
+            MRHS_TIMED("k_multi_dot", s);
+            k_multi_dot<T, W><<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(basis) + 2 * j0 * stride,
+                                                                stride, kk, static_cast<const T *>(w), rows, n, g.rpb,
+                                                                partials, counter, out + (int64_t)j0 * n, 0);
+        });
         MRHS_LAUNCHED("k_multi_dot");
     }
 }
 
 void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s) {
     check_n(n);
-    const RedGeom g = red_geom(rows, n);
-    sc.ensure(g.blocks, n);
-    const size_t smem = sizeof(double2) * (size_t)g.rpb * n;
-    if (p == MRHS_FP32)
-        k_norm2<float><<<g.blocks, g.threads, smem, s>>>(static_cast<const float *>(w), rows, n, g.rpb,
-                                                         sc.partials.as<double2>(), sc.counter.as<unsigned int>(), out);
-    else if (p == MRHS_FP64)
-        k_norm2<double><<<g.blocks, g.threads, smem, s>>>(static_cast<const double *>(w), rows, n, g.rpb,
-                                                          sc.partials.as<double2>(), sc.counter.as<unsigned int>(), out);
-    else
-        fail(MRHS_ERR_INVALID, "norm2: FP32 or FP64 fields");
+    const RedGeom g0 = red_geom(rows, n, pair_width(p, n, {w}));
+    const size_t smem = sizeof(double2) * (size_t)g0.rpb * n;
+    dispatch(p, g0.w, "norm2", [&](auto tT, auto tW) {
+        RED_TYPES(tT, tW);
+        RedGeom g = g0;
+        fit_wave(g, k_norm2<T, W>, smem);
+        sc.ensure(g.blocks, n);
+        MRHS_TIMED("k_norm2", s);
+        k_norm2<T, W><<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(w), rows, n, g.rpb,
+                                                        sc.partials.as<double2>(), sc.counter.as<unsigned int>(), out);
+    });
     MRHS_LAUNCHED("k_norm2");
 }
 
-template <typename TW, typename TB>
+template <typename TW, typename TB, int W>
 static void lincomb_t(void *w, const void *basis, int64_t stride, int k, const double2 *coef, double alpha,
-                      int64_t rows, int n, cudaStream_t s, double *norm_out, Scratch *sc) {
-    const RedGeom g = red_geom(rows, n);
+                      const RedGeom &g0, int64_t rows, int n, cudaStream_t s, double *norm_out, Scratch *sc) {
+    RedGeom g = g0;
+    fit_wave(g, norm_out ? k_lincomb<TW, TB, true, W> : k_lincomb<TW, TB, false, W>,
+             norm_out ? sizeof(double2) * (size_t)g0.rpb * n : 0);
     for (int j0 = 0; j0 < k; j0 += KCHUNK) {
         const int kk = std::min(KCHUNK, k - j0);
-        const bool last_chunk = j0 + kk >= k;
-        const bool want_norm = norm_out != nullptr && last_chunk;
+        const bool want_norm = norm_out != nullptr && j0 + kk >= k;
         const TB *b = static_cast<const TB *>(basis) + 2 * j0 * stride;
         const double2 *c = coef + (int64_t)j0 * n;
+        MRHS_TIMED("k_lincomb", s);
         if (want_norm) {
             if (!sc) fail(MRHS_ERR_INVALID, "lincomb with norm needs scratch");
             sc->ensure(g.blocks, n);
             const size_t smem = sizeof(double2) * (size_t)g.rpb * n;
-            k_lincomb<TW, TB, true><<<g.blocks, g.threads, smem, s>>>(
+            k_lincomb<TW, TB, true, W><<<g.blocks, g.threads, smem, s>>>(
                 static_cast<TW *>(w), b, stride, kk, c, alpha, rows, n, g.rpb, sc->partials.as<double2>(),
                 sc->counter.as<unsigned int>(), norm_out);
         } else {
-            k_lincomb<TW, TB, false><<<g.blocks, g.threads, 0, s>>>(static_cast<TW *>(w), b, stride, kk, c, alpha,
-                                                                    rows, n, g.rpb, nullptr, nullptr, nullptr);
+            k_lincomb<TW, TB, false, W><<<g.blocks, g.threads, 0, s>>>(static_cast<TW *>(w), b, stride, kk, c,
+                                                                       alpha, rows, n, g.rpb, nullptr, nullptr,
+                                                                       nullptr);
         }
         MRHS_LAUNCHED("k_lincomb");
     }
@@ -529,22 +722,30 @@ void lincomb(mrhs_precision pw, void *w, mrhs_precision pb, const void *basis, i
         if (norm_out) norm2(pw, w, rows, n, norm_out, *sc, s);
         return;
     }
-    if (pw == MRHS_FP32 && pb == MRHS_FP32) lincomb_t<float, float>(w, basis, stride, k, coef, alpha, rows, n, s, norm_out, sc);
-    else if (pw == MRHS_FP64 && pb == MRHS_FP64) lincomb_t<double, double>(w, basis, stride, k, coef, alpha, rows, n, s, norm_out, sc);
-    else if (pw == MRHS_FP64 && pb == MRHS_FP32) lincomb_t<double, float>(w, basis, stride, k, coef, alpha, rows, n, s, norm_out, sc);
-    else fail(MRHS_ERR_INVALID, "lincomb: unsupported precision pair");
+    if (pw == MRHS_FP32 && pb == MRHS_FP32) {
+        const RedGeom g = red_geom(rows, n, pair_width(MRHS_FP32, n, {w, basis}, stride));
+        if (g.w == 2) lincomb_t<float, float, 2>(w, basis, stride, k, coef, alpha, g, rows, n, s, norm_out, sc);
+        else lincomb_t<float, float, 1>(w, basis, stride, k, coef, alpha, g, rows, n, s, norm_out, sc);
+    } else if (pw == MRHS_FP64 && pb == MRHS_FP64) {
+        lincomb_t<double, double, 1>(w, basis, stride, k, coef, alpha, red_geom(rows, n), rows, n, s, norm_out, sc);
+    } else if (pw == MRHS_FP64 && pb == MRHS_FP32) {
+        lincomb_t<double, float, 1>(w, basis, stride, k, coef, alpha, red_geom(rows, n), rows, n, s, norm_out, sc);
+    } else {
+        fail(MRHS_ERR_INVALID, "lincomb: unsupported precision pair");
+    }
 }
 
 void scale_inv_sqrt(mrhs_precision p, void *dst, const void *src, const double *nrm2, int64_t rows, int n,
                     cudaStream_t s) {
     check_n(n);
-    const RedGeom g = red_geom(rows, n);
-    if (p == MRHS_FP32)
-        k_scale_inv_sqrt<float><<<g.blocks, g.threads, 0, s>>>(static_cast<float *>(dst),
-                                                              static_cast<const float *>(src), nrm2, rows, n, g.rpb);
-    else
-        k_scale_inv_sqrt<double><<<g.blocks, g.threads, 0, s>>>(static_cast<double *>(dst),
-                                                               static_cast<const double *>(src), nrm2, rows, n, g.rpb);
+    const RedGeom g0 = red_geom(rows, n, pair_width(p, n, {dst, src}));
+    dispatch(p, g0.w, "scale_inv_sqrt", [&](auto tT, auto tW) {
+        RED_TYPES(tT, tW);
+        RedGeom g = g0;
+        fit_wave(g, k_scale_inv_sqrt<T, W>, 0);
+        k_scale_inv_sqrt<T, W><<<g.blocks, g.threads, 0, s>>>(static_cast<T *>(dst), static_cast<const T *>(src),
+                                                              nrm2, rows, n, g.rpb);
+    });
     MRHS_LAUNCHED("k_scale_inv_sqrt");
 }
 

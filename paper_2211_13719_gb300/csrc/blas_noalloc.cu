@@ -29,7 +29,8 @@ namespace {
 
 constexpr int NOALLOC_MAX_RHS = 64;
 constexpr int NOALLOC_MAX_BLOCKS = 512;
-constexpr size_t NOALLOC_PARTIALS = (size_t)NOALLOC_MAX_BLOCKS * KCHUNK * NOALLOC_MAX_RHS;  // 4 MiB of double2
+// per-block partials plus one total per group of 32 blocks: 4.1 MiB of double2
+constexpr size_t NOALLOC_PARTIALS = (size_t)(NOALLOC_MAX_BLOCKS + NOALLOC_MAX_BLOCKS / 32) * KCHUNK * NOALLOC_MAX_RHS;
 
 static __device__ __align__(256) double2 g_noalloc_partials[NOALLOC_PARTIALS];
 static __device__ __align__(256) unsigned int g_noalloc_counter[64];
@@ -81,7 +82,7 @@ extern "C" mrhs_status mrhs_blas_multi_dot_noalloc(const void *basis_dev, int k,
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         // the completion counter must start at zero (a previous call that failed
         // part-way could have left it set)
-        MRHS_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int), s));
+        MRHS_CUDA(cudaMemsetAsync(d.counter, 0, sizeof(unsigned int) * 64, s));
         multi_dot_fixed_scratch(prec, basis_dev, rows * nrhs, k, w_dev, rows, nrhs, static_cast<double2 *>(out_dev),
                                 d.partials, d.counter, NOALLOC_MAX_BLOCKS, s);
     } catch (const mrhs::Error &e) {

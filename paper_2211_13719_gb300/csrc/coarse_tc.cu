@@ -31,104 +31,21 @@
 // Every wait on an mbarrier is bounded; on expiry the kernel records an
 // error flag, drains its outstanding copies (bounded), frees its tensor
 // memory and returns.  The host reads the flag at the end of a solve.
-#include <cuda_fp16.h>
-
 #include <algorithm>
 
 #include "mg.cuh"
+#include "tc_common.cuh"
 
 namespace mrhs {
 
 namespace {
 
+using namespace tc;
+
 constexpr int NC = 64;                 // coarse dof handled by this kernel
 constexpr int MROWS = 128;             // 2 * NC real rows
 constexpr int STAGES = 3;
 constexpr int A_TILE = MROWS * NC * 2; // bytes of one BF16 link tile (16 KB)
-constexpr uint32_t SPIN_LIMIT = 1u << 20;
-
-__host__ __device__ __forceinline__ int npad_of(int n) { return ((2 * n + 15) / 16) * 16; }
-
-// byte offset of element (row, k) in a swizzled K-major tile of 64 BF16 columns
-__host__ __device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
-    const int atom = row >> 3, r = row & 7, chunk = k >> 3, within = k & 7;
-    return (uint32_t)(atom * 1024 + r * 128 + ((chunk ^ r) << 4) + within * 2);
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred P1;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
-        " selp.b32 %0, 1, 0, P1;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait; false on expiry
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < SPIN_LIMIT; ++i)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-
-// shared-memory matrix descriptor: 128B swizzle, K-major, 8-row atoms 1024 B apart
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);      // start address
-    // leading byte offset: unused for a swizzled K-major tile one atom wide (left 0)
-    d |= (uint64_t)(1024u >> 4) << 32;             // stride byte offset: next 8-row atom
-    d |= (uint64_t)1 << 46;                        // descriptor version
-    d |= (uint64_t)2 << 61;                        // 128-byte swizzle
-    return d;
-}
-
-// instruction descriptor: 16-bit A, B (fmt 0 = F16, 1 = BF16) -> FP32, both K-major, M x N
-__host__ __device__ __forceinline__ uint32_t idesc_16bit(int M, int N, uint32_t fmt) {
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-template <int FMT> __device__ __forceinline__ uint16_t to16(float v);
-template <> __device__ __forceinline__ uint16_t to16<0>(float v) { return __half_as_ushort(__float2half_rn(v)); }
-template <> __device__ __forceinline__ uint16_t to16<1>(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 struct TcArgs {
     int L[4];
@@ -208,7 +125,7 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ A
                 const uint32_t sa = sbase + s * stage_bytes, sb = sa + A_TILE;
 #pragma unroll
                 for (int kk = 0; kk < NC / 16; ++kk)
-                    mma_bf16(tmem, sdesc(sa + kk * 32), sdesc(sb + kk * 32), a.idesc, (e > 0 || kk > 0) ? 1u : 0u);
+                    mma_16bit(tmem, sdesc(sa + kk * 32), sdesc(sb + kk * 32), a.idesc, (e > 0 || kk > 0) ? 1u : 0u);
                 mma_commit(empty0 + 8 * s);
             }
         }
@@ -396,6 +313,7 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
         MRHS_CUDA(cudaFuncSetAttribute(k_coarse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(128)));
         attr = true;
     }
+    MRHS_TIMED("k_coarse_tc", s);
     k_coarse_tc<<<(unsigned)c.V, 128, smem, s>>>(c.Abf.as<uint8_t>(), c.PhiBf.as<uint8_t>(), out, y, a,
                                                   c.LinkScale.as<float>(), c.ColScale.as<float>(), c.TcErr.as<int>());
     MRHS_LAUNCHED("k_coarse_tc");

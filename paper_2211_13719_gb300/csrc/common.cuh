@@ -33,6 +33,21 @@ inline void cuda_check(cudaError_t e, const char *what) {
 void count_launches(uint64_t k);
 #define MRHS_LAUNCHED(name) (::mrhs::count_launches(1), ::mrhs::cuda_check(cudaGetLastError(), name))
 
+// Event timing of one kernel's launches for measurement harnesses
+// (mrhs_kernel_timer_start / _stop): declared just before a launch, the scope
+// records an event on the launching stream before the launch and another when
+// the scope closes, if that kernel is being timed and the stream is not being
+// captured into a graph (captured launches are only counted).
+struct KernelTimerScope {
+    int slot = -1;
+    cudaStream_t stream = nullptr;
+    KernelTimerScope(const char *name, cudaStream_t s);
+    ~KernelTimerScope();
+    KernelTimerScope(const KernelTimerScope &) = delete;
+    KernelTimerScope &operator=(const KernelTimerScope &) = delete;
+};
+#define MRHS_TIMED(name, stream) ::mrhs::KernelTimerScope mrhs_timer_scope_(name, stream)
+
 // -------------------------------------------------------- device buffers
 struct DeviceBuffer {
     void *ptr = nullptr;

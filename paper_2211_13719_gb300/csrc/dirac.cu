@@ -465,6 +465,7 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
     const unsigned blocks = (unsigned)((items + threads - 1) / threads);
     const float2 *U = lat.U32.as<float2>();
     const float2 *C = lat.C32.as<float2>();
+    MRHS_TIMED("k_dslash_x2", s);
     if (y)
         k_dslash_x2<true><<<blocks, threads, 0, s>>>(U, C, static_cast<const float2 *>(in), static_cast<float2 *>(out),
                                                      static_cast<const float2 *>(y), a);
@@ -491,6 +492,7 @@ static void launch_dslash(const mrhs_lattice &lat, const void *in, void *out, co
     const int64_t blocks = (items + threads - 1) / threads;
     const cplx<Real> *U = sizeof(Real) == 4 ? lat.U32.as<cplx<Real>>() : lat.U64.as<cplx<Real>>();
     const cplx<Real> *C = sizeof(Real) == 4 ? lat.C32.as<cplx<Real>>() : lat.C64.as<cplx<Real>>();
+    MRHS_TIMED("k_dslash", s);
     k_dslash<Real, TIn, R, RESID, GENERAL><<<(unsigned)blocks, threads, 0, s>>>(
         U, C, static_cast<const TIn *>(in), static_cast<Real *>(out), static_cast<const Real *>(y), a, mask);
     MRHS_LAUNCHED("k_dslash");

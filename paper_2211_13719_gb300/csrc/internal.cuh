@@ -55,8 +55,9 @@ void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const
                int64_t rows, int n, double2 *out, Scratch &sc, cudaStream_t s, bool accumulate = false);
 void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s);
 // multi_dot with caller-provided reduction scratch: `partials` holds at least
-// max_blocks * KCHUNK * n double2, `counter` must be zero on entry (the kernel
-// leaves it zero); the grid is capped at max_blocks.
+// (max_blocks + ceil(max_blocks / 32)) * KCHUNK * n double2, `counter` holds
+// 64 unsigned ints that are zero on entry (the kernel leaves them zero);
+// the grid is capped at max_blocks (at most 2016).
 void multi_dot_fixed_scratch(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w, int64_t rows,
                              int n, double2 *out, double2 *partials, unsigned int *counter, int max_blocks,
                              cudaStream_t s);

@@ -29,6 +29,12 @@ struct Level {
     DeviceBuffer LinkScale;  // float [V]: per-site scale of the 16-bit links
     DeviceBuffer ColScale;   // float [64]: per-RHS scale of the packed input (max |component|)
     int tc_fmt = 0;          // MRHS_FP16 or MRHS_BF16 when the 16-bit links exist
+    // tensor-core transfer to the next level (16-bit hierarchies): packed P tiles
+    DeviceBuffer PA;         // prolongation A tiles [Vc][2][tiles] 128 x 64 FP16
+    DeviceBuffer RB;         // restriction B tiles [Vc][2][chunks] 64 x 64 FP16
+    DeviceBuffer IgErr;      // int: set when a tensor-core transfer gave up waiting
+    DeviceBuffer IgBound;    // float [2][64]: ones (unit-norm inputs), then the column maxima of the last input
+    bool tc_intergrid = false;
     int64_t rows() const { return V * dof; }
 };
 
@@ -54,6 +60,14 @@ bool coarse_bf16_supported(const Level &c);
 // nonzero if a tensor-core stencil launch on this level gave up waiting (reads device memory)
 int coarse_tc_error(const Level &c);
 void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s);
+// tensor-core restriction / prolongation (FP16, <= 32 null vectors, <= 64 RHS)
+bool intergrid_tc_supported(const Level &f);
+void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s);
+// unit_norm: every RHS column of `fine` has norm <= 1 (its components are then bounded by 1)
+void restrict_fields_tc(const Level &f, const Level &c, const float2 *fine, float2 *coarse, int n, int64_t ostride,
+                        bool unit_norm, cudaStream_t s);
+void prolong_fields_tc(const Level &f, const Level &c, const float2 *coarse, float2 *fine, int n, cudaStream_t s);
+int intergrid_tc_error(const Level &f);
 // FP64 modified Gram-Schmidt (twice) of the chiral halves of `vecs` per aggregate, in place
 void block_orthonormalize(const Level &f, double2 *vecs, cudaStream_t s);
 // P [V][dof][N] -> Pexp [V][dof][2N] with column K = chi*N + k nonzero only on chirality chi

@@ -244,7 +244,9 @@ struct EventTimer {
     }
 };
 
-void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t s);
+// unit_norm: every RHS column of v has norm <= 1 (true for the Arnoldi vectors
+// the preconditioned Krylov cycles pass in)
+void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t s, bool unit_norm = true);
 
 struct VcyclePrecond : Precond {
     mrhs_mg *mg;
@@ -253,14 +255,15 @@ struct VcyclePrecond : Precond {
     void apply(const float2 *v, float2 *z, int n, cudaStream_t s) override { vcycle(*mg, level, v, z, n, s); }
 };
 
-void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t s) {
+void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t s, bool unit_norm) {
     Level &F = mg.lev[l];
     Level &Cl = mg.lev[l + 1];
     LevelWork &WC = mg.work[l + 1];
     const bool prof = mg.profile && l == 0;
     {
         EventTimer t(prof, s, &mg.t_restrict);
-        restrict_fields(F, Cl, v, WC.rhs.as<float2>(), n, (int64_t)Cl.dof * n, s);
+        if (F.tc_intergrid) restrict_fields_tc(F, Cl, v, WC.rhs.as<float2>(), n, (int64_t)Cl.dof * n, unit_norm, s);
+        else restrict_fields(F, Cl, v, WC.rhs.as<float2>(), n, (int64_t)Cl.dof * n, s);
     }
     {
         EventTimer t(prof, s, &mg.t_coarse);
@@ -276,7 +279,8 @@ void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t 
     }
     {
         EventTimer t(prof, s, &mg.t_prolong);
-        prolong_fields(F, Cl, WC.sol.as<float2>(), z, n, s);
+        if (F.tc_intergrid) prolong_fields_tc(F, Cl, WC.sol.as<float2>(), z, n, s);
+        else prolong_fields(F, Cl, WC.sol.as<float2>(), z, n, s);
     }
     {
         EventTimer t(prof, s, &mg.t_fine);
@@ -489,9 +493,25 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
     for (int r = 0; r < n; ++r) target[r] = 0.5 * tols[r] * std::sqrt(bn2[r]);
     const int cap = max_outer > 0 ? max_outer : mg.p.max_outer_iters;
     bool converged = false;
+    // a zero start vector (the usual cold start) makes the first residual b itself:
+    // skip that FP64 operator application
+    bool x_zero = false;
+    {
+        norm2(MRHS_FP64, x, rows, n, mg.oks.hn2.as<double>(), mg.osc, s);
+        MRHS_CUDA(cudaMemcpyAsync(hres, mg.oks.hn2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        MRHS_CUDA(cudaStreamSynchronize(s));
+        x_zero = true;
+        for (int r = 0; r < n; ++r)
+            if (hres[r] != 0.0) x_zero = false;
+    }
     while (true) {
         // true residual in FP64
-        dslash(lat, MRHS_FP64, MRHS_FP64, x, V0, b, n, s);
+        if (x_zero) {
+            MRHS_CUDA(cudaMemcpyAsync(V0, b, sizeof(double2) * F, cudaMemcpyDeviceToDevice, s));
+            x_zero = false;
+        } else {
+            dslash(lat, MRHS_FP64, MRHS_FP64, x, V0, b, n, s);
+        }
         norm2(MRHS_FP64, V0, rows, n, mg.oks.beta2.as<double>(), mg.osc, s);
         MRHS_CUDA(cudaMemcpyAsync(hres, mg.oks.beta2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
         MRHS_CUDA(cudaStreamSynchronize(s));
@@ -533,6 +553,13 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
         }
         krylov_solve(mg.oks, steps, n, s);
         lincomb(MRHS_FP64, x, MRHS_FP32, Z0, F, steps, mg.oks.y.as<double2>(), 1.0, rows, n, s);
+    }
+    for (int l = 0; l + 1 < mg.nlev; ++l) {
+        if (intergrid_tc_error(mg.lev[l])) {
+            MRHS_CUDA(cudaMemsetAsync(mg.lev[l].IgErr.ptr, 0, sizeof(int), s));
+            MRHS_CUDA(cudaStreamSynchronize(s));
+            fail(MRHS_ERR_TIMEOUT, "tensor-core restriction / prolongation gave up waiting");
+        }
     }
     for (int l = 1; l < mg.nlev; ++l) {
         if (coarse_tc_error(mg.lev[l])) {
@@ -618,15 +645,15 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->setup_sweeps = 6;
     p->setup_m = 8;
     p->smooth_m = 4;
-    p->coarse_m = 16;
-    p->coarse_cycles = 2;
-    p->inter_m = 8;
+    p->coarse_m = 12;
+    p->coarse_cycles = 1;
+    p->inter_m = 3;
     p->inner_m = 8;
     p->inner_max_iters = 200;
     p->inner_tol = 1e-5;
     p->outer_m = 4;
     p->max_outer_iters = 30;
-    p->coarse_precision = MRHS_FP32;
+    p->coarse_precision = MRHS_FP16;
     p->max_rhs = 48;
     p->use_graph = 1;
     p->seed = 1234;
@@ -673,6 +700,13 @@ mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_
             const bool use_tc = (params->coarse_precision == MRHS_BF16 || params->coarse_precision == MRHS_FP16) &&
                                 coarse_bf16_supported(C);
             if (use_tc) coarse_links_to_16bit(C, (mrhs_precision)params->coarse_precision, s);
+            // 16-bit hierarchies also move fields between levels on the tensor cores
+            Level &F = mg->lev[l];
+            if ((params->coarse_precision == MRHS_BF16 || params->coarse_precision == MRHS_FP16) &&
+                intergrid_tc_supported(F)) {
+                intergrid_tc_prepare(F, C, s);
+                F.tc_intergrid = true;
+            }
             mg->ops.emplace_back(new CoarseOp(&C, use_tc));
         }
         MRHS_CUDA(cudaStreamSynchronize(s));
@@ -746,8 +780,13 @@ mrhs_status mrhs_restrict(mrhs_mg *mg, int level, const void *fine_dev, void *co
     if (!fine_dev || !coarse_dev) fail(MRHS_ERR_INVALID, "fields must be non-null");
     DevGuard dg(mg->lat->device);
     const Level &C = mg->lev[level + 1];
-    restrict_fields(mg->lev[level], C, static_cast<const float2 *>(fine_dev), static_cast<float2 *>(coarse_dev), nrhs,
-                    (int64_t)C.dof * nrhs, static_cast<cudaStream_t>(stream));
+    const Level &F = mg->lev[level];
+    if (F.tc_intergrid)
+        restrict_fields_tc(F, C, static_cast<const float2 *>(fine_dev), static_cast<float2 *>(coarse_dev), nrhs,
+                           (int64_t)C.dof * nrhs, false, static_cast<cudaStream_t>(stream));
+    else
+        restrict_fields(F, C, static_cast<const float2 *>(fine_dev), static_cast<float2 *>(coarse_dev), nrhs,
+                        (int64_t)C.dof * nrhs, static_cast<cudaStream_t>(stream));
     return ok();
     API_CATCH
 }
@@ -758,8 +797,12 @@ mrhs_status mrhs_prolong(mrhs_mg *mg, int level, const void *coarse_dev, void *f
     check_n(mg, nrhs);
     if (!fine_dev || !coarse_dev) fail(MRHS_ERR_INVALID, "fields must be non-null");
     DevGuard dg(mg->lat->device);
-    prolong_fields(mg->lev[level], mg->lev[level + 1], static_cast<const float2 *>(coarse_dev),
-                   static_cast<float2 *>(fine_dev), nrhs, static_cast<cudaStream_t>(stream));
+    if (mg->lev[level].tc_intergrid)
+        prolong_fields_tc(mg->lev[level], mg->lev[level + 1], static_cast<const float2 *>(coarse_dev),
+                          static_cast<float2 *>(fine_dev), nrhs, static_cast<cudaStream_t>(stream));
+    else
+        prolong_fields(mg->lev[level], mg->lev[level + 1], static_cast<const float2 *>(coarse_dev),
+                       static_cast<float2 *>(fine_dev), nrhs, static_cast<cudaStream_t>(stream));
     return ok();
     API_CATCH
 }
@@ -793,7 +836,7 @@ mrhs_status mrhs_vcycle(mrhs_mg *mg, const void *v_dev, void *z_dev, int nrhs, v
     if (!v_dev || !z_dev || v_dev == z_dev) fail(MRHS_ERR_INVALID, "distinct non-null fields required");
     DevGuard dg(mg->lat->device);
     vcycle(*mg, 0, static_cast<const float2 *>(v_dev), static_cast<float2 *>(z_dev), nrhs,
-           static_cast<cudaStream_t>(stream));
+           static_cast<cudaStream_t>(stream), false);
     return ok();
     API_CATCH
 }

@@ -105,6 +105,8 @@ _D = C.c_double
 PROTOTYPES = {
     "mrhs_last_error": (C.c_char_p, []),
     "mrhs_kernel_launch_count": (C.c_uint64, []),
+    "mrhs_kernel_timer_start": (_I, [C.c_char_p]),
+    "mrhs_kernel_timer_stop": (_I, [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mrhs_create_lattice": (_I, [C.POINTER(C.c_int), _I, _I, C.POINTER(_P)]),
     "mrhs_destroy_lattice": (None, [_P]),
     "mrhs_load_gauge": (_I, [_P, _P]),
@@ -181,6 +183,17 @@ def _stream(s):
 
 def mrhs_kernel_launch_count() -> int:
     return int(lib().mrhs_kernel_launch_count())
+
+
+def mrhs_kernel_timer_start(kernel_name: str):
+    _check(lib().mrhs_kernel_timer_start(kernel_name.encode()))
+
+
+def mrhs_kernel_timer_stop():
+    """(summed event milliseconds, timed launches, graph-captured launches)"""
+    ms, timed, captured = C.c_double(), C.c_int64(), C.c_int64()
+    _check(lib().mrhs_kernel_timer_stop(C.byref(ms), C.byref(timed), C.byref(captured)))
+    return ms.value, timed.value, captured.value
 
 
 # ------------------------------------------------------------------ lattice

@@ -53,4 +53,13 @@ def test_default_params_are_sane(lib):
     p = mrhs.mrhs_mg_default_params()
     assert p.n_levels in (2, 3)
     assert p.n_vec[0] >= 1 and p.outer_m >= 1 and p.max_rhs >= 1
-    assert p.coarse_precision in (mrhs.MRHS_FP32, mrhs.MRHS_BF16)
+    assert p.coarse_precision in (mrhs.MRHS_FP32, mrhs.MRHS_FP16, mrhs.MRHS_BF16)
+
+
+def test_kernel_timer_state_without_gpu(lib):
+    # start / stop with nothing launched needs no GPU; a second start is refused
+    assert lib.mrhs_kernel_timer_stop(None, None, None) == mrhs.MRHS_ERR_INVALID
+    assert lib.mrhs_kernel_timer_start(None) == mrhs.MRHS_ERR_INVALID
+    mrhs.mrhs_kernel_timer_start("k_dslash_x2")
+    assert lib.mrhs_kernel_timer_start(b"k_dots_norm") == mrhs.MRHS_ERR_INVALID
+    assert mrhs.mrhs_kernel_timer_stop() == (0.0, 0, 0)
