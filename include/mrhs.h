@@ -66,7 +66,11 @@ typedef enum {
     MRHS_FP32 = 0,
     MRHS_FP64 = 1,
     MRHS_BF16 = 2,
-    MRHS_FP16 = 3
+    MRHS_FP16 = 3,
+    /* float-float: each real carried as an unevaluated sum of two floats
+     * (48 significant bits), evaluated on the FP32 units; only for the fine
+     * operator, which then reads an FP32 field and writes an FP64 field */
+    MRHS_DF64 = 4
 } mrhs_precision;
 
 typedef struct mrhs_lattice mrhs_lattice;
@@ -125,7 +129,9 @@ mrhs_status mrhs_build_clover(mrhs_lattice *lat, double mass, double csw);
 mrhs_status mrhs_get_clover(mrhs_lattice *lat, double *clover_host);
 
 /* out_dev = D in_dev for nrhs >= 1 RHS (Sec. 4: hopping + clover fused),
- * both [V][12][nrhs] complex in precision `prec` (MRHS_FP32 or MRHS_FP64).
+ * both [V][12][nrhs] complex in precision `prec` (MRHS_FP32 or MRHS_FP64);
+ * with MRHS_DF64 in_dev is FP32 and out_dev FP64, computed in float-float
+ * arithmetic (within about 2^-48 of the largest term of each sum).
  * in and out must not overlap. */
 mrhs_status mrhs_apply_D(mrhs_lattice *lat, const void *in_dev, void *out_dev,
                          int nrhs, mrhs_precision prec, void *stream);
@@ -192,6 +198,9 @@ typedef struct {
     int coarse_precision;                  /* MRHS_FP32, MRHS_FP16 or MRHS_BF16   */
     int max_rhs;                           /* largest nrhs a solve may use        */
     int use_graph;                         /* replay the V-cycle as a CUDA graph  */
+    int outer_op_precision;                /* outer Arnoldi applies D z: MRHS_DF64
+                                              (float-float) or MRHS_FP64; the
+                                              true residual is always FP64        */
     uint64_t seed;                         /* start vectors when none supplied    */
     /* Optional host start vectors per level, [V_l][dof_l][n_vec[l]] complex
      * FP64 (dof_0 = 12, dof_l = nc of level l).  NULL entries: random. */

@@ -73,9 +73,10 @@ static RedGeom red_geom(int64_t rows, int n, int w = 1) {
     const int target = w == 2 ? 128 : 256;
     r.rpb = nw >= target ? 1 : target / nw;
     r.threads = nw * r.rpb;
-    // at least 32 rows per thread; at most 4 blocks of 256 (8 of 128) threads per
-    // SM: enough loads in flight for HBM on large fields, few partials on small ones
-    const int64_t need = (rows + 32 * r.rpb - 1) / (32 * r.rpb);
+    // at least 4 rows per thread, at most one wave of resident blocks (fit_wave):
+    // large fields run one full wave, small ones spread over many blocks so that
+    // no thread walks a long chain of dependent row loads
+    const int64_t need = (rows + 4 * r.rpb - 1) / (4 * r.rpb);
     const int64_t cap = (int64_t)current_sms() * (w == 2 ? 8 : 4);
     r.blocks = (int)std::max<int64_t>(1, std::min(need, cap));
     return r;
@@ -144,6 +145,16 @@ template <int W, typename T> __device__ __forceinline__ void stw(T *p, int64_t e
         *reinterpret_cast<float4 *>(p + 2 * e) = make_float4(x[0].re, x[0].im, x[1].re, x[1].im);
     } else {
         stv(p, e, x[0]);
+    }
+}
+
+// as ldw, zeros when !ok (the second row of a pair past the end)
+template <int W, typename T> __device__ __forceinline__ void ldw_if(const T *p, int64_t e, bool ok, cplx<T> (&x)[W]) {
+    if (ok) {
+        ldw<W>(p, e, x);
+    } else {
+#pragma unroll
+        for (int v = 0; v < W; ++v) x[v] = {0, 0};
     }
 }
 
@@ -254,37 +265,63 @@ __device__ void block_finish(double2 *smem, const double2 *vals, int cols, int n
     const int rsub = (int)(threadIdx.x / nw);   \
     const int64_t step = (int64_t)gridDim.x * rpb
 
-// out[j][r] = sum_i conj(b_j[i][r]) w[i][r], j < k <= KCHUNK
-template <typename T, int W>
+// Kernels with a basis loop take KM, a compile-time bound on the number k of
+// basis vectors (KM in {1, 2, 4, 8}, the smallest >= k): the unrolled loop then
+// issues no work for the slots j >= k, which matters at GB300's FP64 rate.
+// U = 2 walks a thread's rows two at a time into two partial sums (independent
+// FMA chains, added in a fixed order at the end); used where the FMA latency
+// chain, not memory, would bound the kernel (FP64, and FP32 with KM <= 2).
+
+// out[j][r] = sum_i conj(b_j[i][r]) w[i][r], j < k <= KM
+template <typename T, int W, int KM, int U>
 __global__ void k_multi_dot(const T *__restrict__ basis, int64_t stride, int k, const T *__restrict__ w,
                             int64_t rows, int n, int rpb, double2 *partials, unsigned int *counter,
                             double2 *out, int accumulate) {
     extern __shared__ double2 smem[];
     RED_THREAD_GEOMETRY;
-    cplx<T> acc[KCHUNK][W];
+    cplx<T> acc[U][KM][W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j)
+    for (int h = 0; h < U; ++h)
 #pragma unroll
-        for (int v = 0; v < W; ++v) acc[j][v] = {0, 0};
-    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
-        const int64_t e = row * n + col;
-        cplx<T> x[W];
-        ldw<W>(w, e, x);
+        for (int j = 0; j < KM; ++j)
 #pragma unroll
-        for (int j = 0; j < KCHUNK; ++j) {
+            for (int v = 0; v < W; ++v) acc[h][j][v] = {0, 0};
+    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += U * step) {
+        cplx<T> x[U][W];
+        int64_t e[U];
+        bool ok[U];
+#pragma unroll
+        for (int h = 0; h < U; ++h) {
+            e[h] = (row + h * step) * n + col;
+            ok[h] = h == 0 || row + h * step < rows;
+            ldw_if<W>(w, e[h], ok[h], x[h]);
+        }
+#pragma unroll
+        for (int j = 0; j < KM; ++j) {
             if (j < k) {
-                cplx<T> b[W];
-                ldw<W>(basis + 2 * j * stride, e, b);
 #pragma unroll
-                for (int v = 0; v < W; ++v) cmac_conj(acc[j][v], b[v], x[v]);
+                for (int h = 0; h < U; ++h) {
+                    cplx<T> b[W];
+                    ldw_if<W>(basis + 2 * j * stride, e[h], ok[h], b);
+#pragma unroll
+                    for (int v = 0; v < W; ++v) cmac_conj(acc[h][j][v], b[v], x[h][v]);
+                }
             }
         }
     }
-    double2 vals[KCHUNK * W];
+    double2 vals[KM * W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j)
+    for (int j = 0; j < KM; ++j)
 #pragma unroll
-        for (int v = 0; v < W; ++v) vals[j * W + v] = make_double2((double)acc[j][v].re, (double)acc[j][v].im);
+        for (int v = 0; v < W; ++v) {
+            double re = 0.0, im = 0.0;
+#pragma unroll
+            for (int h = 0; h < U; ++h) {
+                re += (double)acc[h][j][v].re;
+                im += (double)acc[h][j][v].im;
+            }
+            vals[j * W + v] = make_double2(re, im);
+        }
     block_finish<W>(smem, vals, k, n, rpb, col, rsub, partials, counter,
                     FinishOut{out, accumulate != 0, false, nullptr, false});
 }
@@ -294,26 +331,29 @@ __global__ void k_norm2(const T *__restrict__ w, int64_t rows, int n, int rpb, d
                         unsigned int *counter, double *out) {
     extern __shared__ double2 smem[];
     RED_THREAD_GEOMETRY;
-    T acc[W];
+    T acc[2][W];
 #pragma unroll
-    for (int v = 0; v < W; ++v) acc[v] = 0;
-    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
-        cplx<T> x[W];
-        ldw<W>(w, row * n + col, x);
+    for (int v = 0; v < W; ++v) acc[0][v] = acc[1][v] = 0;
+    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += 2 * step) {
+        cplx<T> x0[W], x1[W];
+        ldw<W>(w, row * n + col, x0);
+        ldw_if<W>(w, (row + step) * n + col, row + step < rows, x1);
 #pragma unroll
         for (int v = 0; v < W; ++v) {
-            acc[v] = fmadd(x[v].re, x[v].re, acc[v]);
-            acc[v] = fmadd(x[v].im, x[v].im, acc[v]);
+            acc[0][v] = fmadd(x0[v].re, x0[v].re, acc[0][v]);
+            acc[0][v] = fmadd(x0[v].im, x0[v].im, acc[0][v]);
+            acc[1][v] = fmadd(x1[v].re, x1[v].re, acc[1][v]);
+            acc[1][v] = fmadd(x1[v].im, x1[v].im, acc[1][v]);
         }
     }
     double2 vals[W];
 #pragma unroll
-    for (int v = 0; v < W; ++v) vals[v] = make_double2((double)acc[v], 0.0);
+    for (int v = 0; v < W; ++v) vals[v] = make_double2((double)acc[0][v] + (double)acc[1][v], 0.0);
     block_finish<W>(smem, vals, 1, n, rpb, col, rsub, partials, counter, FinishOut{nullptr, false, true, out, false});
 }
 
-// w += alpha * sum_j coef[j][r] b_j ; optional ||w||^2 per RHS
-template <typename TW, typename TB, bool NORM, int W>
+// w += alpha * sum_j coef[j][r] b_j (k <= KM) ; optional ||w||^2 per RHS
+template <typename TW, typename TB, bool NORM, int W, int KM>
 __global__ void k_lincomb(TW *__restrict__ w, const TB *__restrict__ basis, int64_t stride, int k,
                           const double2 *__restrict__ coef, double alpha, int64_t rows, int n, int rpb,
                           double2 *partials, unsigned int *counter, double *norm_out) {
@@ -321,9 +361,9 @@ __global__ void k_lincomb(TW *__restrict__ w, const TB *__restrict__ basis, int6
     // coefficients of this thread's columns, scaled by alpha, in the basis precision
     using TC = typename std::conditional<sizeof(TW) == 8 || sizeof(TB) == 8, double, float>::type;
     RED_THREAD_GEOMETRY;
-    cplx<TC> cf[KCHUNK][W];
+    cplx<TC> cf[KM][W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j) {
+    for (int j = 0; j < KM; ++j) {
 #pragma unroll
         for (int v = 0; v < W; ++v) {
             if (j < k) {
@@ -334,40 +374,46 @@ __global__ void k_lincomb(TW *__restrict__ w, const TB *__restrict__ basis, int6
             }
         }
     }
-    TW nacc[W];
+    // rows two at a time: independent work per row, two norm accumulators
+    TW nacc[2][W];
 #pragma unroll
-    for (int v = 0; v < W; ++v) nacc[v] = 0;
-    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
-        const int64_t e = row * n + col;
-        cplx<TC> s[W];
+    for (int v = 0; v < W; ++v) nacc[0][v] = nacc[1][v] = 0;
+    for (int64_t row0 = (int64_t)blockIdx.x * rpb + rsub; row0 < rows; row0 += 2 * step) {
 #pragma unroll
-        for (int v = 0; v < W; ++v) s[v] = {0, 0};
+        for (int h = 0; h < 2; ++h) {
+            const int64_t row = row0 + h * step;
+            if (h == 1 && row >= rows) break;
+            const int64_t e = row * n + col;
+            cplx<TC> s[W];
 #pragma unroll
-        for (int j = 0; j < KCHUNK; ++j) {
-            if (j < k) {
-                cplx<TB> b[W];
-                ldw<W>(basis + 2 * j * stride, e, b);
+            for (int v = 0; v < W; ++v) s[v] = {0, 0};
 #pragma unroll
-                for (int v = 0; v < W; ++v) cmac(s[v], cf[j][v], cplx<TC>{(TC)b[v].re, (TC)b[v].im});
+            for (int j = 0; j < KM; ++j) {
+                if (j < k) {
+                    cplx<TB> b[W];
+                    ldw<W>(basis + 2 * j * stride, e, b);
+#pragma unroll
+                    for (int v = 0; v < W; ++v) cmac(s[v], cf[j][v], cplx<TC>{(TC)b[v].re, (TC)b[v].im});
+                }
             }
-        }
-        cplx<TW> x[W];
-        ldw<W>(w, e, x);
+            cplx<TW> x[W];
+            ldw<W>(w, e, x);
 #pragma unroll
-        for (int v = 0; v < W; ++v) {
-            x[v].re += (TW)s[v].re;
-            x[v].im += (TW)s[v].im;
-            if (NORM) {
-                nacc[v] = fmadd(x[v].re, x[v].re, nacc[v]);
-                nacc[v] = fmadd(x[v].im, x[v].im, nacc[v]);
+            for (int v = 0; v < W; ++v) {
+                x[v].re += (TW)s[v].re;
+                x[v].im += (TW)s[v].im;
+                if (NORM) {
+                    nacc[h][v] = fmadd(x[v].re, x[v].re, nacc[h][v]);
+                    nacc[h][v] = fmadd(x[v].im, x[v].im, nacc[h][v]);
+                }
             }
+            stw<W>(w, e, x);
         }
-        stw<W>(w, e, x);
     }
     if (NORM) {
         double2 vals[W];
 #pragma unroll
-        for (int v = 0; v < W; ++v) vals[v] = make_double2((double)nacc[v], 0.0);
+        for (int v = 0; v < W; ++v) vals[v] = make_double2((double)nacc[0][v] + (double)nacc[1][v], 0.0);
         block_finish<W>(smem, vals, 1, n, rpb, col, rsub, partials, counter,
                         FinishOut{nullptr, false, true, norm_out, false});
     }
@@ -412,61 +458,85 @@ __global__ void k_axpy(T a, const T *x, T *y, int64_t count) {
     stv(y, i, v);
 }
 
-// out[j][r] = <b_j, w>_r for j < k (k < KCHUNK) and nrm2[r] = ||w_r||^2, one pass over w
-template <typename T, int W>
+// out[j][r] = <b_j, w>_r for j < k (k <= KM, k < KCHUNK) and nrm2[r] = ||w_r||^2, one pass over w
+template <typename T, int W, int KM, int U>
 __global__ void k_dots_norm(const T *__restrict__ basis, int64_t stride, int k, const T *__restrict__ w,
                             int64_t rows, int n, int rpb, double2 *partials, unsigned int *counter, double2 *out,
                             double *nrm2) {
     extern __shared__ double2 smem[];
     RED_THREAD_GEOMETRY;
-    cplx<T> acc[KCHUNK][W];
-    T nacc[W];
+    cplx<T> acc[U][KM][W];
+    T nacc[U][W];
 #pragma unroll
-    for (int v = 0; v < W; ++v) {
-        nacc[v] = 0;
-#pragma unroll
-        for (int j = 0; j < KCHUNK; ++j) acc[j][v] = {0, 0};
-    }
-    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
-        const int64_t e = row * n + col;
-        cplx<T> x[W];
-        ldw<W>(w, e, x);
+    for (int h = 0; h < U; ++h)
 #pragma unroll
         for (int v = 0; v < W; ++v) {
-            nacc[v] = fmadd(x[v].re, x[v].re, nacc[v]);
-            nacc[v] = fmadd(x[v].im, x[v].im, nacc[v]);
+            nacc[h][v] = 0;
+#pragma unroll
+            for (int j = 0; j < KM; ++j) acc[h][j][v] = {0, 0};
+        }
+    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += U * step) {
+        cplx<T> x[U][W];
+        int64_t e[U];
+        bool ok[U];
+#pragma unroll
+        for (int h = 0; h < U; ++h) {
+            e[h] = (row + h * step) * n + col;
+            ok[h] = h == 0 || row + h * step < rows;
+            ldw_if<W>(w, e[h], ok[h], x[h]);
+#pragma unroll
+            for (int v = 0; v < W; ++v) {
+                nacc[h][v] = fmadd(x[h][v].re, x[h][v].re, nacc[h][v]);
+                nacc[h][v] = fmadd(x[h][v].im, x[h][v].im, nacc[h][v]);
+            }
         }
 #pragma unroll
-        for (int j = 0; j < KCHUNK - 1; ++j) {
+        for (int j = 0; j < KM; ++j) {
             if (j < k) {
-                cplx<T> b[W];
-                ldw<W>(basis + 2 * j * stride, e, b);
 #pragma unroll
-                for (int v = 0; v < W; ++v) cmac_conj(acc[j][v], b[v], x[v]);
+                for (int h = 0; h < U; ++h) {
+                    cplx<T> b[W];
+                    ldw_if<W>(basis + 2 * j * stride, e[h], ok[h], b);
+#pragma unroll
+                    for (int v = 0; v < W; ++v) cmac_conj(acc[h][j][v], b[v], x[h][v]);
+                }
             }
         }
     }
-    double2 vals[KCHUNK * W];
+    double2 vals[(KM + 1) * W];
 #pragma unroll
-    for (int j = 0; j < KCHUNK; ++j)
+    for (int j = 0; j < KM; ++j)
 #pragma unroll
-        for (int v = 0; v < W; ++v) vals[j * W + v] = make_double2((double)acc[j][v].re, (double)acc[j][v].im);
+        for (int v = 0; v < W; ++v) {
+            double re = 0.0, im = 0.0;
 #pragma unroll
-    for (int v = 0; v < W; ++v) vals[k * W + v] = make_double2((double)nacc[v], 0.0);
+            for (int h = 0; h < U; ++h) {
+                re += (double)acc[h][j][v].re;
+                im += (double)acc[h][j][v].im;
+            }
+            vals[j * W + v] = make_double2(re, im);
+        }
+#pragma unroll
+    for (int v = 0; v < W; ++v) {
+        double q = 0.0;
+#pragma unroll
+        for (int h = 0; h < U; ++h) q += (double)nacc[h][v];
+        vals[k * W + v] = make_double2(q, 0.0);
+    }
     block_finish<W>(smem, vals, k + 1, n, rpb, col, rsub, partials, counter, FinishOut{out, false, false, nrm2, true});
 }
 
 // w <- (w - sum_{j<k} h_j b_j) / beta with beta^2 = max(||w||^2 - sum_{all j<kall} |h_j|^2, 1e-6 ||w||^2)
 // (Pythagoras for an orthonormal basis); writes beta^2 to hn2 and ||w_new||^2 to nn.
 // `coef` points at the first of the k coefficients handled here, `hall` at all kall of them.
-template <typename T, int W>
+template <typename T, int W, int KM>
 __global__ void k_lincomb_scale(T *__restrict__ w, const T *__restrict__ basis, int64_t stride, int k,
                                 const double2 *__restrict__ coef, const double2 *__restrict__ hall, int kall,
                                 const double *__restrict__ nrm2, double *__restrict__ hn2, int64_t rows, int n,
                                 int rpb, double2 *partials, unsigned int *counter, double *nn) {
     extern __shared__ double2 smem[];
     RED_THREAD_GEOMETRY;
-    cplx<T> cf[KCHUNK][W];
+    cplx<T> cf[KM][W];
     T f[W];
 #pragma unroll
     for (int v = 0; v < W; ++v) {
@@ -480,7 +550,7 @@ __global__ void k_lincomb_scale(T *__restrict__ w, const T *__restrict__ basis, 
         f[v] = (T)(b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0);
         if (blockIdx.x == 0 && rsub == 0) hn2[col + v] = b2;
 #pragma unroll
-        for (int j = 0; j < KCHUNK; ++j) {
+        for (int j = 0; j < KM; ++j) {
             if (j < k) {
                 const double2 c = coef[(int64_t)j * n + col + v];
                 cf[j][v] = {(T)(-c.x), (T)(-c.y)};
@@ -489,34 +559,40 @@ __global__ void k_lincomb_scale(T *__restrict__ w, const T *__restrict__ basis, 
             }
         }
     }
-    T nacc[W];
+    // rows two at a time: two independent norm accumulators
+    T nacc[2][W];
 #pragma unroll
-    for (int v = 0; v < W; ++v) nacc[v] = 0;
-    for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += step) {
-        const int64_t e = row * n + col;
-        cplx<T> x[W];
-        ldw<W>(w, e, x);
+    for (int v = 0; v < W; ++v) nacc[0][v] = nacc[1][v] = 0;
+    for (int64_t row0 = (int64_t)blockIdx.x * rpb + rsub; row0 < rows; row0 += 2 * step) {
 #pragma unroll
-        for (int j = 0; j < KCHUNK; ++j) {
-            if (j < k) {
-                cplx<T> b[W];
-                ldw<W>(basis + 2 * j * stride, e, b);
+        for (int h = 0; h < 2; ++h) {
+            const int64_t row = row0 + h * step;
+            if (h == 1 && row >= rows) break;
+            const int64_t e = row * n + col;
+            cplx<T> x[W];
+            ldw<W>(w, e, x);
 #pragma unroll
-                for (int v = 0; v < W; ++v) cmac(x[v], cf[j][v], b[v]);
+            for (int j = 0; j < KM; ++j) {
+                if (j < k) {
+                    cplx<T> b[W];
+                    ldw<W>(basis + 2 * j * stride, e, b);
+#pragma unroll
+                    for (int v = 0; v < W; ++v) cmac(x[v], cf[j][v], b[v]);
+                }
             }
-        }
 #pragma unroll
-        for (int v = 0; v < W; ++v) {
-            x[v].re *= f[v];
-            x[v].im *= f[v];
-            nacc[v] = fmadd(x[v].re, x[v].re, nacc[v]);
-            nacc[v] = fmadd(x[v].im, x[v].im, nacc[v]);
+            for (int v = 0; v < W; ++v) {
+                x[v].re *= f[v];
+                x[v].im *= f[v];
+                nacc[h][v] = fmadd(x[v].re, x[v].re, nacc[h][v]);
+                nacc[h][v] = fmadd(x[v].im, x[v].im, nacc[h][v]);
+            }
+            stw<W>(w, e, x);
         }
-        stw<W>(w, e, x);
     }
     double2 vals[W];
 #pragma unroll
-    for (int v = 0; v < W; ++v) vals[v] = make_double2((double)nacc[v], 0.0);
+    for (int v = 0; v < W; ++v) vals[v] = make_double2((double)nacc[0][v] + (double)nacc[1][v], 0.0);
     block_finish<W>(smem, vals, 1, n, rpb, col, rsub, partials, counter, FinishOut{nullptr, false, true, nn, false});
 }
 
@@ -567,6 +643,16 @@ template <typename F> static void dispatch(mrhs_precision p, int w, const char *
     using T = decltype(tT);        \
     constexpr int W = decltype(tW)::value
 
+// calls f(integral_constant<KM>) with KM in {1, 2, 4, 8}, the smallest >= k
+template <typename F> static void with_kmax(int k, F &&f) {
+    if (k <= 1) f(std::integral_constant<int, 1>{});
+    else if (k <= 2) f(std::integral_constant<int, 2>{});
+    else if (k <= 4) f(std::integral_constant<int, 4>{});
+    else f(std::integral_constant<int, 8>{});
+}
+// rows two at a time where FMA latency chains would bound the kernel
+template <typename T, int KM> constexpr int unroll_rows() { return (sizeof(T) == 8 || KM <= 2) ? 2 : 1; }
+
 void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w, int64_t rows, int n,
                double2 *out, Scratch &sc, cudaStream_t s, bool accumulate) {
     check_n(n);
@@ -577,13 +663,18 @@ void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const
         const size_t smem = sizeof(double2) * (size_t)g0.rpb * kk * n;
         dispatch(p, g0.w, "multi_dot", [&](auto tT, auto tW) {
             RED_TYPES(tT, tW);
-            RedGeom g = g0;
-            fit_wave(g, k_multi_dot<T, W>, smem);
-            sc.ensure(g.blocks, kk * n);
-            MRHS_TIMED("k_multi_dot", s);
-            k_multi_dot<T, W><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const T *>(w), rows, n,
-                g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), out + (int64_t)j0 * n, accumulate);
+            with_kmax(kk, [&](auto tK) {
+                constexpr int KM = decltype(tK)::value;
+                auto kern = k_multi_dot<T, W, KM, unroll_rows<T, KM>()>;
+                RedGeom g = g0;
+                fit_wave(g, kern, smem);
+                sc.ensure(g.blocks, kk * n);
+                MRHS_TIMED("k_multi_dot", s);
+                kern<<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk,
+                                                       static_cast<const T *>(w), rows, n, g.rpb,
+                                                       sc.partials.as<double2>(), sc.counter.as<unsigned int>(),
+                                                       out + (int64_t)j0 * n, accumulate);
+            });
         });
         MRHS_LAUNCHED("k_multi_dot");
     }
@@ -607,13 +698,18 @@ void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, in
         const size_t smem = sizeof(double2) * (size_t)g0.rpb * (kk + 1) * n;
         dispatch(p, g0.w, "orthonormalize", [&](auto tT, auto tW) {
             RED_TYPES(tT, tW);
-            RedGeom g = g0;
-            fit_wave(g, k_dots_norm<T, W>, smem);
-            sc.ensure(g.blocks, (kk + 1) * n);
-            MRHS_TIMED("k_dots_norm", s);
-            k_dots_norm<T, W><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk, static_cast<const T *>(w), rows, n,
-                g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), h + (int64_t)j0 * n, nrm2);
+            with_kmax(kk, [&](auto tK) {
+                constexpr int KM = decltype(tK)::value;
+                auto kern = k_dots_norm<T, W, KM, unroll_rows<T, KM>()>;
+                RedGeom g = g0;
+                fit_wave(g, kern, smem);
+                sc.ensure(g.blocks, (kk + 1) * n);
+                MRHS_TIMED("k_dots_norm", s);
+                kern<<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk,
+                                                       static_cast<const T *>(w), rows, n, g.rpb,
+                                                       sc.partials.as<double2>(), sc.counter.as<unsigned int>(),
+                                                       h + (int64_t)j0 * n, nrm2);
+            });
         });
         MRHS_LAUNCHED("k_dots_norm");
         break;
@@ -629,13 +725,17 @@ void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, in
         const size_t smem = sizeof(double2) * (size_t)g0.rpb * n;
         dispatch(p, g0.w, "orthonormalize", [&](auto tT, auto tW) {
             RED_TYPES(tT, tW);
-            RedGeom g = g0;
-            fit_wave(g, k_lincomb_scale<T, W>, smem);
-            sc.ensure(g.blocks, n);
-            MRHS_TIMED("k_lincomb_scale", s);
-            k_lincomb_scale<T, W><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<T *>(w), static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk, h + (int64_t)j0 * n,
-                h, k, nrm2, hn2, rows, n, g.rpb, sc.partials.as<double2>(), sc.counter.as<unsigned int>(), nn);
+            with_kmax(kk, [&](auto tK) {
+                constexpr int KM = decltype(tK)::value;
+                RedGeom g = g0;
+                fit_wave(g, k_lincomb_scale<T, W, KM>, smem);
+                sc.ensure(g.blocks, n);
+                MRHS_TIMED("k_lincomb_scale", s);
+                k_lincomb_scale<T, W, KM><<<g.blocks, g.threads, smem, s>>>(
+                    static_cast<T *>(w), static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk,
+                    h + (int64_t)j0 * n, h, k, nrm2, hn2, rows, n, g.rpb, sc.partials.as<double2>(),
+                    sc.counter.as<unsigned int>(), nn);
+            });
         });
         MRHS_LAUNCHED("k_lincomb_scale");
         break;
@@ -660,12 +760,16 @@ void multi_dot_fixed_scratch(mrhs_precision p, const void *basis, int64_t stride
         const size_t smem = sizeof(double2) * (size_t)g0.rpb * kk * n;
         dispatch(p, g0.w, "multi_dot", [&](auto tT, auto tW) {
             RED_TYPES(tT, tW);
-            RedGeom g = g0;
-            fit_wave(g, k_multi_dot<T, W>, smem);
-            MRHS_TIMED("k_multi_dot", s);
-            k_multi_dot<T, W><<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(basis) + 2 * j0 * stride,
-                                                                stride, kk, static_cast<const T *>(w), rows, n, g.rpb,
-                                                                partials, counter, out + (int64_t)j0 * n, 0);
+            with_kmax(kk, [&](auto tK) {
+                constexpr int KM = decltype(tK)::value;
+                auto kern = k_multi_dot<T, W, KM, unroll_rows<T, KM>()>;
+                RedGeom g = g0;
+                fit_wave(g, kern, smem);
+                MRHS_TIMED("k_multi_dot", s);
+                kern<<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk,
+                                                       static_cast<const T *>(w), rows, n, g.rpb, partials, counter,
+                                                       out + (int64_t)j0 * n, 0);
+            });
         });
         MRHS_LAUNCHED("k_multi_dot");
     }
@@ -690,27 +794,29 @@ void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Sc
 template <typename TW, typename TB, int W>
 static void lincomb_t(void *w, const void *basis, int64_t stride, int k, const double2 *coef, double alpha,
                       const RedGeom &g0, int64_t rows, int n, cudaStream_t s, double *norm_out, Scratch *sc) {
-    RedGeom g = g0;
-    fit_wave(g, norm_out ? k_lincomb<TW, TB, true, W> : k_lincomb<TW, TB, false, W>,
-             norm_out ? sizeof(double2) * (size_t)g0.rpb * n : 0);
     for (int j0 = 0; j0 < k; j0 += KCHUNK) {
         const int kk = std::min(KCHUNK, k - j0);
         const bool want_norm = norm_out != nullptr && j0 + kk >= k;
         const TB *b = static_cast<const TB *>(basis) + 2 * j0 * stride;
         const double2 *c = coef + (int64_t)j0 * n;
-        MRHS_TIMED("k_lincomb", s);
-        if (want_norm) {
-            if (!sc) fail(MRHS_ERR_INVALID, "lincomb with norm needs scratch");
-            sc->ensure(g.blocks, n);
-            const size_t smem = sizeof(double2) * (size_t)g.rpb * n;
-            k_lincomb<TW, TB, true, W><<<g.blocks, g.threads, smem, s>>>(
-                static_cast<TW *>(w), b, stride, kk, c, alpha, rows, n, g.rpb, sc->partials.as<double2>(),
-                sc->counter.as<unsigned int>(), norm_out);
-        } else {
-            k_lincomb<TW, TB, false, W><<<g.blocks, g.threads, 0, s>>>(static_cast<TW *>(w), b, stride, kk, c,
-                                                                       alpha, rows, n, g.rpb, nullptr, nullptr,
-                                                                       nullptr);
-        }
+        if (want_norm && !sc) fail(MRHS_ERR_INVALID, "lincomb with norm needs scratch");
+        with_kmax(kk, [&](auto tK) {
+            constexpr int KM = decltype(tK)::value;
+            RedGeom g = g0;
+            MRHS_TIMED("k_lincomb", s);
+            if (want_norm) {
+                const size_t smem = sizeof(double2) * (size_t)g0.rpb * n;
+                fit_wave(g, k_lincomb<TW, TB, true, W, KM>, smem);
+                sc->ensure(g.blocks, n);
+                k_lincomb<TW, TB, true, W, KM><<<g.blocks, g.threads, smem, s>>>(
+                    static_cast<TW *>(w), b, stride, kk, c, alpha, rows, n, g.rpb, sc->partials.as<double2>(),
+                    sc->counter.as<unsigned int>(), norm_out);
+            } else {
+                fit_wave(g, k_lincomb<TW, TB, false, W, KM>, 0);
+                k_lincomb<TW, TB, false, W, KM><<<g.blocks, g.threads, 0, s>>>(
+                    static_cast<TW *>(w), b, stride, kk, c, alpha, rows, n, g.rpb, nullptr, nullptr, nullptr);
+            }
+        });
         MRHS_LAUNCHED("k_lincomb");
     }
 }
@@ -747,6 +853,24 @@ void scale_inv_sqrt(mrhs_precision p, void *dst, const void *src, const double *
                                                               nrm2, rows, n, g.rpb);
     });
     MRHS_LAUNCHED("k_scale_inv_sqrt");
+}
+
+__global__ void k_any_nonzero(const uint4 *__restrict__ p, int64_t count, unsigned *flag) {
+    unsigned acc = 0u;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldcs(p + i);
+        acc |= v.x | v.y | v.z | v.w;
+    }
+    acc = __reduce_or_sync(0xffffffffu, acc);
+    if ((threadIdx.x & 31) == 0 && acc) atomicOr(flag, 1u);
+}
+
+void any_nonzero(const void *p, int64_t bytes, unsigned *flag, cudaStream_t s) {
+    MRHS_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), s));
+    const int64_t count = bytes / 16;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)current_sms() * 8, ceil_div(count, 256)));
+    k_any_nonzero<<<blocks, 256, 0, s>>>(static_cast<const uint4 *>(p), count, flag);
+    MRHS_LAUNCHED("k_any_nonzero");
 }
 
 void cast(mrhs_precision pd, void *dst, mrhs_precision ps, const void *src, int64_t count, cudaStream_t s) {

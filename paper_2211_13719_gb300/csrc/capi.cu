@@ -93,6 +93,8 @@ mrhs_status mrhs_create_lattice(const int dims[4], int t_boundary, int device, m
     lat->U32.alloc(V * 36 * sizeof(float2));
     lat->C64.alloc(V * 36 * sizeof(double2));
     lat->C32.alloc(V * 36 * sizeof(float2));
+    lat->Udf.alloc(V * 36 * sizeof(float4));
+    lat->Cdf.alloc(V * 36 * sizeof(float4));
     *out = lat.release();
     MRHS_API_END
 }
@@ -166,17 +168,21 @@ static void check_apply(mrhs_lattice *lat, const void *in, const void *out, int 
     if (!in || !out) fail(MRHS_ERR_INVALID, "in and out must be non-null");
     if (in == out) fail(MRHS_ERR_INVALID, "in and out must not overlap");
     if (nrhs < 1) fail(MRHS_ERR_INVALID, "nrhs must be >= 1");
-    if (prec != MRHS_FP32 && prec != MRHS_FP64) fail(MRHS_ERR_INVALID, "precision must be FP32 or FP64");
+    if (prec != MRHS_FP32 && prec != MRHS_FP64 && prec != MRHS_DF64)
+        fail(MRHS_ERR_INVALID, "precision must be FP32, FP64 or DF64");
     if (!aligned16(in) || !aligned16(out)) fail(MRHS_ERR_INVALID, "fields must be 16-byte aligned");
     if (!lat->has_clover) fail(MRHS_ERR_INVALID, "clover term not built");
 }
+
+// input precision of an operator computing in `prec`: float-float takes FP32 fields
+static mrhs_precision input_prec(mrhs_precision prec) { return prec == MRHS_DF64 ? MRHS_FP32 : prec; }
 
 mrhs_status mrhs_apply_D(mrhs_lattice *lat, const void *in_dev, void *out_dev, int nrhs, mrhs_precision prec,
                          void *stream) {
     MRHS_API_BEGIN
     check_apply(lat, in_dev, out_dev, nrhs, prec);
     DeviceGuard dg(lat->device);
-    dslash(*lat, prec, prec, in_dev, out_dev, nullptr, nrhs, static_cast<cudaStream_t>(stream));
+    dslash(*lat, prec, input_prec(prec), in_dev, out_dev, nullptr, nrhs, static_cast<cudaStream_t>(stream));
     MRHS_API_END
 }
 
@@ -186,7 +192,7 @@ mrhs_status mrhs_residual_D(mrhs_lattice *lat, const void *in_dev, const void *y
     check_apply(lat, in_dev, out_dev, nrhs, prec);
     if (!y_dev || !aligned16(y_dev)) fail(MRHS_ERR_INVALID, "y must be non-null and 16-byte aligned");
     DeviceGuard dg(lat->device);
-    dslash(*lat, prec, prec, in_dev, out_dev, y_dev, nrhs, static_cast<cudaStream_t>(stream));
+    dslash(*lat, prec, input_prec(prec), in_dev, out_dev, y_dev, nrhs, static_cast<cudaStream_t>(stream));
     MRHS_API_END
 }
 

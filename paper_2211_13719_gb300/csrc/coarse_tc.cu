@@ -182,37 +182,55 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ A
 }
 
 // per-RHS scale of the input: col_scale[r] = max over sites and components of
-// max(|Re|, |Im|) (float bits compared as unsigned: valid for non-negative floats)
-__global__ void k_col_absmax(const float2 *__restrict__ phi, int64_t count, int n, unsigned *__restrict__ col_max) {
+// max(|Re|, |Im|) (float bits compared as unsigned: valid for non-negative
+// floats).  One column per thread, rows strided over the block and grid.
+__global__ void k_col_absmax(const float2 *__restrict__ phi, int64_t rows, int n, unsigned *__restrict__ col_max) {
     __shared__ unsigned sm[64];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sm[i] = 0u;
+    const int rpb = blockDim.x / n;
+    const int col = threadIdx.x % n, rsub = threadIdx.x / n;
+    if (threadIdx.x < 64) sm[threadIdx.x] = 0u;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-        const float2 v = phi[i];
-        const float m = fmaxf(fabsf(v.x), fabsf(v.y));
-        atomicMax(&sm[(int)(i % n)], __float_as_uint(m));
+    if (rsub < rpb) {
+        float m = 0.f;
+        for (int64_t row = (int64_t)blockIdx.x * rpb + rsub; row < rows; row += (int64_t)gridDim.x * rpb) {
+            const float2 v = phi[row * n + col];
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        atomicMax(&sm[col], __float_as_uint(m));
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicMax(&col_max[i], sm[i]);
+    if (threadIdx.x < n) atomicMax(&col_max[threadIdx.x], sm[threadIdx.x]);
 }
 
-// coarse field [V][64][n] FP32 -> per-site swizzled 16-bit image of [Re phi | Im phi]^T / col_scale
+// coarse field [V][64][n] FP32 -> per-site swizzled 16-bit image of [Re phi | Im phi]^T / col_scale.
+// One CTA per site: coalesced reads of the site's 64 x n values, the tile is
+// built in shared memory and written out with 16-byte stores.
 template <int FMT>
-__global__ void k_pack_phi(const float2 *__restrict__ phi, uint8_t *__restrict__ img, int64_t V, int n, int npad,
+__global__ void k_pack_phi(const float2 *__restrict__ phi, uint8_t *__restrict__ img, int n, int npad,
                            const float *__restrict__ col_scale) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= V * npad * NC) return;
-    const int64_t site = i / (npad * NC);
-    const int rem = (int)(i - site * npad * NC);
-    const int j = rem / NC, k = rem - j * NC;
-    float v = 0.f;
-    if (j < 2 * n) {
-        const int r = j < n ? j : j - n;
-        const float c = col_scale[r];
-        const float2 p = phi[(site * NC + k) * n + r];
-        v = c > 0.f ? (j < n ? p.x : p.y) / c : 0.f;
+    extern __shared__ uint4 tile4[];
+    __shared__ float inv[64];
+    uint8_t *tile = reinterpret_cast<uint8_t *>(tile4);
+    const int64_t site = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int words = npad * 128 / 16;
+    for (int i = tid; i < words; i += blockDim.x) tile4[i] = make_uint4(0, 0, 0, 0);
+    if (tid < n) {
+        const float c = col_scale[tid];
+        inv[tid] = c > 0.f ? 1.f / c : 0.f;
     }
-    *reinterpret_cast<uint16_t *>(img + site * (int64_t)npad * 128 + sw128_offset(j, k)) = to16<FMT>(v);
+    __syncthreads();
+    const float2 *src = phi + site * NC * n;
+    for (int e = tid; e < NC * n; e += blockDim.x) {
+        const int k = e / n, r = e - k * n;
+        const float2 p = src[e];
+        const float c = inv[r];
+        *reinterpret_cast<uint16_t *>(tile + sw128_offset(r, k)) = to16<FMT>(p.x * c);
+        *reinterpret_cast<uint16_t *>(tile + sw128_offset(n + r, k)) = to16<FMT>(p.y * c);
+    }
+    __syncthreads();
+    uint4 *dst = reinterpret_cast<uint4 *>(img + site * (int64_t)npad * 128);
+    for (int i = tid; i < words; i += blockDim.x) dst[i] = tile4[i];
 }
 
 // per-site scale of the links: max over the 9 blocks of max(|Re|, |Im|)
@@ -287,18 +305,18 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
     if (n < 1 || n > 64) fail(MRHS_ERR_INVALID, "tensor-core coarse stencil supports 1..64 RHS");
     const int npad = npad_of(n);
     MRHS_CUDA(cudaMemsetAsync(c.ColScale.ptr, 0, sizeof(float) * 64, s));
-    const int64_t fcount = c.V * NC * n;
-    const int gmax = sm_count(0) * 4;
-    k_col_absmax<<<std::max(1, std::min(gmax, ceil_div(fcount, 256))), 256, 0, s>>>(in, fcount, n,
-                                                                                  c.ColScale.as<unsigned>());
+    const int64_t rows = c.V * NC;
+    const int rpb = 256 / n;
+    const int ablocks = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(0) * 4, ceil_div(rows, 8LL * rpb)));
+    k_col_absmax<<<ablocks, 256, 0, s>>>(in, rows, n, c.ColScale.as<unsigned>());
     MRHS_LAUNCHED("k_col_absmax");
-    const int64_t count = c.V * npad * NC;
+    const size_t tile_bytes = (size_t)npad * 128;
     if (c.tc_fmt == MRHS_FP16)
-        k_pack_phi<0><<<ceil_div(count, 256), 256, 0, s>>>(in, c.PhiBf.as<uint8_t>(), c.V, n, npad,
-                                                           c.ColScale.as<float>());
+        k_pack_phi<0><<<(unsigned)c.V, 256, tile_bytes, s>>>(in, c.PhiBf.as<uint8_t>(), n, npad,
+                                                             c.ColScale.as<float>());
     else
-        k_pack_phi<1><<<ceil_div(count, 256), 256, 0, s>>>(in, c.PhiBf.as<uint8_t>(), c.V, n, npad,
-                                                           c.ColScale.as<float>());
+        k_pack_phi<1><<<(unsigned)c.V, 256, tile_bytes, s>>>(in, c.PhiBf.as<uint8_t>(), n, npad,
+                                                             c.ColScale.as<float>());
     MRHS_LAUNCHED("k_pack_phi");
     TcArgs a;
     for (int mu = 0; mu < 4; ++mu) a.L[mu] = c.L[mu];

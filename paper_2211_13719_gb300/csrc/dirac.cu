@@ -15,29 +15,9 @@
 // forms a 2-spin half spinor h = psi_up -+ A psi_dn, multiplies it by the
 // link, and rebuilds the lower spins from the two products.
 #include "internal.cuh"
+#include "spin.cuh"
 
 namespace mrhs {
-
-// ---------------------------------------------------------------- factors
-// multiply by one of +1, -1, +i, -i
-enum { FP = 0, FM = 1, FI = 2, FMI = 3 };
-template <int F, typename T> __device__ __forceinline__ cplx<T> fmul(cplx<T> a) {
-    if constexpr (F == FP) return a;
-    else if constexpr (F == FM) return {-a.re, -a.im};
-    else if constexpr (F == FI) return ti(a);
-    else return tmi(a);
-}
-template <int F> struct neg_f { static constexpr int v = F == FP ? FM : F == FM ? FP : F == FI ? FMI : FI; };
-
-// Half-spinor rule of direction MU for the forward hop (1 - gamma_mu):
-//   h0 = psi0 + F0 psi_{P0},  h1 = psi1 + F1 psi_{P1}
-//   acc2 += G2 (U h)_{Q2},    acc3 += G3 (U h)_{Q3},  acc0 += (U h)_0, acc1 += (U h)_1
-// The backward hop (1 + gamma_mu) negates F0, F1, G2, G3.
-template <int MU> struct Proj;
-template <> struct Proj<0> { static constexpr int P0 = 3, F0 = FI, P1 = 2, F1 = FI, Q2 = 1, G2 = FMI, Q3 = 0, G3 = FMI; };
-template <> struct Proj<1> { static constexpr int P0 = 3, F0 = FP, P1 = 2, F1 = FM, Q2 = 1, G2 = FM, Q3 = 0, G3 = FP; };
-template <> struct Proj<2> { static constexpr int P0 = 2, F0 = FI, P1 = 3, F1 = FMI, Q2 = 0, G2 = FMI, Q3 = 1, G3 = FI; };
-template <> struct Proj<3> { static constexpr int P0 = 2, F0 = FM, P1 = 3, F1 = FM, Q2 = 0, G2 = FM, Q3 = 1, G3 = FM; };
 
 // ------------------------------------------------------------ vector loads
 // R consecutive complex values of the input field at complex offset `off`.
@@ -533,8 +513,12 @@ void dslash(const mrhs_lattice &lat, mrhs_precision compute, mrhs_precision in_p
         } else {
             fail(MRHS_ERR_INVALID, "unsupported input precision");
         }
+    } else if (compute == MRHS_DF64) {
+        if (general) fail(MRHS_ERR_INVALID, "masked operator has no float-float form");
+        if (in_prec != MRHS_FP32) fail(MRHS_ERR_INVALID, "float-float operator takes an FP32 input");
+        dslash_df(lat, in, out, y, n, s);
     } else {
-        fail(MRHS_ERR_INVALID, "fine operator computes in FP32 or FP64");
+        fail(MRHS_ERR_INVALID, "fine operator computes in FP32, FP64 or float-float");
     }
 }
 
@@ -556,6 +540,7 @@ void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s) {
     k_gauge_to_soa<<<ceil_div(n, 256), 256, 0, s>>>(reinterpret_cast<const double2 *>(aos_dev),
                                                      lat.U64.as<double2>(), lat.U32.as<float2>(), V);
     MRHS_LAUNCHED("k_gauge_to_soa");
+    split_df(lat.U64.ptr, lat.Udf.ptr, n, s);
 }
 
 // ------------------------------------------------------------ clover build
@@ -703,6 +688,7 @@ void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s) {
     k_build_clover<<<ceil_div(V, 128), 128, 0, s>>>(lat.U64.as<double2>(), lat.g, mass, csw,
                                                      lat.C64.as<double2>(), lat.C32.as<float2>());
     MRHS_LAUNCHED("k_build_clover");
+    split_df(lat.C64.ptr, lat.Cdf.ptr, V * 36, s);
 }
 
 }  // namespace mrhs

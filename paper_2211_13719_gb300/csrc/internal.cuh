@@ -16,6 +16,9 @@ struct mrhs_lattice {
     // compact clover + mass, SoA: [(chi*18 + q)*V + x], q < 3 packs diagonal
     // pairs (d_{2q}, d_{2q+1}); q >= 3 is lower-triangle entry q - 3
     mrhs::DeviceBuffer C64, C32;
+    // the same links and clover as float-float pairs (float4 per complex:
+    // re hi, re lo, im hi, im lo) for the float-float operator
+    mrhs::DeviceBuffer Udf, Cdf;
     bool has_gauge = false, has_clover = false;
     double mass = 0.0, csw = 0.0;
 };
@@ -32,6 +35,10 @@ struct HopMask {
 };
 
 void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s);
+// dst[i] = (hi, lo) float pairs of the FP64 complex src[i], i < count
+void split_df(const void *src_c128, void *dst_f4, int64_t count, cudaStream_t s);
+// out = D in (y == nullptr) or y - D in; `in` FP32, out and y FP64, float-float arithmetic
+void dslash_df(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n, cudaStream_t s);
 void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s);
 // out = D in (y == nullptr) or out = y - D in; compute in `compute` precision,
 // input in `in_prec` (FP32 input allowed with FP64 compute); out and y in `compute`.
@@ -54,6 +61,8 @@ constexpr int KCHUNK = 8;  // basis vectors per multi-dot pass
 void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const void *w,
                int64_t rows, int n, double2 *out, Scratch &sc, cudaStream_t s, bool accumulate = false);
 void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s);
+// *flag = 0 if all `bytes` bytes at p (a multiple of 16, 16-byte aligned) are zero, else nonzero
+void any_nonzero(const void *p, int64_t bytes, unsigned *flag, cudaStream_t s);
 // multi_dot with caller-provided reduction scratch: `partials` holds at least
 // (max_blocks + ceil(max_blocks / 32)) * KCHUNK * n double2, `counter` holds
 // 64 unsigned ints that are zero on entry (the kernel leaves them zero);

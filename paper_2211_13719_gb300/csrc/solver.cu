@@ -382,6 +382,8 @@ void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
     if (p.max_rhs < 1 || p.max_rhs > 64) fail(MRHS_ERR_INVALID, "max_rhs must be in 1..64");
     if (p.coarse_precision != MRHS_FP32 && p.coarse_precision != MRHS_BF16 && p.coarse_precision != MRHS_FP16)
         fail(MRHS_ERR_INVALID, "coarse_precision must be FP32, FP16 or BF16");
+    if (p.outer_op_precision != MRHS_DF64 && p.outer_op_precision != MRHS_FP64)
+        fail(MRHS_ERR_INVALID, "outer_op_precision must be DF64 or FP64");
     if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
 }
 
@@ -497,12 +499,12 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
     // skip that FP64 operator application
     bool x_zero = false;
     {
-        norm2(MRHS_FP64, x, rows, n, mg.oks.hn2.as<double>(), mg.osc, s);
-        MRHS_CUDA(cudaMemcpyAsync(hres, mg.oks.hn2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        unsigned *flag = reinterpret_cast<unsigned *>(mg.oks.nn.as<double>());
+        any_nonzero(x, sizeof(double2) * F, flag, s);
+        unsigned *hflag = reinterpret_cast<unsigned *>(hres);
+        MRHS_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         MRHS_CUDA(cudaStreamSynchronize(s));
-        x_zero = true;
-        for (int r = 0; r < n; ++r)
-            if (hres[r] != 0.0) x_zero = false;
+        x_zero = *hflag == 0u;
     }
     while (true) {
         // true residual in FP64
@@ -530,15 +532,16 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
             double2 *wj = V0 + (size_t)(j + 1) * F;
             cast(MRHS_FP32, mg.inner_b.ptr, MRHS_FP64, vj, F, s);
             inner_total += inner_solve(mg, mg.inner_b.as<float2>(), zj, n, s);
-            dslash(lat, MRHS_FP64, MRHS_FP32, zj, wj, nullptr, n, s);
-            double2 *hcol = mg.oks.hcol.as<double2>();
-            double2 *h2 = mg.oks.h2.as<double2>();
-            multi_dot(MRHS_FP64, V0, F, j + 1, wj, rows, n, hcol, mg.osc, s);
-            lincomb(MRHS_FP64, wj, MRHS_FP64, V0, F, j + 1, hcol, -1.0, rows, n, s);
-            multi_dot(MRHS_FP64, V0, F, j + 1, wj, rows, n, h2, mg.osc, s);
-            lincomb(MRHS_FP64, wj, MRHS_FP64, V0, F, j + 1, h2, -1.0, rows, n, s, mg.oks.hn2.as<double>(), &mg.osc);
-            scale_inv_sqrt(MRHS_FP64, wj, wj, mg.oks.hn2.as<double>(), rows, n, s);
-            krylov_givens(mg.oks, j, n, s);
+            // w = D z_j: z_j is FP32, w FP64 (float-float or FP64 arithmetic)
+            dslash(lat, mg.p.outer_op_precision == MRHS_DF64 ? MRHS_DF64 : MRHS_FP64, MRHS_FP32, zj, wj, nullptr, n,
+                   s);
+            // one pass of classical Gram-Schmidt with the Pythagorean norm (and the
+            // cancellation fix-up), as in the FP32 cycles: the outer basis has at most
+            // outer_m vectors and FP64 keeps its loss of orthogonality far below tol
+            orthonormalize_step(MRHS_FP64, V0, F, j + 1, wj, rows, n, mg.oks.hcol.as<double2>(),
+                                mg.oks.nrm2w.as<double>(), mg.oks.hn2.as<double>(), mg.oks.nn.as<double>(), mg.osc,
+                                s);
+            krylov_givens(mg.oks, j, n, s, true);
             ++outer;
             HostCheck chk{target.data(), hres};
             bool halt = chk.test(mg.oks, n, s) || outer >= cap;
@@ -656,6 +659,7 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->coarse_precision = MRHS_FP16;
     p->max_rhs = 48;
     p->use_graph = 1;
+    p->outer_op_precision = MRHS_DF64;
     p->seed = 1234;
 }
 

@@ -30,6 +30,7 @@ MRHS_FP32 = 0
 MRHS_FP64 = 1
 MRHS_BF16 = 2
 MRHS_FP16 = 3
+MRHS_DF64 = 4  # float-float fine operator: FP32 input, FP64 output
 
 MAX_LEVELS = 3
 
@@ -62,6 +63,7 @@ class MgParams(C.Structure):
         ("coarse_precision", C.c_int),
         ("max_rhs", C.c_int),
         ("use_graph", C.c_int),
+        ("outer_op_precision", C.c_int),
         ("seed", C.c_uint64),
         ("init_vecs", C.c_void_p * (MAX_LEVELS - 1)),
     ]

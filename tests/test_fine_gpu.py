@@ -1,7 +1,7 @@
 """GPU parity: fused fine hopping + clover operator (Sec. 4) vs the FP64 oracle.
 
 Bars: FP32 <= 1e-6 relative per site and RHS (norm over the 12 components),
-FP64 <= 1e-12.  Lattices span several thread blocks with a ragged tail, odd
+FP64 <= 1e-12, float-float (FP32 input, FP64 output) <= 1e-12.  Lattices span several thread blocks with a ragged tail, odd
 and even RHS counts (scalar and vector load paths), both time boundaries, and
 the full 24^4 x 64-RHS workload on sampled sites.
 """
@@ -58,6 +58,45 @@ def test_apply_D_fp32_fp64_parity(dims, nrhs, tb, hot):
             got = to_host(d_out).astype(np.complex128)
             ref = y.astype(np.complex128) - expect
             assert site_rel_err(got, ref) <= 10 * tol
+    finally:
+        mrhs.mrhs_destroy_lattice(lat)
+
+
+DF64_TOL = 1e-12
+
+
+@pytest.mark.parametrize("dims,nrhs,tb,hot", [
+    ((4, 4, 4, 4), 1, -1, True),
+    ((6, 4, 2, 8), 3, -1, False),
+    ((8, 4, 4, 6), 4, 1, True),
+    ((3, 5, 2, 7), 48, -1, True),    # odd extents, the workload's RHS count, ragged block tail
+    ((1, 2, 1, 4), 2, -1, True),
+])
+def test_apply_D_float_float_parity(dims, nrhs, tb, hot):
+    """MRHS_DF64: FP32 input, FP64 output, float-float arithmetic, against the FP64
+    oracle on the same (exactly representable) input, and against the FP64 kernel."""
+    mass, csw = -0.2, 1.0
+    U = _problem(dims, 1301 + nrhs, hot)
+    V = wilson.volume(dims)
+    C = wilson.clover_term(U, dims, csw)
+    psi = synth.gaussian_field(V, 12, nrhs, 2301 + nrhs, np.complex64)
+    lat = make_lattice(U, dims, mass, csw, tb)
+    try:
+        expect = wilson.apply_D(U, C, psi.astype(np.complex128), dims, mass, antiperiodic=(tb == -1))
+        d_in = to_dev(psi)
+        d_out = to_dev(np.full(psi.shape, np.nan, np.complex128))
+        mrhs.mrhs_apply_D(lat, d_in, d_out, nrhs, mrhs.MRHS_DF64)
+        got = to_host(d_out)
+        assert got.dtype == np.complex128 and np.all(np.isfinite(got))
+        assert site_rel_err(got, expect) <= DF64_TOL
+        d_in64 = to_dev(psi.astype(np.complex128))
+        d_out64 = to_dev(np.full(psi.shape, np.nan, np.complex128))
+        mrhs.mrhs_apply_D(lat, d_in64, d_out64, nrhs, mrhs.MRHS_FP64)
+        assert site_rel_err(got, to_host(d_out64)) <= DF64_TOL
+        # fused residual y - D psi with FP64 y
+        y = synth.gaussian_field(V, 12, nrhs, 2401 + nrhs)
+        mrhs.mrhs_residual_D(lat, d_in, to_dev(y), d_out, nrhs, mrhs.MRHS_DF64)
+        assert site_rel_err(to_host(d_out), y - expect) <= 10 * DF64_TOL
     finally:
         mrhs.mrhs_destroy_lattice(lat)
 

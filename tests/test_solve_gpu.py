@@ -70,6 +70,44 @@ def test_solve_true_residual_and_oracle_solution(problem):
     assert np.all(err <= 1e-6), err
 
 
+def test_outer_operator_precisions_agree(problem):
+    """Outer Arnoldi applies in float-float (default) or FP64: both reach the
+    FP64 true residual, and their solutions agree within what it allows."""
+    U, b, v0 = problem
+    C = wilson.clover_term(U, DIMS, CSW)
+    xs = []
+    for prec in (mrhs.MRHS_DF64, mrhs.MRHS_FP64):
+        (x, rel, st), = _gpu_solve(U, b, v0, [list(range(NRHS))], outer_op_precision=prec)
+        r = b - wilson.apply_D(U, C, x, DIMS, MASS)
+        assert np.all(krylov.norms(r) / krylov.norms(b) <= 1e-10)
+        xs.append(x)
+    err = krylov.norms(xs[0] - xs[1]) / krylov.norms(xs[1])
+    assert np.all(err <= 1e-7), err
+
+
+def test_nonzero_start_vector(problem):
+    """A nonzero initial x takes the FP64 residual path (no zero-start shortcut)."""
+    U, b, v0 = problem
+    params = dict(n_levels=2, blocks=BLOCKS, nvec=NVEC, setup_sweeps=4, max_rhs=NRHS,
+                  coarse_precision=mrhs.MRHS_FP32)
+    lat = make_lattice(U, DIMS, MASS, CSW)
+    mg = make_mg(lat, params, [v0])
+    try:
+        d_b = to_dev(b)
+        x0 = np.zeros_like(b)
+        x0[5, 3, 1] = 1e-3   # a single nonzero entry in one RHS column
+        d_x = to_dev(x0)
+        rel = np.zeros(NRHS)
+        mrhs.mrhs_solve(mg, d_b, d_x, NRHS, 1e-10, rel)
+        x = to_host(d_x)
+    finally:
+        mrhs.mrhs_destroy_mg(mg)
+        mrhs.mrhs_destroy_lattice(lat)
+    C = wilson.clover_term(U, DIMS, CSW)
+    r = b - wilson.apply_D(U, C, x, DIMS, MASS)
+    assert np.all(krylov.norms(r) / krylov.norms(b) <= 1e-10)
+
+
 def test_mrhs_equals_single_rhs(problem):
     U, b, v0 = problem
     outs = _gpu_solve(U, b, v0, [list(range(NRHS)), [0], [3]])
