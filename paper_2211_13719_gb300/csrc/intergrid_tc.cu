@@ -138,9 +138,12 @@ constexpr int IG_STAGES = 3;  // P tiles in flight per CTA
 // psi[r]), so tensor-memory lane rho holds fine row rho in memory order and
 // each thread stores its own row.  Two accumulators: the MMAs of tile t + 1
 // run while tile t is drained.
+constexpr int IG_PTHREADS = 128;
+
 template <int VEC>
-__global__ void __launch_bounds__(128) k_prolong_tc(const float2 *__restrict__ coarse, const uint8_t *__restrict__ PA,
-                                                    float2 *__restrict__ fine, IgArgs a, int *__restrict__ err) {
+__global__ void __launch_bounds__(IG_PTHREADS) k_prolong_tc(const float2 *__restrict__ coarse,
+                                                            const uint8_t *__restrict__ PA, float2 *__restrict__ fine,
+                                                            IgArgs a, int *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t full[IG_STAGES];  // the stage's P tile landed
     __shared__ uint64_t done[2];          // MMAs into accumulator b complete
@@ -588,10 +591,10 @@ void prolong_fields_tc(const Level &f, const Level &c, const float2 *coarse, flo
     const dim3 grid((unsigned)c.V, 2);
     MRHS_TIMED("k_prolong_tc", s);
     if (paired(fine, n))
-        k_prolong_tc<2><<<grid, 128, prolong_smem(a.npad, a.R), s>>>(coarse, f.PA.as<uint8_t>(), fine, a,
+        k_prolong_tc<2><<<grid, IG_PTHREADS, prolong_smem(a.npad, a.R), s>>>(coarse, f.PA.as<uint8_t>(), fine, a,
                                                                      f.IgErr.as<int>());
     else
-        k_prolong_tc<1><<<grid, 128, prolong_smem(a.npad, a.R), s>>>(coarse, f.PA.as<uint8_t>(), fine, a,
+        k_prolong_tc<1><<<grid, IG_PTHREADS, prolong_smem(a.npad, a.R), s>>>(coarse, f.PA.as<uint8_t>(), fine, a,
                                                                      f.IgErr.as<int>());
     MRHS_LAUNCHED("k_prolong_tc");
 }
