@@ -507,14 +507,15 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
         x_zero = *hflag == 0u;
     }
     while (true) {
-        // true residual in FP64
+        // true residual in FP64 (for x = 0 it is b, whose norms are known)
         if (x_zero) {
             MRHS_CUDA(cudaMemcpyAsync(V0, b, sizeof(double2) * F, cudaMemcpyDeviceToDevice, s));
+            MRHS_CUDA(cudaMemcpyAsync(mg.oks.beta2.ptr, mg.obn2.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             x_zero = false;
         } else {
             dslash(lat, MRHS_FP64, MRHS_FP64, x, V0, b, n, s);
+            norm2(MRHS_FP64, V0, rows, n, mg.oks.beta2.as<double>(), mg.osc, s);
         }
-        norm2(MRHS_FP64, V0, rows, n, mg.oks.beta2.as<double>(), mg.osc, s);
         MRHS_CUDA(cudaMemcpyAsync(hres, mg.oks.beta2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
         MRHS_CUDA(cudaStreamSynchronize(s));
         converged = true;
