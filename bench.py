@@ -140,6 +140,28 @@ def profiled_traffic(kernel_file):
     return None
 
 
+# -------------------------------------------------------------- N replicas
+def max_over_ranks(t, world, device):
+    """The job time: the slowest rank's time (all-reduce MAX over the ranks)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(nrhs_per_rank, steps, world, t_job):
+    """Whole-job solves/s: every rank (replica) solves its own nrhs_per_rank RHS per step."""
+    return nrhs_per_rank * steps * world / t_job
+
+
+def replica_source_seed(w, rank):
+    """Each replica draws its own sources."""
+    return w["source_seed"] + 1000 * rank
+
+
 # --------------------------------------------------------------- oracle arm
 def oracle_sample_solve(steps: int, warmup: int):
     """Time the oracle's FP64 MG-FGMRES on the sample lattice (one RHS per step)."""
@@ -196,7 +218,7 @@ def run_reference(args, rank, world):
     wall = time.perf_counter() - t0
     line = {
         "impl": "reference", "metric": "MG solves/s at 1e-10", "value": res["value"], "unit": "solves/s",
-        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": (res.get("seconds_per_sample_solve") or 0) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "sample": ORACLE_SAMPLE["dims"]},
@@ -337,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
     setup_s = time.perf_counter() - t0
 
     gen = torch.Generator(device="cuda")
-    gen.manual_seed(w["source_seed"] + 1000 * rank)
+    gen.manual_seed(replica_source_seed(w, rank))
     b = torch.randn((V, 12, n), dtype=torch.complex128, device="cuda", generator=gen)
     x = torch.zeros_like(b)
     rel = np.zeros(n)
@@ -371,15 +393,12 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.nvtx.range_pop()
     k_ms, k_timed, k_captured = mrhs.mrhs_kernel_timer_stop()
     launches = mrhs.mrhs_kernel_launch_count() - launches0
-    t_dev = e0.elapsed_time(e1) * 1e-3
+    t_dev = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world, "cuda")
     if world > 1:
         import torch.distributed as dist
-        tt = torch.tensor([t_dev], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
         dist.barrier()
     max_rel = float(max(s.max_rel_residual for s in stats))
-    value = n * args.steps * world / t_dev
+    value = job_throughput(n, args.steps, world, t_dev)
 
     extra = {}
     if rank == 0:
