@@ -17,7 +17,7 @@ serving run (p50 / p99 latency), and the oracle timed on the host cores as
 the CPU baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-  python bench.py --case stencil|intergrid|blas   (small cases for ncu captures)
+  python bench.py --case stencil|schur|intergrid|blas   (small cases for ncu captures)
 """
 from __future__ import annotations
 
@@ -504,6 +504,7 @@ def run_case(name, reps):
     """Small launches of one kernel family, for ncu captures (a few GB on the device).
 
     stencil:   FP32 fine operator, 24^4 lattice, 48 RHS
+    schur:     even-odd hop and Schur operator (FP32), 24^4 lattice, 48 RHS
     intergrid: tensor-core restriction + prolongation, 16^4 lattice, 4^4 aggregates, 32 vectors, 48 RHS
     blas:      the FP32 batched multi-dot and linear combination, 16^4 x 12 rows, 48 RHS, 4 vectors
     Prints one JSON line with the CUDA-event time per launch."""
@@ -544,7 +545,7 @@ def run_case(name, reps):
                                                                   mrhs.MRHS_FP32))
         out["GBs_lincomb_k4"] = (k + 2) * rows * n * 8 / out["ms_lincomb_k4"] / 1e6
         return print(json.dumps(out), flush=True)
-    dims = (24, 24, 24, 24) if name == "stencil" else (16, 16, 16, 16)
+    dims = (24, 24, 24, 24) if name in ("stencil", "schur") else (16, 16, 16, 16)
     V = volume(dims)
     U = synth.gauge_exp(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
     lat = mrhs.mrhs_create_lattice(dims, -1, torch.cuda.current_device())
@@ -556,6 +557,14 @@ def run_case(name, reps):
         o = torch.empty_like(a)
         out["ms_apply_fp32"] = ev(lambda: mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream))
         out["alg_GBs"] = V * (576 + 192 * n) / out["ms_apply_fp32"] / 1e6
+    elif name == "schur":
+        a = torch.randn((V // 2, 12, n), dtype=torch.complex64, device="cuda")
+        o = torch.empty_like(a)
+        out["ms_hop_eo"] = ev(lambda: mrhs.mrhs_apply_hop_eo(lat, 0, a, o, n, stream))
+        out["ms_schur"] = ev(lambda: mrhs.mrhs_apply_schur(lat, a, o, n, stream))
+        # per output site: 4 links x 72 B, clover (or inverse) 288 B, 96 B out per RHS; 8 neighbour spinors
+        # of 96 B per RHS each counted once (a half field in) -> (576 + 192 n) B per output site, two kernels
+        out["schur_alg_GBs"] = 2 * (V // 2) * (576 + 192 * n) / out["ms_schur"] / 1e6
     elif name == "intergrid":
         p = mrhs.mrhs_mg_default_params()
         p.n_levels = 2
@@ -591,7 +600,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.8)
-    ap.add_argument("--case", default=None, choices=["stencil", "intergrid", "blas"],
+    ap.add_argument("--case", default=None, choices=["stencil", "schur", "intergrid", "blas"],
                     help="run a small profiling case of one kernel family instead of the benchmark")
     ap.add_argument("--case-reps", type=int, default=3)
     args = ap.parse_args()

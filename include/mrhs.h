@@ -140,6 +140,25 @@ mrhs_status mrhs_apply_D(mrhs_lattice *lat, const void *in_dev, void *out_dev,
 mrhs_status mrhs_residual_D(mrhs_lattice *lat, const void *in_dev, const void *y_dev,
                             void *out_dev, int nrhs, mrhs_precision prec, void *stream);
 
+
+/* Even-odd decomposition (Sec. 4, M_eooe: the hopping term between the
+ * checkerboarded lattices).  Half-lattice fields are [V/2][12][nrhs] complex
+ * FP32 holding the sites of one parity p = (x + y + z + t) mod 2 in
+ * increasing lexicographic order (site s at index s / 2).  All four lattice
+ * extents must be even and nrhs even (MRHS_ERR_INVALID otherwise); in and out
+ * must not overlap and be 16-byte aligned.  With D = C - 1/2 H (C the clover +
+ * mass term, H the hopping term):
+ * mrhs_apply_hop_eo: out_dev (parity out_parity) = H in_dev (the other parity),
+ *   without the -1/2 factor.
+ * mrhs_apply_schur: out_o = D_hat in_o = C_oo in_o - 1/4 H_oe C_ee^-1 H_eo in_o,
+ *   the Schur complement of D on the odd sites.  C^-1 is built by
+ *   mrhs_build_clover (FP64 Gauss-Jordan per 6x6 chirality block); if a block is
+ *   singular the call fails with MRHS_ERR_INVALID.  Uses a half-lattice scratch
+ *   field owned by the lattice (allocated on first use). */
+mrhs_status mrhs_apply_hop_eo(mrhs_lattice *lat, int out_parity, const void *in_dev, void *out_dev, int nrhs,
+                              void *stream);
+mrhs_status mrhs_apply_schur(mrhs_lattice *lat, const void *in_dev, void *out_dev, int nrhs, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Batched BLAS-1 over the RHS index (Sec. 7, "simultaneous" inner      */
 /* products).  A field is `rows` rows of `nrhs` complex values, RHS     */

@@ -60,7 +60,10 @@ def from_half(half: np.ndarray, dims, p: int) -> np.ndarray:
 def hop_between(U: np.ndarray, psi_half: np.ndarray, dims, out_parity: int,
                 antiperiodic: bool = True) -> np.ndarray:
     """H_{p,1-p} psi: the hopping term (without -1/2) from the sites of parity
-    1 - out_parity to those of parity out_parity (M_eooe)."""
+    1 - out_parity to those of parity out_parity (M_eooe).  Needs even extents
+    in all four directions (else a periodic wrap joins equal parities)."""
+    if any(int(L) % 2 for L in dims):
+        raise ValueError("the even-odd decomposition needs even lattice extents")
     full = from_half(psi_half, dims, 1 - out_parity)
     return to_half(wilson.hop_term(U, full, dims, antiperiodic), dims, out_parity)
 

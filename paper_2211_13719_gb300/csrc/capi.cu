@@ -95,6 +95,9 @@ mrhs_status mrhs_create_lattice(const int dims[4], int t_boundary, int device, m
     lat->C32.alloc(V * 36 * sizeof(float2));
     lat->Udf.alloc(V * 36 * sizeof(float4));
     lat->Cdf.alloc(V * 36 * sizeof(float4));
+    lat->Cinv64.alloc(V * 36 * sizeof(double2));
+    lat->Cinv32.alloc(V * 36 * sizeof(float2));
+    lat->CinvErr.alloc(sizeof(int));
     *out = lat.release();
     MRHS_API_END
 }
@@ -131,6 +134,7 @@ mrhs_status mrhs_build_clover(mrhs_lattice *lat, double mass, double csw) {
     DeviceGuard dg(lat->device);
     build_clover(*lat, mass, csw, 0);
     MRHS_CUDA(cudaDeviceSynchronize());
+    lat->cinv_singular = clover_inverse_error(*lat) != 0;
     lat->mass = mass;
     lat->csw = csw;
     lat->has_clover = true;
@@ -193,6 +197,24 @@ mrhs_status mrhs_residual_D(mrhs_lattice *lat, const void *in_dev, const void *y
     if (!y_dev || !aligned16(y_dev)) fail(MRHS_ERR_INVALID, "y must be non-null and 16-byte aligned");
     DeviceGuard dg(lat->device);
     dslash(*lat, prec, input_prec(prec), in_dev, out_dev, y_dev, nrhs, static_cast<cudaStream_t>(stream));
+    MRHS_API_END
+}
+
+mrhs_status mrhs_apply_hop_eo(mrhs_lattice *lat, int out_parity, const void *in_dev, void *out_dev, int nrhs,
+                              void *stream) {
+    MRHS_API_BEGIN
+    check_apply(lat, in_dev, out_dev, nrhs, MRHS_FP32);
+    if (out_parity != 0 && out_parity != 1) fail(MRHS_ERR_INVALID, "out_parity must be 0 (even) or 1 (odd)");
+    DeviceGuard dg(lat->device);
+    hop_eo(*lat, out_parity, in_dev, out_dev, nrhs, static_cast<cudaStream_t>(stream));
+    MRHS_API_END
+}
+
+mrhs_status mrhs_apply_schur(mrhs_lattice *lat, const void *in_dev, void *out_dev, int nrhs, void *stream) {
+    MRHS_API_BEGIN
+    check_apply(lat, in_dev, out_dev, nrhs, MRHS_FP32);
+    DeviceGuard dg(lat->device);
+    schur_apply(*lat, in_dev, out_dev, nrhs, static_cast<cudaStream_t>(stream));
     MRHS_API_END
 }
 

@@ -358,6 +358,29 @@ __device__ __forceinline__ void hop_pair_x2(P2 (&acc)[12], const float2 *__restr
     hop_x2<MU, false>(acc, U, in, a, sb, sb, flipB, r0);
 }
 
+// o = M v for chirality block chi of a compact Hermitian site matrix M (the
+// clover term C or its inverse): 3 diagonal pairs, then the 15 lower entries
+__device__ __forceinline__ void site_mat_x2(const float2 *__restrict__ M, int V, int site, int chi,
+                                            const P2 (&v)[6], P2 (&o)[6]) {
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float2 d = __ldg(M + (int64_t)(chi * 18 + q) * V + site);
+        const float2 d0 = make_float2(d.x, d.x), d1 = make_float2(d.y, d.y);
+        o[2 * q] = {__fmul2_rn(d0, v[2 * q].re), __fmul2_rn(d0, v[2 * q].im)};
+        o[2 * q + 1] = {__fmul2_rn(d1, v[2 * q + 1].re), __fmul2_rn(d1, v[2 * q + 1].im)};
+    }
+    int q = 3;
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j < i; ++j, ++q) {
+            const float2 l = __ldg(M + (int64_t)(chi * 18 + q) * V + site);
+            p2mac(o[i], l, v[j]);
+            p2mac_conj(o[j], l, v[i]);
+        }
+    }
+}
+
 template <bool RESID>
 __global__ void __launch_bounds__(128, 4) k_dslash_x2(const float2 *__restrict__ U, const float2 *__restrict__ C,
                                                        const float2 *__restrict__ in, float2 *__restrict__ out,
@@ -401,23 +424,7 @@ __global__ void __launch_bounds__(128, 4) k_dslash_x2(const float2 *__restrict__
         P2 v[6], o[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) v[i] = ld_p2(in, base + (int64_t)(6 * chi + i) * a.n);
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-            const float2 d = __ldg(C + (int64_t)(chi * 18 + q) * V + site);
-            const float2 d0 = make_float2(d.x, d.x), d1 = make_float2(d.y, d.y);
-            o[2 * q] = {__fmul2_rn(d0, v[2 * q].re), __fmul2_rn(d0, v[2 * q].im)};
-            o[2 * q + 1] = {__fmul2_rn(d1, v[2 * q + 1].re), __fmul2_rn(d1, v[2 * q + 1].im)};
-        }
-        int q = 3;
-#pragma unroll
-        for (int i = 1; i < 6; ++i) {
-#pragma unroll
-            for (int j = 0; j < i; ++j, ++q) {
-                const float2 l = __ldg(C + (int64_t)(chi * 18 + q) * V + site);
-                p2mac(o[i], l, v[j]);
-                p2mac_conj(o[j], l, v[i]);
-            }
-        }
+        site_mat_x2(C, V, site, chi, v, o);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             const P2 acc_i = acc[6 * chi + i];
@@ -473,6 +480,163 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
                                                       static_cast<float2 *>(out), nullptr, a);
     MRHS_LAUNCHED("k_dslash_x2");
     return true;
+}
+
+// ------------------------------------------------ even-odd (M_eooe) kernels
+// Half-lattice fields [V/2][12][n] hold the sites of one parity
+// ((x + y + z + t) mod 2) in increasing lexicographic order: with an even x
+// extent, site s sits at index s / 2.  The hopping term only connects sites
+// of opposite parity (H_eo, H_oe: the paper's M_eooe, Sec. 4), so every
+// neighbour of an output site is read from the other parity's half field at
+// index neighbour / 2.  One thread per (output site, RHS pair), FFMA2 as in
+// k_dslash_x2; modes:
+//   EO_HOP      out = H in
+//   EO_CINV_HOP out = C^-1 H in                 (C = clover + mass of the output site)
+//   EO_SCHUR    out = C self - 1/4 H in         (self: the output parity's own field)
+// so that D_hat = C_oo - 1/4 H_oe C_ee^-1 H_eo is EO_CINV_HOP onto the even
+// sites followed by EO_SCHUR onto the odd ones.
+enum { EO_HOP = 0, EO_CINV_HOP = 1, EO_SCHUR = 2 };
+
+struct KArgsEO {
+    KArgs32 k;   // full-lattice geometry (k.V is the full volume), n, RHS pairs
+    int parity;  // parity of the output sites
+    int V2;      // V / 2
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, const float2 *__restrict__ M,
+                                                   const float2 *__restrict__ in, const float2 *__restrict__ self,
+                                                   float2 *__restrict__ out, KArgsEO e) {
+    const KArgs32 &a = e.k;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cb = item / a.G;
+    if (cb >= e.V2) return;
+    const int r0 = (item - cb * a.G) * 2;
+    // the output-parity site of the pair (2 cb, 2 cb + 1): x = 2k or 2k + 1
+    int c[4];
+    {
+        int q = 2 * cb;
+        c[0] = q % a.L[0];
+        q /= a.L[0];
+        c[1] = q % a.L[1];
+        q /= a.L[1];
+        c[2] = q % a.L[2];
+        c[3] = q / a.L[2];
+        if (((c[0] + c[1] + c[2] + c[3]) & 1) != e.parity) ++c[0];
+    }
+    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+    P2 acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const int L = a.L[mu], st = a.stride[mu];
+        const bool wrapF = (c[mu] == L - 1), wrapB = (c[mu] == 0);
+        const int sf = wrapF ? site - st * (L - 1) : site + st;
+        const int sb = wrapB ? site + st * (L - 1) : site - st;
+        const bool flipF = mu == 3 && wrapF && a.tb < 0;
+        const bool flipB = mu == 3 && wrapB && a.tb < 0;
+        // neighbours live in the other parity's half field, at index site / 2
+        if (mu == 0) {
+            hop_x2<0, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<0, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+        } else if (mu == 1) {
+            hop_x2<1, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<1, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+        } else if (mu == 2) {
+            hop_x2<2, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<2, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+        } else {
+            hop_x2<3, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<3, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+        }
+    }
+    const int64_t base = (int64_t)cb * 12 * a.n + r0;
+    if constexpr (MODE == EO_HOP) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) st_p2(out, base + (int64_t)i * a.n, acc[i]);
+    } else {
+        const float2 quarter = make_float2(-0.25f, -0.25f);
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi) {
+            P2 v[6], o[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                v[i] = MODE == EO_CINV_HOP ? acc[6 * chi + i] : ld_p2(self, base + (int64_t)(6 * chi + i) * a.n);
+            site_mat_x2(M, a.V, site, chi, v, o);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                P2 res = o[i];
+                if constexpr (MODE == EO_SCHUR) {
+                    const P2 ai = acc[6 * chi + i];
+                    res = {__ffma2_rn(quarter, ai.re, o[i].re), __ffma2_rn(quarter, ai.im, o[i].im)};
+                }
+                st_p2(out, base + (int64_t)(6 * chi + i) * a.n, res);
+            }
+        }
+    }
+}
+
+static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity) {
+    KArgsEO e;
+    KArgs32 &a = e.k;
+    for (int mu = 0; mu < 4; ++mu) a.L[mu] = lat.g.L[mu];
+    a.V = (int)lat.g.V;
+    a.n = n;
+    a.G = n / 2;
+    a.stride[0] = 1;
+    a.stride[1] = a.L[0];
+    a.stride[2] = a.L[0] * a.L[1];
+    a.stride[3] = a.L[0] * a.L[1] * a.L[2];
+    a.tb = lat.g.tb;
+    a.tsites = 1;
+    for (int mu = 0; mu < 4; ++mu) a.T[mu] = 1;
+    for (int mu = 0; mu < 3; ++mu) a.NT[mu] = a.L[mu];
+    e.parity = parity;
+    e.V2 = a.V / 2;
+    return e;
+}
+
+static void check_eo(const mrhs_lattice &lat, int n) {
+    for (int mu = 0; mu < 4; ++mu)
+        if (lat.g.L[mu] % 2) fail(MRHS_ERR_INVALID, "even-odd decomposition needs even lattice extents");
+    if (n < 2 || n % 2) fail(MRHS_ERR_INVALID, "even-odd operators take an even RHS count");
+    if (lat.g.V * 6LL * n >= (1LL << 31)) fail(MRHS_ERR_INVALID, "half-lattice field too large for 32-bit indexing");
+}
+
+template <int MODE>
+static void launch_eo(const mrhs_lattice &lat, const float2 *M, const float2 *in, const float2 *self, float2 *out,
+                      int n, int parity, cudaStream_t s) {
+    const KArgsEO e = eo_args(lat, n, parity);
+    const int64_t items = (int64_t)e.V2 * e.k.G;
+    MRHS_TIMED("k_eo_x2", s);
+    k_eo_x2<MODE><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(lat.U32.as<float2>(), M, in, self, out, e);
+    MRHS_LAUNCHED("k_eo_x2");
+}
+
+void hop_eo(const mrhs_lattice &lat, int out_parity, const void *in, void *out, int n, cudaStream_t s) {
+    check_eo(lat, n);
+    launch_eo<EO_HOP>(lat, nullptr, static_cast<const float2 *>(in), nullptr, static_cast<float2 *>(out), n,
+                      out_parity, s);
+}
+
+void schur_apply(mrhs_lattice &lat, const void *in_odd, void *out_odd, int n, cudaStream_t s) {
+    check_eo(lat, n);
+    if (!lat.has_clover) fail(MRHS_ERR_INVALID, "clover term not built");
+    if (lat.cinv_singular) fail(MRHS_ERR_INVALID, "a block of the clover term is singular: no even-odd inverse");
+    const size_t half = sizeof(float2) * (size_t)(lat.g.V / 2) * 12 * n;
+    if (lat.EOtmp.bytes < half) lat.EOtmp.alloc(half);
+    float2 *t_e = lat.EOtmp.as<float2>();
+    // t_e = C_ee^-1 H_eo psi_o, then out_o = C_oo psi_o - 1/4 H_oe t_e
+    launch_eo<EO_CINV_HOP>(lat, lat.Cinv32.as<float2>(), static_cast<const float2 *>(in_odd), nullptr, t_e, n, 0, s);
+    launch_eo<EO_SCHUR>(lat, lat.C32.as<float2>(), t_e, static_cast<const float2 *>(in_odd),
+                        static_cast<float2 *>(out_odd), n, 1, s);
+}
+
+int clover_inverse_error(const mrhs_lattice &lat) {
+    int e = 0;
+    MRHS_CUDA(cudaMemcpy(&e, lat.CinvErr.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    return e;
 }
 
 template <typename Real, typename TIn, int R, bool RESID, bool GENERAL>
@@ -702,12 +866,85 @@ __global__ void k_build_clover(const double2 *__restrict__ U, Geom g, double mas
     }
 }
 
+// Inverse of the site matrix C (clover + mass) per site and chirality block:
+// Gauss-Jordan elimination with partial pivoting in FP64 on the 6 x 6
+// Hermitian block, written back in the compact Hermitian layout of C.  A
+// pivot below 1e-300 (a singular block) sets *singular.
+__global__ void k_clover_inverse(const double2 *__restrict__ C64, int64_t V, double2 *__restrict__ I64,
+                                 float2 *__restrict__ I32, int *__restrict__ singular) {
+    const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (item >= 2 * V) return;
+    const int chi = (int)(item / V);
+    const int64_t site = item - chi * V;
+    cplx<double> A[6][12];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 12; ++j) A[i][j] = {0.0, 0.0};
+    for (int q = 0; q < 3; ++q) {
+        const double2 d = C64[(int64_t)(chi * 18 + q) * V + site];
+        A[2 * q][2 * q] = {d.x, 0.0};
+        A[2 * q + 1][2 * q + 1] = {d.y, 0.0};
+    }
+    int q = 3;
+    for (int i = 1; i < 6; ++i)
+        for (int j = 0; j < i; ++j, ++q) {
+            const double2 l = C64[(int64_t)(chi * 18 + q) * V + site];
+            A[i][j] = {l.x, l.y};
+            A[j][i] = {l.x, -l.y};
+        }
+    for (int i = 0; i < 6; ++i) A[i][6 + i] = {1.0, 0.0};
+    for (int col = 0; col < 6; ++col) {
+        int piv = col;
+        double best = A[col][col].re * A[col][col].re + A[col][col].im * A[col][col].im;
+        for (int r = col + 1; r < 6; ++r) {
+            const double m = A[r][col].re * A[r][col].re + A[r][col].im * A[r][col].im;
+            if (m > best) {
+                best = m;
+                piv = r;
+            }
+        }
+        if (!(best > 1e-300)) {
+            atomicExch(singular, 1);
+            return;
+        }
+        if (piv != col)
+            for (int j = 0; j < 12; ++j) {
+                const cplx<double> t = A[col][j];
+                A[col][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+        const cplx<double> p = A[col][col];
+        const cplx<double> pinv = {p.re / best, -p.im / best};
+        for (int j = 0; j < 12; ++j) A[col][j] = A[col][j] * pinv;
+        for (int r = 0; r < 6; ++r) {
+            if (r == col) continue;
+            const cplx<double> f = A[r][col];
+            for (int j = 0; j < 12; ++j) A[r][j] = A[r][j] - f * A[col][j];
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double2 d = make_double2(A[2 * k][6 + 2 * k].re, A[2 * k + 1][6 + 2 * k + 1].re);
+        I64[(int64_t)(chi * 18 + k) * V + site] = d;
+        I32[(int64_t)(chi * 18 + k) * V + site] = make_float2((float)d.x, (float)d.y);
+    }
+    q = 3;
+    for (int i = 1; i < 6; ++i)
+        for (int j = 0; j < i; ++j, ++q) {
+            const double2 l = make_double2(A[i][6 + j].re, A[i][6 + j].im);
+            I64[(int64_t)(chi * 18 + q) * V + site] = l;
+            I32[(int64_t)(chi * 18 + q) * V + site] = make_float2((float)l.x, (float)l.y);
+        }
+}
+
 void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s) {
     const int64_t V = lat.g.V;
     k_build_clover<<<ceil_div(V, 128), 128, 0, s>>>(lat.U64.as<double2>(), lat.g, mass, csw,
                                                      lat.C64.as<double2>(), lat.C32.as<float2>());
     MRHS_LAUNCHED("k_build_clover");
     split_df(lat.C64.ptr, lat.Cdf.ptr, V * 36, s);
+    MRHS_CUDA(cudaMemsetAsync(lat.CinvErr.ptr, 0, sizeof(int), s));
+    k_clover_inverse<<<ceil_div(2 * V, 128), 128, 0, s>>>(lat.C64.as<double2>(), V, lat.Cinv64.as<double2>(),
+                                                          lat.Cinv32.as<float2>(), lat.CinvErr.as<int>());
+    MRHS_LAUNCHED("k_clover_inverse");
 }
 
 }  // namespace mrhs

@@ -19,7 +19,12 @@ struct mrhs_lattice {
     // the same links and clover as float-float pairs (float4 per complex:
     // re hi, re lo, im hi, im lo) for the float-float operator
     mrhs::DeviceBuffer Udf, Cdf;
+    // inverse of the site matrix C per site, same compact layout as C (for the
+    // even-odd decomposition); CinvErr: int, set when a block was singular
+    mrhs::DeviceBuffer Cinv64, Cinv32, CinvErr;
+    mrhs::DeviceBuffer EOtmp;  // half-lattice scratch of the Schur operator
     bool has_gauge = false, has_clover = false;
+    bool cinv_singular = false;  // a block of C was singular (no even-odd inverse)
     double mass = 0.0, csw = 0.0;
 };
 
@@ -35,6 +40,14 @@ struct HopMask {
 };
 
 void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s);
+// Even-odd decomposition, FP32, even n, half-lattice fields [V/2][12][n]
+// (sites of one parity in lexicographic order, site s at index s / 2):
+// out = H in from the other parity (M_eooe), and out_o = D_hat in_o =
+// C_oo in_o - 1/4 H_oe C_ee^-1 H_eo in_o; clover_inverse_error: nonzero if a
+// block of C was singular when the inverse was built.
+void hop_eo(const mrhs_lattice &lat, int out_parity, const void *in, void *out, int n, cudaStream_t s);
+void schur_apply(mrhs_lattice &lat, const void *in_odd, void *out_odd, int n, cudaStream_t s);
+int clover_inverse_error(const mrhs_lattice &lat);
 // dst[i] = (hi, lo) float pairs of the FP64 complex src[i], i < count
 void split_df(const void *src_c128, void *dst_f4, int64_t count, cudaStream_t s);
 // out = D in (y == nullptr) or y - D in; `in` FP32, out and y FP64, float-float arithmetic

@@ -108,6 +108,8 @@ PROTOTYPES = {
     "mrhs_last_error": (C.c_char_p, []),
     "mrhs_kernel_launch_count": (C.c_uint64, []),
     "mrhs_kernel_timer_start": (_I, [C.c_char_p]),
+    "mrhs_apply_hop_eo": (_I, [_P, _I, _P, _P, _I, _P]),
+    "mrhs_apply_schur": (_I, [_P, _P, _P, _I, _P]),
     "mrhs_kernel_timer_stop": (_I, [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mrhs_create_lattice": (_I, [C.POINTER(C.c_int), _I, _I, C.POINTER(_P)]),
     "mrhs_destroy_lattice": (None, [_P]),
@@ -220,6 +222,14 @@ def mrhs_build_clover(lat, mass, csw):
 
 def mrhs_get_clover(lat, out_host):
     _check(lib().mrhs_get_clover(lat, _ptr(out_host)))
+
+
+def mrhs_apply_hop_eo(lat, out_parity, in_dev, out_dev, nrhs, stream=None):
+    _check(lib().mrhs_apply_hop_eo(lat, int(out_parity), _ptr(in_dev), _ptr(out_dev), int(nrhs), _stream(stream)))
+
+
+def mrhs_apply_schur(lat, in_dev, out_dev, nrhs, stream=None):
+    _check(lib().mrhs_apply_schur(lat, _ptr(in_dev), _ptr(out_dev), int(nrhs), _stream(stream)))
 
 
 def mrhs_apply_D(lat, in_dev, out_dev, nrhs, prec, stream=None):
