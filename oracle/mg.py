@@ -14,6 +14,10 @@ the setup or the cycle, so the oracle fixes these readings:
         cycle preconditioned by the V-cycle of level l+1;
     z0 = P_l e;
     z = `smooth_m` iterations of GMRES on A_l v from z0 (post-smoothing only);
+  with `smoother_evenodd` the fine level's post-smoothing is instead
+    r = v - D z0;  z = z0 + delta,  delta the even-odd solution of D delta = r
+    with `smooth_m` GMRES iterations (from 0) on the Schur complement D_hat
+    (evenodd.py: right-hand side b_hat, D_hat delta_o = b_hat, reconstruction);
 * outer solve: FGMRES(`outer_m`) on the fine operator, restarted from the
   true residual until ||b - D x|| / ||b|| <= tol for every RHS.
 """
@@ -23,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import coarse, krylov, wilson
+from . import coarse, evenodd, krylov, wilson
 from .conventions import FINE_CHIRALITY
 
 
@@ -40,6 +44,7 @@ class MGParams:
     outer_m: int = 8
     tol: float = 1e-10
     max_outer_cycles: int = 100
+    smoother_evenodd: bool = False
 
 
 @dataclass
@@ -51,6 +56,7 @@ class Level:
     stencil: np.ndarray = None   # (V, 9, dof, dof) on coarse levels
     P: np.ndarray = None         # prolongator to the next level
     block: tuple = None
+    eo: tuple = None             # fine level: (U, site matrix C, dims, antiperiodic) for the even-odd smoother
 
 
 def setup_nullvecs(apply_A, v0: np.ndarray, sweeps: int, m: int) -> np.ndarray:
@@ -74,7 +80,8 @@ def build_hierarchy(U, dims, mass, csw, params: MGParams, init_vecs,
     def fine(psi):
         return wilson.apply_D(U, clover, psi, dims, mass, antiperiodic)
 
-    levels = [Level(tuple(dims), 12, fine, FINE_CHIRALITY)]
+    levels = [Level(tuple(dims), 12, fine, FINE_CHIRALITY,
+                    eo=(U, evenodd.site_matrix(clover, mass), tuple(dims), antiperiodic))]
     for l, (block, N) in enumerate(zip(params.blocks, params.nvec)):
         lev = levels[l]
         if nullvecs is not None:
@@ -108,7 +115,18 @@ def vcycle(levels, l: int, v: np.ndarray, params: MGParams) -> np.ndarray:
         e = krylov.fgmres_fixed(nxt.apply, c, lambda u: vcycle(levels, l + 1, u, params),
                                 params.inter_m)
     z0 = coarse.prolong(lev.P, e, lev.dims, lev.block)
+    if l == 0 and params.smoother_evenodd:
+        return z0 + evenodd_smooth(lev, v - lev.apply(z0), params.smooth_m)
     return krylov.gmres(lev.apply, v, z0, params.smooth_m, 1)
+
+
+def evenodd_smooth(lev, r: np.ndarray, m: int) -> np.ndarray:
+    """delta with D delta ~= r: m GMRES iterations on D_hat delta_o = b_hat from 0,
+    then delta_e from the reconstruction formula."""
+    U, C, dims, ap = lev.eo
+    bhat = evenodd.schur_rhs(U, C, r, dims, ap)
+    d_o = krylov.gmres(lambda psi: evenodd.schur_apply(U, C, psi, dims, ap), bhat, np.zeros_like(bhat), m, 1)
+    return evenodd.schur_reconstruct(U, C, r, d_o, dims, ap)
 
 
 def solve(levels, b: np.ndarray, params: MGParams):

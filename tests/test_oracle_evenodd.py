@@ -113,3 +113,20 @@ def test_planted_mistakes_are_caught(old, new, pin):
     dims, hot, antiperiodic = CASES[0]
     err = _schur_error(mod, dims, hot, antiperiodic) if pin == "schur" else _solve_error(mod, dims, hot, antiperiodic)
     assert err > 1e-6
+
+
+def test_evenodd_smoother_in_the_full_krylov_limit_solves_exactly():
+    """With as many GMRES steps as odd-site unknowns, the even-odd smoother
+    returns delta = D^-1 r (dense solve), so z0 + delta solves D z = v."""
+    from oracle import mg as omg
+
+    dims, mass, csw = (2, 2, 2, 4), -0.3, 1.1
+    U = synth.gauge_haar(dims, 21)
+    clover = wilson.clover_term(U, dims, csw)
+    lev = omg.Level(dims, 12, None, None, eo=(U, eo.site_matrix(clover, mass), dims, True))
+    V = wilson.volume(dims)
+    r = synth.gaussian_field(V, 12, 2, 22)
+    delta = omg.evenodd_smooth(lev, r, 12 * V // 2)
+    D = wilson.dense_D(U, clover, dims, mass)
+    ref = np.linalg.solve(D, r.reshape(-1, 2)).reshape(r.shape)
+    assert np.abs(delta - ref).max() / np.abs(ref).max() < 1e-9
