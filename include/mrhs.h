@@ -220,6 +220,10 @@ typedef struct {
     int outer_op_precision;                /* outer Arnoldi applies D z: MRHS_DF64
                                               (float-float) or MRHS_FP64; the
                                               true residual is always FP64        */
+    int smoother_evenodd;                  /* 1: the fine post-smoother runs GMRES on
+                                              the even-odd Schur complement D_hat
+                                              (even extents and nrhs; otherwise,
+                                              and with 0, GMRES on D)             */
     uint64_t seed;                         /* start vectors when none supplied    */
     /* Optional host start vectors per level, [V_l][dof_l][n_vec[l]] complex
      * FP64 (dof_0 = 12, dof_l = nc of level l).  NULL entries: random. */

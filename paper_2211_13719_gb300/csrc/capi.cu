@@ -214,7 +214,12 @@ mrhs_status mrhs_apply_schur(mrhs_lattice *lat, const void *in_dev, void *out_de
     MRHS_API_BEGIN
     check_apply(lat, in_dev, out_dev, nrhs, MRHS_FP32);
     DeviceGuard dg(lat->device);
-    schur_apply(*lat, in_dev, out_dev, nrhs, static_cast<cudaStream_t>(stream));
+    const size_t half = sizeof(float2) * (size_t)(lat->g.V / 2) * 12 * nrhs;
+    if (lat->EOtmp.bytes < half) {
+        MRHS_CUDA(cudaDeviceSynchronize());  // the old scratch may still be in use by earlier calls
+        lat->EOtmp.alloc(half);
+    }
+    schur_apply(*lat, in_dev, out_dev, nrhs, lat->EOtmp.ptr, static_cast<cudaStream_t>(stream));
     MRHS_API_END
 }
 

@@ -493,9 +493,13 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
 //   EO_HOP      out = H in
 //   EO_CINV_HOP out = C^-1 H in                 (C = clover + mass of the output site)
 //   EO_SCHUR    out = C self - 1/4 H in         (self: the output parity's own field)
+//   EO_AXPY_HOP      out = self + 1/2 H in
+//   EO_CINV_AXPY_HOP out = C^-1 (self + 1/2 H in)
 // so that D_hat = C_oo - 1/4 H_oe C_ee^-1 H_eo is EO_CINV_HOP onto the even
-// sites followed by EO_SCHUR onto the odd ones.
-enum { EO_HOP = 0, EO_CINV_HOP = 1, EO_SCHUR = 2 };
+// sites followed by EO_SCHUR onto the odd ones, and the even-odd solution of
+// D x = b takes b_hat = b_o + 1/2 H_oe C_ee^-1 b_e (EO_AXPY_HOP onto the odd
+// sites) and x_e = C_ee^-1 (b_e + 1/2 H_eo x_o) (EO_CINV_AXPY_HOP).
+enum { EO_HOP = 0, EO_CINV_HOP = 1, EO_SCHUR = 2, EO_AXPY_HOP = 3, EO_CINV_AXPY_HOP = 4 };
 
 struct KArgsEO {
     KArgs32 k;   // full-lattice geometry (k.V is the full volume), n, RHS pairs
@@ -555,6 +559,22 @@ __global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, 
     if constexpr (MODE == EO_HOP) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) st_p2(out, base + (int64_t)i * a.n, acc[i]);
+    } else if constexpr (MODE == EO_AXPY_HOP || MODE == EO_CINV_AXPY_HOP) {
+        const float2 half = make_float2(0.5f, 0.5f);
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi) {
+            P2 v[6], o[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const P2 y = ld_p2(self, base + (int64_t)(6 * chi + i) * a.n);
+                const P2 ai = acc[6 * chi + i];
+                v[i] = {__ffma2_rn(half, ai.re, y.re), __ffma2_rn(half, ai.im, y.im)};
+            }
+            if constexpr (MODE == EO_CINV_AXPY_HOP) site_mat_x2(M, a.V, site, chi, v, o);
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+                st_p2(out, base + (int64_t)(6 * chi + i) * a.n, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
+        }
     } else {
         const float2 quarter = make_float2(-0.25f, -0.25f);
 #pragma unroll
@@ -620,17 +640,115 @@ void hop_eo(const mrhs_lattice &lat, int out_parity, const void *in, void *out, 
                       out_parity, s);
 }
 
-void schur_apply(mrhs_lattice &lat, const void *in_odd, void *out_odd, int n, cudaStream_t s) {
+void schur_apply(const mrhs_lattice &lat, const void *in_odd, void *out_odd, int n, void *tmp_even, cudaStream_t s) {
     check_eo(lat, n);
     if (!lat.has_clover) fail(MRHS_ERR_INVALID, "clover term not built");
     if (lat.cinv_singular) fail(MRHS_ERR_INVALID, "a block of the clover term is singular: no even-odd inverse");
-    const size_t half = sizeof(float2) * (size_t)(lat.g.V / 2) * 12 * n;
-    if (lat.EOtmp.bytes < half) lat.EOtmp.alloc(half);
-    float2 *t_e = lat.EOtmp.as<float2>();
+    float2 *t_e = static_cast<float2 *>(tmp_even);
     // t_e = C_ee^-1 H_eo psi_o, then out_o = C_oo psi_o - 1/4 H_oe t_e
     launch_eo<EO_CINV_HOP>(lat, lat.Cinv32.as<float2>(), static_cast<const float2 *>(in_odd), nullptr, t_e, n, 0, s);
     launch_eo<EO_SCHUR>(lat, lat.C32.as<float2>(), t_e, static_cast<const float2 *>(in_odd),
                         static_cast<float2 *>(out_odd), n, 1, s);
+}
+
+// the even and the odd site of the pair (2 cb, 2 cb + 1)
+__device__ __forceinline__ void eo_pair_sites(const KArgs32 &a, int cb, int &even, int &odd) {
+    int q = 2 * cb;
+    const int x = q % a.L[0];
+    q /= a.L[0];
+    const int y = q % a.L[1];
+    q /= a.L[1];
+    const int z = q % a.L[2];
+    const int t = q / a.L[2];
+    const bool first_even = ((x + y + z + t) & 1) == 0;
+    even = first_even ? 2 * cb : 2 * cb + 1;
+    odd = first_even ? 2 * cb + 1 : 2 * cb;
+}
+
+// full field r -> r_e, r_o and t_e = C_ee^-1 r_e (half fields)
+__global__ void __launch_bounds__(128) k_eo_split(const float2 *__restrict__ r, const float2 *__restrict__ Cinv,
+                                                   float2 *__restrict__ re, float2 *__restrict__ ro,
+                                                   float2 *__restrict__ te, KArgsEO e) {
+    const KArgs32 &a = e.k;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cb = item / a.G;
+    if (cb >= e.V2) return;
+    const int r0 = (item - cb * a.G) * 2;
+    int se, so;
+    eo_pair_sites(a, cb, se, so);
+    const int64_t hb = (int64_t)cb * 12 * a.n + r0;
+    const int64_t fe = (int64_t)se * 12 * a.n + r0, fo = (int64_t)so * 12 * a.n + r0;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) st_p2(ro, hb + (int64_t)i * a.n, ld_p2(r, fo + (int64_t)i * a.n));
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        P2 v[6], o[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            v[i] = ld_p2(r, fe + (int64_t)(6 * chi + i) * a.n);
+            st_p2(re, hb + (int64_t)(6 * chi + i) * a.n, v[i]);
+        }
+        site_mat_x2(Cinv, a.V, se, chi, v, o);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) st_p2(te, hb + (int64_t)(6 * chi + i) * a.n, o[i]);
+    }
+}
+
+// z += (d_e on the even sites, d_o on the odd sites)
+__global__ void __launch_bounds__(128) k_eo_merge_add(const float2 *__restrict__ de, const float2 *__restrict__ dod,
+                                                       float2 *__restrict__ z, KArgsEO e) {
+    const KArgs32 &a = e.k;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const int cb = item / a.G;
+    if (cb >= e.V2) return;
+    const int r0 = (item - cb * a.G) * 2;
+    int se, so;
+    eo_pair_sites(a, cb, se, so);
+    const int64_t hb = (int64_t)cb * 12 * a.n + r0;
+    const int64_t fe = (int64_t)se * 12 * a.n + r0, fo = (int64_t)so * 12 * a.n + r0;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        const P2 ze = ld_p2(z, fe + (int64_t)i * a.n), zo = ld_p2(z, fo + (int64_t)i * a.n);
+        const P2 ae = ld_p2(de, hb + (int64_t)i * a.n), ao = ld_p2(dod, hb + (int64_t)i * a.n);
+        st_p2(z, fe + (int64_t)i * a.n, p2add(ze, ae));
+        st_p2(z, fo + (int64_t)i * a.n, p2add(zo, ao));
+    }
+}
+
+bool eo_supported(const mrhs_lattice &lat, int n) {
+    for (int mu = 0; mu < 4; ++mu)
+        if (lat.g.L[mu] % 2) return false;
+    return n >= 2 && n % 2 == 0 && !lat.cinv_singular && lat.g.V * 6LL * n < (1LL << 31);
+}
+
+void eo_split(const mrhs_lattice &lat, const void *r, void *re, void *ro, void *te, int n, cudaStream_t s) {
+    check_eo(lat, n);
+    const KArgsEO e = eo_args(lat, n, 0);
+    const int64_t items = (int64_t)e.V2 * e.k.G;
+    k_eo_split<<<(unsigned)((items + 127) / 128), 128, 0, s>>>(
+        static_cast<const float2 *>(r), lat.Cinv32.as<float2>(), static_cast<float2 *>(re),
+        static_cast<float2 *>(ro), static_cast<float2 *>(te), e);
+    MRHS_LAUNCHED("k_eo_split");
+}
+
+void eo_axpy_hop(const mrhs_lattice &lat, int out_parity, const void *self, const void *in, void *out, bool cinv,
+                 int n, cudaStream_t s) {
+    check_eo(lat, n);
+    if (cinv)
+        launch_eo<EO_CINV_AXPY_HOP>(lat, lat.Cinv32.as<float2>(), static_cast<const float2 *>(in),
+                                    static_cast<const float2 *>(self), static_cast<float2 *>(out), n, out_parity, s);
+    else
+        launch_eo<EO_AXPY_HOP>(lat, nullptr, static_cast<const float2 *>(in), static_cast<const float2 *>(self),
+                               static_cast<float2 *>(out), n, out_parity, s);
+}
+
+void eo_merge_add(const mrhs_lattice &lat, const void *de, const void *d_o, void *z, int n, cudaStream_t s) {
+    check_eo(lat, n);
+    const KArgsEO e = eo_args(lat, n, 0);
+    const int64_t items = (int64_t)e.V2 * e.k.G;
+    k_eo_merge_add<<<(unsigned)((items + 127) / 128), 128, 0, s>>>(
+        static_cast<const float2 *>(de), static_cast<const float2 *>(d_o), static_cast<float2 *>(z), e);
+    MRHS_LAUNCHED("k_eo_merge_add");
 }
 
 int clover_inverse_error(const mrhs_lattice &lat) {

@@ -46,8 +46,18 @@ void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s);
 // C_oo in_o - 1/4 H_oe C_ee^-1 H_eo in_o; clover_inverse_error: nonzero if a
 // block of C was singular when the inverse was built.
 void hop_eo(const mrhs_lattice &lat, int out_parity, const void *in, void *out, int n, cudaStream_t s);
-void schur_apply(mrhs_lattice &lat, const void *in_odd, void *out_odd, int n, cudaStream_t s);
+// tmp_even: a half field of n RHS, overwritten
+void schur_apply(const mrhs_lattice &lat, const void *in_odd, void *out_odd, int n, void *tmp_even, cudaStream_t s);
 int clover_inverse_error(const mrhs_lattice &lat);
+// even-odd solution pieces (FP32, even n): eo_supported tells whether the lattice
+// and n allow them; eo_split: r (full) -> r_e, r_o, t_e = C_ee^-1 r_e (halves);
+// eo_axpy_hop: out = self + 1/2 H in onto out_parity (cinv: C^-1 of that);
+// eo_merge_add: z (full) += (d_e, d_o)
+bool eo_supported(const mrhs_lattice &lat, int n);
+void eo_split(const mrhs_lattice &lat, const void *r, void *re, void *ro, void *te, int n, cudaStream_t s);
+void eo_axpy_hop(const mrhs_lattice &lat, int out_parity, const void *self, const void *in, void *out, bool cinv,
+                 int n, cudaStream_t s);
+void eo_merge_add(const mrhs_lattice &lat, const void *de, const void *d_o, void *z, int n, cudaStream_t s);
 // dst[i] = (hi, lo) float pairs of the FP64 complex src[i], i < count
 void split_df(const void *src_c128, void *dst_f4, int64_t count, cudaStream_t s);
 // out = D in (y == nullptr) or y - D in; `in` FP32, out and y FP64, float-float arithmetic

@@ -73,6 +73,25 @@ struct CoarseOp : Op {
     }
 };
 
+// D_hat = C_oo - 1/4 H_oe C_ee^-1 H_eo on odd half-lattice fields (the fine
+// level's even-odd Schur complement); `tmp` is its own half-field scratch
+struct SchurOp : Op {
+    const mrhs_lattice *lat;
+    DeviceBuffer tmp;
+    SchurOp(const mrhs_lattice *l, int nmax) : lat(l) {
+        rows = l->g.V / 2 * 12;
+        tmp.alloc(sizeof(float2) * (size_t)rows * nmax);
+    }
+    void apply(const float2 *in, float2 *out, int n, cudaStream_t s) override {
+        schur_apply(*lat, in, out, n, tmp.ptr, s);
+    }
+    void residual(const float2 *x, const float2 *b, float2 *r, int n, cudaStream_t s) override {
+        schur_apply(*lat, x, r, n, tmp.ptr, s);
+        scale_real(MRHS_FP32, -1.0, r, rows * n, s);
+        axpy(MRHS_FP32, 1.0, b, r, rows * n, s);
+    }
+};
+
 struct Precond {
     virtual ~Precond() = default;
     virtual void apply(const float2 *v, float2 *z, int n, cudaStream_t s) = 0;
@@ -166,6 +185,10 @@ struct LevelWork {
     DeviceBuffer rhs, sol;  // coarse levels: restricted residual and coarse solution
     KWork solve;            // coarse levels: GMRES (coarsest) or FGMRES (intermediate)
     KWork smooth;           // levels with a coarser level: post-smoother GMRES
+    // fine level, even-odd smoother: full residual, half fields r_e, r_o,
+    // C_ee^-1 r_e, b_hat, delta_e, delta_o, and GMRES on D_hat
+    DeviceBuffer eo_r, eo_re, eo_ro, eo_te, eo_bh, eo_de, eo_do;
+    KWork eo_smooth;
 };
 
 struct GraphKey {
@@ -190,6 +213,7 @@ struct mrhs_mg {
     std::vector<Level> lev;
     std::vector<LevelWork> work;
     std::vector<std::unique_ptr<Op>> ops;
+    std::unique_ptr<SchurOp> schur;  // the fine level's even-odd smoother operator (when enabled)
     bool bf16 = false;
     // inner FP32 MG-FGMRES on the fine level
     KWork inner;
@@ -284,7 +308,21 @@ void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t 
     }
     {
         EventTimer t(prof, s, &mg.t_fine);
-        krylov_cycle(*mg.ops[l], nullptr, v, z, n, mg.p.smooth_m, mg.work[l].smooth, s, false, nullptr);
+        if (l == 0 && mg.schur && eo_supported(*mg.lat, n)) {
+            // even-odd smoother: z += delta, D delta ~= r = v - D z through smooth_m GMRES
+            // steps on D_hat delta_o = b_hat = r_o + 1/2 H_oe C_ee^-1 r_e from 0, then
+            // delta_e = C_ee^-1 (r_e + 1/2 H_eo delta_o)
+            LevelWork &W = mg.work[0];
+            mg.ops[0]->residual(z, v, W.eo_r.as<float2>(), n, s);
+            eo_split(*mg.lat, W.eo_r.ptr, W.eo_re.ptr, W.eo_ro.ptr, W.eo_te.ptr, n, s);
+            eo_axpy_hop(*mg.lat, 1, W.eo_ro.ptr, W.eo_te.ptr, W.eo_bh.ptr, false, n, s);
+            krylov_cycle(*mg.schur, nullptr, W.eo_bh.as<float2>(), W.eo_do.as<float2>(), n, mg.p.smooth_m,
+                         W.eo_smooth, s, true, nullptr);
+            eo_axpy_hop(*mg.lat, 0, W.eo_re.ptr, W.eo_do.ptr, W.eo_de.ptr, true, n, s);
+            eo_merge_add(*mg.lat, W.eo_de.ptr, W.eo_do.ptr, z, n, s);
+        } else {
+            krylov_cycle(*mg.ops[l], nullptr, v, z, n, mg.p.smooth_m, mg.work[l].smooth, s, false, nullptr);
+        }
     }
     if (l == 0) mg.vcycles++;
 }
@@ -384,6 +422,7 @@ void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
         fail(MRHS_ERR_INVALID, "coarse_precision must be FP32, FP16 or BF16");
     if (p.outer_op_precision != MRHS_DF64 && p.outer_op_precision != MRHS_FP64)
         fail(MRHS_ERR_INVALID, "outer_op_precision must be DF64 or FP64");
+    if (p.smoother_evenodd != 0 && p.smoother_evenodd != 1) fail(MRHS_ERR_INVALID, "smoother_evenodd must be 0 or 1");
     if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
 }
 
@@ -453,6 +492,15 @@ void alloc_workspace(mrhs_mg &mg) {
             else W.solve.init(mg.p.inter_m, L.rows(), nmax, true);
         }
         if (l < mg.nlev - 1) W.smooth.init(mg.p.smooth_m, L.rows(), nmax, false);
+    }
+    if (mg.p.smoother_evenodd && eo_supported(*mg.lat, 2)) {
+        LevelWork &W = mg.work[0];
+        const int64_t hrows = mg.lat->g.V / 2 * 12;
+        const size_t hb = sizeof(float2) * (size_t)hrows * nmax;
+        W.eo_r.alloc(2 * hb);
+        for (DeviceBuffer *b : {&W.eo_re, &W.eo_ro, &W.eo_te, &W.eo_bh, &W.eo_de, &W.eo_do}) b->alloc(hb);
+        W.eo_smooth.init(mg.p.smooth_m, hrows, nmax, false);
+        mg.schur.reset(new SchurOp(mg.lat, nmax));
     }
     const int64_t rows = mg.lev[0].rows();
     mg.inner.init(mg.p.inner_m, rows, nmax, true);
@@ -661,6 +709,7 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->max_rhs = 48;
     p->use_graph = 1;
     p->outer_op_precision = MRHS_DF64;
+    p->smoother_evenodd = 0;
     p->seed = 1234;
 }
 

@@ -64,6 +64,7 @@ class MgParams(C.Structure):
         ("max_rhs", C.c_int),
         ("use_graph", C.c_int),
         ("outer_op_precision", C.c_int),
+        ("smoother_evenodd", C.c_int),
         ("seed", C.c_uint64),
         ("init_vecs", C.c_void_p * (MAX_LEVELS - 1)),
     ]

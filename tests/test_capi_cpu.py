@@ -55,6 +55,7 @@ def test_default_params_are_sane(lib):
     assert p.n_vec[0] >= 1 and p.outer_m >= 1 and p.max_rhs >= 1
     assert p.coarse_precision in (mrhs.MRHS_FP32, mrhs.MRHS_FP16, mrhs.MRHS_BF16)
     assert p.outer_op_precision in (mrhs.MRHS_DF64, mrhs.MRHS_FP64)
+    assert p.smoother_evenodd in (0, 1)
 
 
 def test_kernel_timer_state_without_gpu(lib):

@@ -84,8 +84,10 @@ def test_two_level_rows(dims, blocks, nvec):
         mrhs.mrhs_destroy_lattice(lat)
 
 
-def test_three_level_second_galerkin_and_vcycle():
-    dims, mass, csw, n = (8, 8, 8, 8), -0.2, 1.0, 3
+@pytest.mark.parametrize("evenodd", [False, True])
+def test_three_level_second_galerkin_and_vcycle(evenodd):
+    dims, mass, csw = (8, 8, 8, 8), -0.2, 1.0
+    n = 4 if evenodd else 3      # the even-odd smoother takes an even RHS count
     blocks, nvec = [(2, 2, 2, 2), (2, 2, 2, 2)], [6, 4]
     U = synth.gauge_exp(dims, 0.4, 1001)
     V = wilson.volume(dims)
@@ -94,11 +96,13 @@ def test_three_level_second_galerkin_and_vcycle():
     v0 = synth.gaussian_field(V, 12, nvec[0], 3101)
     v1 = synth.gaussian_field(wilson.volume(d1), 2 * nvec[0], nvec[1], 3102)
     params = dict(n_levels=3, blocks=blocks, nvec=nvec, setup_sweeps=0, max_rhs=4, smooth_m=3,
-                  coarse_m=5, coarse_cycles=1, inter_m=2, coarse_precision=mrhs.MRHS_FP32, use_graph=0)
+                  coarse_m=5, coarse_cycles=1, inter_m=2, coarse_precision=mrhs.MRHS_FP32, use_graph=0,
+                  smoother_evenodd=int(evenodd))
     lat = make_lattice(U, dims, mass, csw)
     mg = make_mg(lat, params, [v0, v1])
     try:
-        op = omg.MGParams(blocks=blocks, nvec=nvec, smooth_m=3, coarse_m=5, coarse_cycles=1, inter_m=2)
+        op = omg.MGParams(blocks=blocks, nvec=nvec, smooth_m=3, coarse_m=5, coarse_cycles=1, inter_m=2,
+                          smoother_evenodd=evenodd)
         levels = omg.build_hierarchy(U, dims, mass, csw, op, None, nullvecs=[v0, v1])
         nc2 = 2 * nvec[1]
         Ag = np.zeros((wilson.volume(d2), 9, nc2, nc2), np.complex128)

@@ -85,6 +85,21 @@ def test_outer_operator_precisions_agree(problem):
     assert np.all(err <= 1e-7), err
 
 
+def test_evenodd_smoother_solve(problem):
+    """With the even-odd post-smoother the solve still reaches the FP64 true
+    residual, and its solution agrees with the default smoother's."""
+    U, b, v0 = problem
+    C = wilson.clover_term(U, DIMS, CSW)
+    xs = []
+    for eo in (1, 0):
+        (x, rel, st), = _gpu_solve(U, b, v0, [list(range(NRHS))], smoother_evenodd=eo)
+        r = b - wilson.apply_D(U, C, x, DIMS, MASS)
+        assert np.all(krylov.norms(r) / krylov.norms(b) <= 1e-10)
+        xs.append(x)
+    err = krylov.norms(xs[0] - xs[1]) / krylov.norms(xs[1])
+    assert np.all(err <= 1e-7), err
+
+
 def test_nonzero_start_vector(problem):
     """A nonzero initial x takes the FP64 residual path (no zero-start shortcut)."""
     U, b, v0 = problem
