@@ -374,7 +374,9 @@ struct FinePrecond : Precond {
 };
 
 // FP32 MG-preconditioned FGMRES on the fine level: x = approx D^{-1} b.
-int inner_solve(mrhs_mg &mg, const float2 *b, float2 *x, int n, cudaStream_t s) {
+// rel[r]: relative residual reduction asked of RHS r (the inner FGMRES stops
+// when every RHS has reached its own)
+int inner_solve(mrhs_mg &mg, const float2 *b, float2 *x, int n, const std::vector<double> &rel, cudaStream_t s) {
     Op &A = *mg.ops[0];
     FinePrecond M(&mg);
     const int64_t F = A.rows * n;
@@ -384,7 +386,7 @@ int inner_solve(mrhs_mg &mg, const float2 *b, float2 *x, int n, cudaStream_t s) 
     norm2(MRHS_FP32, b, A.rows, n, mg.inner.ks.beta2.as<double>(), mg.inner.sc, s);
     MRHS_CUDA(cudaMemcpyAsync(bn, mg.inner.ks.beta2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     MRHS_CUDA(cudaStreamSynchronize(s));
-    for (int r = 0; r < n; ++r) target[r] = mg.p.inner_tol * std::sqrt(bn[r]);
+    for (int r = 0; r < n; ++r) target[r] = rel[r] * std::sqrt(bn[r]);
     HostCheck chk{target, mg.pinned + mg.nmax};
     int total = 0;
     bool first = true;
@@ -533,7 +535,7 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
     float2 *Z0 = mg.oZ.as<float2>();
     double *hbn2 = mg.pinned;          // ||b||^2
     double *hres = mg.pinned + mg.nmax;
-    std::vector<double> target(n), rel(n, 0.0), relest(n, 0.0);
+    std::vector<double> target(n), rel(n, 0.0), relest(n, 0.0), cur_res(n, 0.0), inner_rel(n, 0.0);
     mg.vcycles = 0;
     int outer = 0, inner_total = 0;
     norm2(MRHS_FP64, b, rows, n, mg.obn2.as<double>(), mg.osc, s);
@@ -574,13 +576,25 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
         if (converged || outer >= cap) break;
         krylov_start(mg.oks, n, s);
         scale_inv_sqrt(MRHS_FP64, V0, V0, mg.oks.beta2.as<double>(), rows, n, s);
+        for (int r = 0; r < n; ++r) cur_res[r] = std::sqrt(hres[r]);
         int steps = mg.om;
         for (int j = 0; j < mg.om; ++j) {
             float2 *zj = Z0 + (size_t)j * F;
             double2 *vj = V0 + (size_t)j * F;
             double2 *wj = V0 + (size_t)(j + 1) * F;
             cast(MRHS_FP32, mg.inner_b.ptr, MRHS_FP64, vj, F, s);
-            inner_total += inner_solve(mg, mg.inner_b.as<float2>(), zj, n, s);
+            // inner accuracy per RHS: inner_tol on the first outer step; later, the
+            // reduction that takes RHS r from its current residual to its target
+            // (clamped to [inner_tol / 4, 0.1]): looser when earlier steps overshot,
+            // tighter when one more step must finish the solve
+            for (int r = 0; r < n; ++r) {
+                if (outer == 0 || !(cur_res[r] > 0.0)) {
+                    inner_rel[r] = mg.p.inner_tol;
+                } else {
+                    inner_rel[r] = std::min(0.1, std::max(0.25 * mg.p.inner_tol, target[r] / cur_res[r]));
+                }
+            }
+            inner_total += inner_solve(mg, mg.inner_b.as<float2>(), zj, n, inner_rel, s);
             // w = D z_j: z_j is FP32, w FP64 (float-float or FP64 arithmetic)
             dslash(lat, mg.p.outer_op_precision == MRHS_DF64 ? MRHS_DF64 : MRHS_FP64, MRHS_FP32, zj, wj, nullptr, n,
                    s);
@@ -594,6 +608,7 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
             ++outer;
             HostCheck chk{target.data(), hres};
             bool halt = chk.test(mg.oks, n, s) || outer >= cap;
+            for (int r = 0; r < n; ++r) cur_res[r] = hres[r];
             if (!halt && stop) {
                 for (int r = 0; r < n; ++r) relest[r] = bn2[r] > 0 ? hres[r] / std::sqrt(bn2[r]) : 0.0;
                 halt = stop(relest.data(), n);
@@ -696,10 +711,10 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->n_vec[1] = 32;
     p->setup_sweeps = 6;
     p->setup_m = 8;
-    p->smooth_m = 4;
-    p->coarse_m = 12;
+    p->smooth_m = 3;
+    p->coarse_m = 14;
     p->coarse_cycles = 1;
-    p->inter_m = 3;
+    p->inter_m = 4;
     p->inner_m = 8;
     p->inner_max_iters = 200;
     p->inner_tol = 1e-5;
@@ -709,7 +724,7 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->max_rhs = 48;
     p->use_graph = 1;
     p->outer_op_precision = MRHS_DF64;
-    p->smoother_evenodd = 0;
+    p->smoother_evenodd = 1;
     p->seed = 1234;
 }
 
