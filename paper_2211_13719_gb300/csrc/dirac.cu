@@ -513,22 +513,32 @@ __global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, 
                                                    float2 *__restrict__ out, KArgsEO e) {
     const KArgs32 &a = e.k;
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cb = item / a.G;
-    if (cb >= e.V2) return;
-    const int r0 = (item - cb * a.G) * 2;
-    // the output-parity site of the pair (2 cb, 2 cb + 1): x = 2k or 2k + 1
+    const int visit = item / a.G;
+    if (visit >= e.V2) return;
+    const int r0 = (item - visit * a.G) * 2;
+    // visit order: tiles of 2 x T[1] x T[2] x T[3] sites (one output site per x
+    // pair), tiles x-fastest, as the full stencil's tile order; x = 2k or 2k + 1
+    // is the member of the pair with the output parity
     int c[4];
     {
-        int q = 2 * cb;
-        c[0] = q % a.L[0];
-        q /= a.L[0];
-        c[1] = q % a.L[1];
-        q /= a.L[1];
-        c[2] = q % a.L[2];
-        c[3] = q / a.L[2];
+        const int tile = visit / a.tsites;
+        int q = visit - tile * a.tsites;
+        int tq = tile;
+        const int t0 = tq % a.NT[0];
+        tq /= a.NT[0];
+        const int t1 = tq % a.NT[1];
+        tq /= a.NT[1];
+        const int t2 = tq % a.NT[2];
+        const int t3 = tq / a.NT[2];
+        c[1] = t1 * a.T[1] + q % a.T[1];
+        q /= a.T[1];
+        c[2] = t2 * a.T[2] + q % a.T[2];
+        c[3] = t3 * a.T[3] + q / a.T[2];
+        c[0] = 2 * t0;
         if (((c[0] + c[1] + c[2] + c[3]) & 1) != e.parity) ++c[0];
     }
     const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+    const int cb = site >> 1;
     P2 acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -609,9 +619,18 @@ static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity) {
     a.stride[2] = a.L[0] * a.L[1];
     a.stride[3] = a.L[0] * a.L[1] * a.L[2];
     a.tb = lat.g.tb;
+    // tiles: one x pair times the largest powers of two up to 4 x 8 x 8 that divide L
+    // (tsites counts output sites: one per x pair)
+    const int pref[4] = {2, 4, 8, 8};
+    a.T[0] = 2;
     a.tsites = 1;
-    for (int mu = 0; mu < 4; ++mu) a.T[mu] = 1;
-    for (int mu = 0; mu < 3; ++mu) a.NT[mu] = a.L[mu];
+    for (int mu = 1; mu < 4; ++mu) {
+        int t = pref[mu];
+        while (t > 1 && a.L[mu] % t) t /= 2;
+        a.T[mu] = t;
+        a.tsites *= t;
+    }
+    for (int mu = 0; mu < 3; ++mu) a.NT[mu] = a.L[mu] / a.T[mu];
     e.parity = parity;
     e.V2 = a.V / 2;
     return e;
