@@ -27,7 +27,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import coarse, evenodd, krylov, wilson
+from . import coarse, evenodd, krylov, sap, wilson
 from .conventions import FINE_CHIRALITY
 
 
@@ -45,6 +45,10 @@ class MGParams:
     tol: float = 1e-10
     max_outer_cycles: int = 100
     smoother_evenodd: bool = False
+    smoother_sap: bool = False
+    sap_block: tuple = (4, 4, 4, 4)
+    sap_cycles: int = 1
+    sap_mr: int = 4
 
 
 @dataclass
@@ -115,6 +119,8 @@ def vcycle(levels, l: int, v: np.ndarray, params: MGParams) -> np.ndarray:
         e = krylov.fgmres_fixed(nxt.apply, c, lambda u: vcycle(levels, l + 1, u, params),
                                 params.inter_m)
     z0 = coarse.prolong(lev.P, e, lev.dims, lev.block)
+    if l == 0 and params.smoother_sap:
+        return sap.sap_smooth(lev.apply, v, z0, lev.dims, params.sap_block, params.sap_cycles, params.sap_mr)
     if l == 0 and params.smoother_evenodd:
         return z0 + evenodd_smooth(lev, v - lev.apply(z0), params.smooth_m)
     return krylov.gmres(lev.apply, v, z0, params.smooth_m, 1)
