@@ -88,7 +88,7 @@ uint64_t mrhs_kernel_launch_count(void);
 
 /* Event timing of one kernel, for measurement harnesses (no effect on any
  * result).  After mrhs_kernel_timer_start(name), every launch of the kernel
- * `name` ("k_dslash_x2", "k_dslash", "k_dots_norm", "k_lincomb_scale",
+ * `name` ("k_dslash_x2", "k_eo_x2", "k_sap_mr", "k_dslash", "k_dots_norm", "k_lincomb_scale",
  * "k_lincomb", "k_multi_dot", "k_norm2", "k_restrict_tc", "k_prolong_tc",
  * "k_coarse_tc") that is not being captured into a CUDA graph is bracketed by
  * two CUDA events recorded on its launching stream; launches captured into a
@@ -159,6 +159,21 @@ mrhs_status mrhs_apply_hop_eo(mrhs_lattice *lat, int out_parity, const void *in_
                               void *stream);
 mrhs_status mrhs_apply_schur(mrhs_lattice *lat, const void *in_dev, void *out_dev, int nrhs, void *stream);
 
+/* SAP smoother (Schwarz alternating procedure; the smoother the paper's
+ * Sec. 9 outlook names next), FP32 fields [V][12][nrhs], z_dev updated in
+ * place: `cycles` SAP cycles for D z = v.  The lattice is cut into blocks of
+ * extents block[4] (each dividing the lattice extent an even number of
+ * times; at most 256 sites per block) coloured by block parity
+ * (sum_mu x_mu / block_mu) mod 2; per cycle, for colour 0 then 1: r = v - D z,
+ * then z += e with e_B approximating D_BB^{-1} r_B on every block of that
+ * colour by `mr_steps` minimal-residual steps from zero with inner products
+ * over the block (D_BB: D with the hops that leave the block dropped).
+ * nrhs even; v, z 16-byte aligned and not overlapping (MRHS_ERR_INVALID
+ * otherwise).  Uses a full-lattice residual field owned by the lattice
+ * (allocated on first use). */
+mrhs_status mrhs_sap_smooth(mrhs_lattice *lat, const void *v_dev, void *z_dev, int nrhs, const int block[4],
+                            int cycles, int mr_steps, void *stream);
+
 /* ------------------------------------------------------------------ */
 /* Batched BLAS-1 over the RHS index (Sec. 7, "simultaneous" inner      */
 /* products).  A field is `rows` rows of `nrhs` complex values, RHS     */
@@ -228,6 +243,13 @@ typedef struct {
     /* Optional host start vectors per level, [V_l][dof_l][n_vec[l]] complex
      * FP64 (dof_0 = 12, dof_l = nc of level l).  NULL entries: random. */
     const double *init_vecs[MRHS_MAX_LEVELS - 1];
+    int smoother_sap;                      /* 1: the fine post-smoother is sap_cycles
+                                              SAP cycles (mrhs_sap_smooth) instead
+                                              of GMRES; takes precedence over
+                                              smoother_evenodd where SAP applies  */
+    int sap_block[4];                      /* SAP block extents                   */
+    int sap_cycles;                        /* SAP cycles per post-smoothing       */
+    int sap_mr;                            /* MR steps per SAP block solve        */
 } mrhs_mg_params;
 
 /* Fill `p` with the defaults used for the 24^3x64 three-level workload. */

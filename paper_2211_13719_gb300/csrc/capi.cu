@@ -223,6 +223,24 @@ mrhs_status mrhs_apply_schur(mrhs_lattice *lat, const void *in_dev, void *out_de
     MRHS_API_END
 }
 
+mrhs_status mrhs_sap_smooth(mrhs_lattice *lat, const void *v_dev, void *z_dev, int nrhs, const int block[4],
+                            int cycles, int mr_steps, void *stream) {
+    MRHS_API_BEGIN
+    check_apply(lat, v_dev, z_dev, nrhs, MRHS_FP32);
+    if (!block) fail(MRHS_ERR_INVALID, "block extents must be non-null");
+    if (!sap_supported(*lat, block, nrhs))
+        fail(MRHS_ERR_INVALID, "SAP needs an even nrhs, block extents dividing the lattice into an even number of "
+                               "blocks per direction, at most 256 sites per block and 32-bit field indexing");
+    DeviceGuard dg(lat->device);
+    const size_t full = sizeof(float2) * (size_t)lat->g.V * 12 * nrhs;
+    if (lat->SAPtmp.bytes < full) {
+        MRHS_CUDA(cudaDeviceSynchronize());  // the old scratch may still be in use by earlier calls
+        lat->SAPtmp.alloc(full);
+    }
+    sap_smooth(*lat, v_dev, z_dev, nrhs, block, cycles, mr_steps, lat->SAPtmp.ptr, static_cast<cudaStream_t>(stream));
+    MRHS_API_END
+}
+
 static void check_blas(const void *p, int64_t rows, int nrhs, mrhs_precision prec) {
     if (!p) fail(MRHS_ERR_INVALID, "field pointer must be non-null");
     if (rows < 1) fail(MRHS_ERR_INVALID, "rows must be >= 1");

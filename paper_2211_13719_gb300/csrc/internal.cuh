@@ -23,6 +23,7 @@ struct mrhs_lattice {
     // even-odd decomposition); CinvErr: int, set when a block was singular
     mrhs::DeviceBuffer Cinv64, Cinv32, CinvErr;
     mrhs::DeviceBuffer EOtmp;  // half-lattice scratch of the Schur operator
+    mrhs::DeviceBuffer SAPtmp; // full-lattice residual scratch of mrhs_sap_smooth
     bool has_gauge = false, has_clover = false;
     bool cinv_singular = false;  // a block of C was singular (no even-odd inverse)
     double mass = 0.0, csw = 0.0;
@@ -58,6 +59,13 @@ void eo_split(const mrhs_lattice &lat, const void *r, void *re, void *ro, void *
 void eo_axpy_hop(const mrhs_lattice &lat, int out_parity, const void *self, const void *in, void *out, bool cinv,
                  int n, cudaStream_t s);
 void eo_merge_add(const mrhs_lattice &lat, const void *de, const void *d_o, void *z, int n, cudaStream_t s);
+// SAP smoother (FP32, even n): `cycles` cycles of the block-coloured Schwarz
+// alternating procedure for D z = v, each block system by `mr_steps` MR steps
+// in shared memory; r_tmp: a full FP32 field of n RHS, overwritten.
+// sap_supported tells whether the lattice, block extents and n allow it.
+bool sap_supported(const mrhs_lattice &lat, const int B[4], int n);
+void sap_smooth(const mrhs_lattice &lat, const void *v, void *z, int n, const int B[4], int cycles, int mr_steps,
+                void *r_tmp, cudaStream_t s);
 // dst[i] = (hi, lo) float pairs of the FP64 complex src[i], i < count
 void split_df(const void *src_c128, void *dst_f4, int64_t count, cudaStream_t s);
 // out = D in (y == nullptr) or y - D in; `in` FP32, out and y FP64, float-float arithmetic

@@ -189,6 +189,7 @@ struct LevelWork {
     // C_ee^-1 r_e, b_hat, delta_e, delta_o, and GMRES on D_hat
     DeviceBuffer eo_r, eo_re, eo_ro, eo_te, eo_bh, eo_de, eo_do;
     KWork eo_smooth;
+    DeviceBuffer sap_r;  // fine level, SAP smoother: its residual field
 };
 
 struct GraphKey {
@@ -308,7 +309,11 @@ void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t 
     }
     {
         EventTimer t(prof, s, &mg.t_fine);
-        if (l == 0 && mg.schur && eo_supported(*mg.lat, n)) {
+        if (l == 0 && mg.p.smoother_sap && sap_supported(*mg.lat, mg.p.sap_block, n)) {
+            // SAP smoother: sap_cycles cycles of block-coloured Schwarz on D z = v from the
+            // coarse-corrected z, each block system by sap_mr MR steps
+            sap_smooth(*mg.lat, v, z, n, mg.p.sap_block, mg.p.sap_cycles, mg.p.sap_mr, mg.work[0].sap_r.ptr, s);
+        } else if (l == 0 && mg.schur && eo_supported(*mg.lat, n)) {
             // even-odd smoother: z += delta, D delta ~= r = v - D z through smooth_m GMRES
             // steps on D_hat delta_o = b_hat = r_o + 1/2 H_oe C_ee^-1 r_e from 0, then
             // delta_e = C_ee^-1 (r_e + 1/2 H_eo delta_o)
@@ -425,6 +430,9 @@ void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
     if (p.outer_op_precision != MRHS_DF64 && p.outer_op_precision != MRHS_FP64)
         fail(MRHS_ERR_INVALID, "outer_op_precision must be DF64 or FP64");
     if (p.smoother_evenodd != 0 && p.smoother_evenodd != 1) fail(MRHS_ERR_INVALID, "smoother_evenodd must be 0 or 1");
+    if (p.smoother_sap != 0 && p.smoother_sap != 1) fail(MRHS_ERR_INVALID, "smoother_sap must be 0 or 1");
+    if (p.smoother_sap && (p.sap_cycles < 1 || p.sap_cycles > 16 || p.sap_mr < 1 || p.sap_mr > 64))
+        fail(MRHS_ERR_INVALID, "sap_cycles must be in 1..16 and sap_mr in 1..64");
     if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
 }
 
@@ -504,6 +512,8 @@ void alloc_workspace(mrhs_mg &mg) {
         W.eo_smooth.init(mg.p.smooth_m, hrows, nmax, false);
         mg.schur.reset(new SchurOp(mg.lat, nmax));
     }
+    if (mg.p.smoother_sap && sap_supported(*mg.lat, mg.p.sap_block, 2))
+        mg.work[0].sap_r.alloc(sizeof(float2) * (size_t)mg.lev[0].rows() * nmax);
     const int64_t rows = mg.lev[0].rows();
     mg.inner.init(mg.p.inner_m, rows, nmax, true);
     mg.inner_b.alloc(sizeof(float2) * (size_t)rows * nmax);
@@ -726,6 +736,10 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->outer_op_precision = MRHS_DF64;
     p->smoother_evenodd = 1;
     p->seed = 1234;
+    p->smoother_sap = 0;
+    for (int mu = 0; mu < 4; ++mu) p->sap_block[mu] = 4;
+    p->sap_cycles = 1;
+    p->sap_mr = 4;
 }
 
 mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_mg **out) {

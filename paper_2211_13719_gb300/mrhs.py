@@ -67,6 +67,10 @@ class MgParams(C.Structure):
         ("smoother_evenodd", C.c_int),
         ("seed", C.c_uint64),
         ("init_vecs", C.c_void_p * (MAX_LEVELS - 1)),
+        ("smoother_sap", C.c_int),
+        ("sap_block", C.c_int * 4),
+        ("sap_cycles", C.c_int),
+        ("sap_mr", C.c_int),
     ]
 
 
@@ -111,6 +115,7 @@ PROTOTYPES = {
     "mrhs_kernel_timer_start": (_I, [C.c_char_p]),
     "mrhs_apply_hop_eo": (_I, [_P, _I, _P, _P, _I, _P]),
     "mrhs_apply_schur": (_I, [_P, _P, _P, _I, _P]),
+    "mrhs_sap_smooth": (_I, [_P, _P, _P, _I, C.POINTER(C.c_int), _I, _I, _P]),
     "mrhs_kernel_timer_stop": (_I, [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mrhs_create_lattice": (_I, [C.POINTER(C.c_int), _I, _I, C.POINTER(_P)]),
     "mrhs_destroy_lattice": (None, [_P]),
@@ -231,6 +236,12 @@ def mrhs_apply_hop_eo(lat, out_parity, in_dev, out_dev, nrhs, stream=None):
 
 def mrhs_apply_schur(lat, in_dev, out_dev, nrhs, stream=None):
     _check(lib().mrhs_apply_schur(lat, _ptr(in_dev), _ptr(out_dev), int(nrhs), _stream(stream)))
+
+
+def mrhs_sap_smooth(lat, v_dev, z_dev, nrhs, block, cycles, mr_steps, stream=None):
+    b = (C.c_int * 4)(*[int(x) for x in block])
+    _check(lib().mrhs_sap_smooth(lat, _ptr(v_dev), _ptr(z_dev), int(nrhs), b, int(cycles), int(mr_steps),
+                                 _stream(stream)))
 
 
 def mrhs_apply_D(lat, in_dev, out_dev, nrhs, prec, stream=None):
