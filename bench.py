@@ -40,8 +40,10 @@ WORKLOAD = dict(dims=(24, 24, 24, 64), eps=0.25, gauge_seed=1301, source_seed=23
                 nrhs=48, tol=1e-10, n_levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[32, 32])
 MG_PARAMS = dict(setup_sweeps=6, setup_m=8, smooth_m=3, coarse_m=14, coarse_cycles=1, inter_m=4, inner_m=8,
                  inner_max_iters=200, inner_tol=1e-5, outer_m=4, max_outer_iters=30, smoother_evenodd=1)
-# the kernel with the largest share of a timed solve in the profiler's launch list
-DOMINANT_KERNEL = "k_dslash_x2"
+# the kernel with the largest share of a timed solve in the profiler's launch list (the even-odd
+# hopping kernel of the fine smoother's Schur operator), and the full-lattice fine stencil
+DOMINANT_KERNEL = "k_eo_x2"
+FINE_STENCIL_KERNEL = "k_dslash_x2"
 WORKLOAD_NAME = ("wilson-clover MG solve 24^3x64 antiperiodic, U=exp(i0.25H), c_sw=1, 3 levels "
                  "(4^4, 2^4 aggregates, 32 null vectors, even-odd fine smoother), nRHS=48, tol 1e-10")
 # the CPU baseline / reference arm: the oracle's FP64 MG-FGMRES on a smaller
@@ -128,13 +130,16 @@ def source_hash(*names):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel_file):
-    """dram bytes per launch from the committed ncu summary, if the kernel is unchanged."""
-    path = os.path.join(ROOT, "profiles", "dslash_fp32_traffic.json")
+STENCIL_SOURCES = ("dirac.cu", "pair.cuh", "spin.cuh")
+
+
+def profiled_traffic(name):
+    """dram bytes per launch from a committed ncu summary, if the kernel sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", name)
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("source_hash") == source_hash(kernel_file):
+        if rec.get("source_hash") == source_hash(*STENCIL_SOURCES):
             return rec
     except Exception:
         pass
@@ -250,6 +255,15 @@ def make_params(mrhs, n_max, coarse_precision, use_graph, **over):
     return p
 
 
+def smoother_params(args):
+    """MG parameter overrides of the --smoother choice."""
+    if args.smoother == "sap":
+        return dict(smoother_sap=1, smoother_evenodd=0, sap_mr=args.sap_mr, sap_cycles=args.sap_cycles)
+    if args.smoother == "gmres":
+        return dict(smoother_sap=0, smoother_evenodd=0)
+    return {}
+
+
 def gauge_field(w):
     import numpy as np
 
@@ -355,7 +369,7 @@ def run_ours(args, rank, world, local_rank):
     mrhs.mrhs_build_clover(lat, w["mass"], w["csw"])
     del U
     t0 = time.perf_counter()
-    mg = mrhs.mrhs_setup_mg(lat, make_params(mrhs, n, mrhs.MRHS_FP16, 1))
+    mg = mrhs.mrhs_setup_mg(lat, make_params(mrhs, n, mrhs.MRHS_FP16, 1, **smoother_params(args)))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
 
@@ -383,7 +397,7 @@ def run_ours(args, rank, world, local_rank):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     # CUDA events around the dominant kernel's launches, on the stream it runs on
-    mrhs.mrhs_kernel_timer_start(DOMINANT_KERNEL)
+    mrhs.mrhs_kernel_timer_start(FINE_STENCIL_KERNEL)
     with ClockSampler(dev) as clk:
         torch.cuda.nvtx.range_push("timed")
         e0.record(stream)
@@ -449,38 +463,71 @@ def run_ours(args, rank, world, local_rank):
         extra["per_solve"] = {"outer_iters": s0.outer_iters, "inner_iters": s0.inner_iters, "vcycles": s0.vcycles,
                               "seconds": s0.seconds, "max_rel_residual": max_rel}
         extra["setup_s"] = setup_s
-        # --- roofline of the dominant kernel (the FP32 fine stencil): its average launch
-        # duration inside the timed region; also timed alone for reference
+        # --- rooflines.  The dominant kernel of a timed solve in the profiler's launch list is the
+        # even-odd hopping kernel k_eo_x2 (the Schur operator D_hat = C_oo - 1/4 H_oe C_ee^-1 H_eo of the
+        # fine smoother: one C^-1 H launch and one C - 1/4 H launch over V/2 output sites each).  Its
+        # launches in the timed region are replayed from the V-cycle graph, where events cannot bracket
+        # them, so it is timed with CUDA events on the solver stream around standalone D_hat
+        # applications of the same size right after the timed region (half fields of 2 GB: larger
+        # than L2).  The full-lattice fine stencil k_dslash_x2 is timed live in the timed region.
         peak, peak_kind = read_peaks()
+
+        def per_call(fn, reps=20):
+            for _ in range(3):
+                fn()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(reps):
+                fn()
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            return ev0.elapsed_time(ev1) * 1e-3 / reps
+
         a = torch.randn((V, 12, n), dtype=torch.complex64, device="cuda", generator=gen)
         o = torch.empty_like(a)
-        for _ in range(3):
-            mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream)
-        reps = 20
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(reps):
-            mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        t_alone = ev0.elapsed_time(ev1) * 1e-3 / reps
+        t_alone = per_call(lambda: mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream))
         t_k = k_ms * 1e-3 / k_timed if k_timed else t_alone
         alg = V * (576 + 192 * n)
-        achieved = alg / t_k / 1e9
-        tr = profiled_traffic("dirac.cu")
-        extra["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-                             "kernel": f"{DOMINANT_KERNEL} (fp32 fine stencil), {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}, "
-                                       f"nRHS={n}",
-                             "algorithmic_bytes_per_launch": alg, "ms_per_launch": t_k * 1e3,
-                             "timing": (f"CUDA events on the solver stream around its {k_timed} launches made "
-                                        f"outside CUDA graphs in the timed region (launches replayed from the "
-                                        f"V-cycle graph are not visible to the events)"
-                                        if k_timed else "timed alone (no launch in the timed region)"),
-                             "ms_per_launch_alone": t_alone * 1e3,
-                             "peak_source": f"{peak_kind} HBM copy bandwidth (burst: the kernel is timed per launch)"}
+        tr = profiled_traffic("dslash_fp32_traffic.json")
+        extra["roofline_fine_stencil"] = {
+            "bound": "hbm", "achieved": alg / t_k / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": alg / t_k / 1e9 / peak, "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+            "kernel": f"{FINE_STENCIL_KERNEL} (fp32 full-lattice fine stencil D), "
+                      f"{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}, nRHS={n}",
+            "algorithmic_bytes_per_launch": alg, "bytes_per_site": f"576 + 192 n = {576 + 192 * n}",
+            "ms_per_launch": t_k * 1e3,
+            "timing": (f"CUDA events on the solver stream around its {k_timed} launches made outside CUDA "
+                       f"graphs in the timed region" if k_timed else "timed alone (no launch in the timed region)"),
+            "ms_per_launch_alone": t_alone * 1e3,
+            "peak_source": f"{peak_kind} HBM copy bandwidth (burst: the kernel is timed per launch)"}
         del a, o
+        ah = torch.randn((V // 2, 12, n), dtype=torch.complex64, device="cuda", generator=gen)
+        oh = torch.empty_like(ah)
+        mrhs.mrhs_kernel_timer_start(DOMINANT_KERNEL)
+        t_dhat = per_call(lambda: mrhs.mrhs_apply_schur(lat, ah, oh, n, stream))
+        eo_ms, eo_timed, _ = mrhs.mrhs_kernel_timer_stop()
+        t_eo = eo_ms * 1e-3 / eo_timed
+        # per D_hat: two launches over V/2 output sites; per output site 8 links (4 forward at the
+        # site, 4 backward at its neighbours: every link of the lattice once) 576 B, the 6x6 blocks of
+        # C^-1 or C 288 B, the 8 neighbour spinors counted once 96 n B, out 96 n B, and for C - 1/4 H
+        # the site's own spinor 96 n B: (1728 + 480 n) B per output site and D_hat
+        alg_dhat = (V // 2) * (1728 + 480 * n)
+        alg_eo = alg_dhat / 2
+        tre = profiled_traffic("eo_fp32_traffic.json")
+        extra["roofline"] = {
+            "bound": "hbm", "achieved": alg_eo / t_eo / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": alg_eo / t_eo / 1e9 / peak, "traffic": (tre["dram_bytes_per_launch"] if tre else None),
+            "kernel": f"{DOMINANT_KERNEL} (fp32 even-odd hopping kernel, both launches of the Schur operator "
+                      f"D_hat), {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}, nRHS={n}",
+            "algorithmic_bytes_per_launch": alg_eo,
+            "bytes_per_output_site": f"per D_hat (2 launches) 1728 + 480 n = {1728 + 480 * n}",
+            "ms_per_launch": t_eo * 1e3, "ms_per_dhat": t_dhat * 1e3,
+            "timing": (f"CUDA events on the solver stream around {eo_timed} launches of standalone D_hat "
+                       f"applications (V/2 x 12 x {n} half fields) after the timed region; inside it the "
+                       f"kernel runs from the V-cycle CUDA graph"),
+            "peak_source": f"{peak_kind} HBM copy bandwidth (burst: the kernel is timed per launch)"}
+        del ah, oh
         # --- plain solver: one RHS at a time, FP32 coarse stencil on CUDA cores, no graphs
         if not args.no_plain:
             mgp = mrhs.mrhs_setup_mg(lat, make_params(mrhs, 1, mrhs.MRHS_FP32, 0))
@@ -516,6 +563,8 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_NAME, "nrhs_per_gpu": n, "lattice": "x".join(map(str, dims)),
                        "mass": w["mass"], "csw": w["csw"], "parallelism": f"replicas x{world}",
+                       "smoother": args.smoother + (f" (SAP {args.sap_cycles} cycle(s), {args.sap_mr} MR steps, "
+                                                    f"4^4 blocks)" if args.smoother == "sap" else ""),
                        "l2": "inputs larger than L2 (FP64 fields of 8 GB)"},
         }
         line.update(extra)
@@ -529,6 +578,7 @@ def run_case(name, reps):
     """Small launches of one kernel family, for ncu captures (a few GB on the device).
 
     stencil:   FP32 fine operator, 24^4 lattice, 48 RHS
+    stencil-sweep: FP32 fine operator, 24^4 lattice, nRHS 1 .. 64
     schur:     even-odd hop and Schur operator (FP32), 24^4 lattice, 48 RHS
     intergrid: tensor-core restriction + prolongation, 16^4 lattice, 4^4 aggregates, 32 vectors, 48 RHS
     blas:      the FP32 batched multi-dot and linear combination, 16^4 x 12 rows, 48 RHS, 4 vectors
@@ -570,14 +620,27 @@ def run_case(name, reps):
                                                                   mrhs.MRHS_FP32))
         out["GBs_lincomb_k4"] = (k + 2) * rows * n * 8 / out["ms_lincomb_k4"] / 1e6
         return print(json.dumps(out), flush=True)
-    dims = (24, 24, 24, 24) if name in ("stencil", "schur") else (16, 16, 16, 16)
+    dims = (24, 24, 24, 24) if name in ("stencil", "schur", "stencil-sweep") else (16, 16, 16, 16)
     V = volume(dims)
     U = synth.gauge_exp(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
     lat = mrhs.mrhs_create_lattice(dims, -1, torch.cuda.current_device())
     mrhs.mrhs_load_gauge(lat, U)
     mrhs.mrhs_build_clover(lat, WORKLOAD["mass"], WORKLOAD["csw"])
     out["dims"] = list(dims)
-    if name == "stencil":
+    if name == "stencil-sweep":
+        # the fine operator alone (FP32) at every RHS count: algorithmic GB/s and fraction of the measured
+        # HBM bandwidth, bytes per site 576 + 192 n (4 links, compact clover, one spinor in and out per RHS)
+        peak, kind = read_peaks()
+        out["peak_GBs"] = peak
+        out["sweep"] = []
+        for nn in (1, 2, 4, 8, 12, 16, 24, 32, 48, 64):
+            a = torch.randn((V, 12, nn), dtype=torch.complex64, device="cuda")
+            o = torch.empty_like(a)
+            ms = ev(lambda: mrhs.mrhs_apply_D(lat, a, o, nn, mrhs.MRHS_FP32, stream))
+            gbs = V * (576 + 192 * nn) / ms / 1e6
+            out["sweep"].append({"nrhs": nn, "ms": ms, "alg_GBs": gbs, "frac": gbs / peak})
+            del a, o
+    elif name == "stencil":
         a = torch.randn((V, 12, n), dtype=torch.complex64, device="cuda")
         o = torch.empty_like(a)
         out["ms_apply_fp32"] = ev(lambda: mrhs.mrhs_apply_D(lat, a, o, n, mrhs.MRHS_FP32, stream))
@@ -587,9 +650,9 @@ def run_case(name, reps):
         o = torch.empty_like(a)
         out["ms_hop_eo"] = ev(lambda: mrhs.mrhs_apply_hop_eo(lat, 0, a, o, n, stream))
         out["ms_schur"] = ev(lambda: mrhs.mrhs_apply_schur(lat, a, o, n, stream))
-        # per output site: 4 links x 72 B, clover (or inverse) 288 B, 96 B out per RHS; 8 neighbour spinors
-        # of 96 B per RHS each counted once (a half field in) -> (576 + 192 n) B per output site, two kernels
-        out["schur_alg_GBs"] = 2 * (V // 2) * (576 + 192 * n) / out["ms_schur"] / 1e6
+        # per output site of D_hat (two launches): 8 links 576 B, C^-1 or C 288 B, neighbours and output
+        # 192 n B, and the site's own spinor in the C - 1/4 H launch 96 n B: 1728 + 480 n
+        out["schur_alg_GBs"] = (V // 2) * (1728 + 480 * n) / out["ms_schur"] / 1e6
     elif name == "intergrid":
         p = mrhs.mrhs_mg_default_params()
         p.n_levels = 2
@@ -625,7 +688,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.8)
-    ap.add_argument("--case", default=None, choices=["stencil", "schur", "intergrid", "blas"],
+    ap.add_argument("--smoother", default="evenodd", choices=["evenodd", "sap", "gmres"],
+                    help="fine post-smoother: GMRES on the even-odd Schur complement (default), SAP, or GMRES on D")
+    ap.add_argument("--sap-mr", type=int, default=4)
+    ap.add_argument("--sap-cycles", type=int, default=1)
+    ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas"],
                     help="run a small profiling case of one kernel family instead of the benchmark")
     ap.add_argument("--case-reps", type=int, default=3)
     args = ap.parse_args()

@@ -97,6 +97,9 @@ mrhs_status mrhs_create_lattice(const int dims[4], int t_boundary, int device, m
     lat->Cdf.alloc(V * 36 * sizeof(float4));
     lat->Cinv64.alloc(V * 36 * sizeof(double2));
     lat->Cinv32.alloc(V * 36 * sizeof(float2));
+    lat->U32a.alloc(V * 36 * sizeof(float2));
+    lat->C32a.alloc(V * 36 * sizeof(float2));
+    lat->Cinv32a.alloc(V * 36 * sizeof(float2));
     lat->CinvErr.alloc(sizeof(int));
     *out = lat.release();
     MRHS_API_END

@@ -14,6 +14,8 @@
 // A_k = -i sigma_k, A_t = 1): (1 -+ gamma_mu) psi has rank 2, so each hop
 // forms a 2-spin half spinor h = psi_up -+ A psi_dn, multiplies it by the
 // link, and rebuilds the lower spins from the two products.
+#include <type_traits>
+
 #include "internal.cuh"
 #include "pair.cuh"
 #include "spin.cuh"
@@ -253,7 +255,13 @@ struct KArgs32 {
     int tsites;   // T[0] * T[1] * T[2] * T[3]
 };
 
-template <int MU, bool FWD>
+// N: the RHS count as a compile-time constant (0: a.n at run time), so that
+// the 12 component loads of a neighbour are immediate offsets from one
+// address.  AOS: links site-major, [V][4][9] (the 9 entries of a link are
+// immediate offsets), else link-major [(mu * 9 + e)][V].
+template <int N> __device__ __forceinline__ int rhs_count(const KArgs32 &a) { return N ? N : a.n; }
+
+template <int MU, bool FWD, int N, bool AOS>
 __device__ __forceinline__ void hop_x2(P2 (&acc)[12], const float2 *__restrict__ U, const float2 *__restrict__ in,
                                       const KArgs32 &a, int nb, int link_site, bool flip, int r0) {
     using P = Proj<MU>;
@@ -261,14 +269,15 @@ __device__ __forceinline__ void hop_x2(P2 (&acc)[12], const float2 *__restrict__
     constexpr int F1 = FWD ? P::F1 : neg_f<P::F1>::v;
     constexpr int G2 = FWD ? P::G2 : neg_f<P::G2>::v;
     constexpr int G3 = FWD ? P::G3 : neg_f<P::G3>::v;
-    const int64_t base = (int64_t)nb * 12 * a.n + r0;
+    const int n = rhs_count<N>(a);
+    const float2 *pin = in + ((int64_t)nb * 12 * n + r0);
     P2 h0[3], h1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const P2 p0 = ld_p2(in, base + (int64_t)(0 * 3 + c) * a.n);
-        const P2 p1 = ld_p2(in, base + (int64_t)(1 * 3 + c) * a.n);
-        const P2 pa = ld_p2(in, base + (int64_t)(P::P0 * 3 + c) * a.n);
-        const P2 pb = ld_p2(in, base + (int64_t)(P::P1 * 3 + c) * a.n);
+        const P2 p0 = ld_p2(pin, (0 * 3 + c) * n);
+        const P2 p1 = ld_p2(pin, (1 * 3 + c) * n);
+        const P2 pa = ld_p2(pin, (P::P0 * 3 + c) * n);
+        const P2 pb = ld_p2(pin, (P::P1 * 3 + c) * n);
         h0[c] = p2add(p0, p2f<F0>(pa));
         h1[c] = p2add(p1, p2f<F1>(pb));
     }
@@ -279,18 +288,19 @@ __device__ __forceinline__ void hop_x2(P2 (&acc)[12], const float2 *__restrict__
             h1[c] = p2f<FM>(h1[c]);
         }
     }
-    const int V = a.V;
+    const float2 *Ul = AOS ? U + ((int64_t)link_site * 4 + MU) * 9 : U + (int64_t)MU * 9 * a.V + link_site;
+    const int64_t ust = AOS ? 1 : a.V;
 #pragma unroll
     for (int row = 0; row < 3; ++row) {
         P2 s0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, s1 = s0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if (FWD) {
-                const float2 u = __ldg(U + (int64_t)(MU * 9 + row * 3 + b) * V + link_site);
+                const float2 u = __ldg(Ul + (row * 3 + b) * ust);
                 p2mac(s0, u, h0[b]);
                 p2mac(s1, u, h1[b]);
             } else {
-                const float2 u = __ldg(U + (int64_t)(MU * 9 + b * 3 + row) * V + link_site);
+                const float2 u = __ldg(Ul + (b * 3 + row) * ust);
                 p2mac_conj(s0, u, h0[b]);
                 p2mac_conj(s1, u, h1[b]);
             }
@@ -302,7 +312,7 @@ __device__ __forceinline__ void hop_x2(P2 (&acc)[12], const float2 *__restrict__
     }
 }
 
-template <int MU>
+template <int MU, int N, bool AOS>
 __device__ __forceinline__ void hop_pair_x2(P2 (&acc)[12], const float2 *__restrict__ U,
                                            const float2 *__restrict__ in, const KArgs32 &a, int site,
                                            const int c[4], int r0) {
@@ -313,12 +323,15 @@ __device__ __forceinline__ void hop_pair_x2(P2 (&acc)[12], const float2 *__restr
     const int sb = wrapB ? site + st * (L - 1) : site - st;
     const bool flipF = MU == 3 && wrapF && a.tb < 0;
     const bool flipB = MU == 3 && wrapB && a.tb < 0;
-    hop_x2<MU, true>(acc, U, in, a, sf, site, flipF, r0);
-    hop_x2<MU, false>(acc, U, in, a, sb, sb, flipB, r0);
+    hop_x2<MU, true, N, AOS>(acc, U, in, a, sf, site, flipF, r0);
+    hop_x2<MU, false, N, AOS>(acc, U, in, a, sb, sb, flipB, r0);
 }
 
-template <bool RESID>
-__global__ void __launch_bounds__(128, 4) k_dslash_x2(const float2 *__restrict__ U, const float2 *__restrict__ C,
+// 128 threads, at most 168 registers (3 CTAs per SM): measured on GB300 (24^3 x
+// 64) 8 % faster than 128 registers (4 CTAs), which left the compiler too few
+// registers to issue the loads of one hop ahead of the previous hop's arithmetic
+template <bool RESID, int N, bool AOS>
+__global__ void __launch_bounds__(128, 3) k_dslash_x2(const float2 *__restrict__ U, const float2 *__restrict__ C,
                                                        const float2 *__restrict__ in, float2 *__restrict__ out,
                                                        const float2 *__restrict__ y, KArgs32 a) {
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
@@ -347,30 +360,31 @@ __global__ void __launch_bounds__(128, 4) k_dslash_x2(const float2 *__restrict__
     P2 acc[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-    hop_pair_x2<0>(acc, U, in, a, site, c, r0);
-    hop_pair_x2<1>(acc, U, in, a, site, c, r0);
-    hop_pair_x2<2>(acc, U, in, a, site, c, r0);
-    hop_pair_x2<3>(acc, U, in, a, site, c, r0);
+    hop_pair_x2<0, N, AOS>(acc, U, in, a, site, c, r0);
+    hop_pair_x2<1, N, AOS>(acc, U, in, a, site, c, r0);
+    hop_pair_x2<2, N, AOS>(acc, U, in, a, site, c, r0);
+    hop_pair_x2<3, N, AOS>(acc, U, in, a, site, c, r0);
 
     const int V = a.V;
-    const int64_t base = (int64_t)site * 12 * a.n + r0;
+    const int n = rhs_count<N>(a);
+    const int64_t base = (int64_t)site * 12 * n + r0;
+    const float2 *pin = in + base;
     const float2 mhalf = make_float2(-0.5f, -0.5f);
 #pragma unroll
     for (int chi = 0; chi < 2; ++chi) {
         P2 v[6], o[6];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) v[i] = ld_p2(in, base + (int64_t)(6 * chi + i) * a.n);
-        site_mat_x2(C, V, site, chi, v, o);
+        for (int i = 0; i < 6; ++i) v[i] = ld_p2(pin, (6 * chi + i) * n);
+        site_mat_x2<AOS>(C, V, site, chi, v, o);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             const P2 acc_i = acc[6 * chi + i];
             P2 res = {__ffma2_rn(mhalf, acc_i.re, o[i].re), __ffma2_rn(mhalf, acc_i.im, o[i].im)};
-            const int64_t off = base + (int64_t)(6 * chi + i) * a.n;
             if constexpr (RESID) {
-                const P2 yy = ld_p2(y, off);
+                const P2 yy = ld_p2(y + base, (6 * chi + i) * n);
                 res = {__fadd2_rn(yy.re, neg2(res.re)), __fadd2_rn(yy.im, neg2(res.im))};
             }
-            st_p2(out, off, res);
+            st_p2(out + base, (6 * chi + i) * n, res);
         }
     }
 }
@@ -405,15 +419,34 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
     const int64_t items = (int64_t)a.V * a.G;
     const int threads = 128;
     const unsigned blocks = (unsigned)((items + threads - 1) / threads);
-    const float2 *U = lat.U32.as<float2>();
-    const float2 *C = lat.C32.as<float2>();
     MRHS_TIMED("k_dslash_x2", s);
-    if (y)
-        k_dslash_x2<true><<<blocks, threads, 0, s>>>(U, C, static_cast<const float2 *>(in), static_cast<float2 *>(out),
-                                                     static_cast<const float2 *>(y), a);
-    else
-        k_dslash_x2<false><<<blocks, threads, 0, s>>>(U, C, static_cast<const float2 *>(in),
-                                                      static_cast<float2 *>(out), nullptr, a);
+    const float2 *yy = static_cast<const float2 *>(y);
+    const float2 *ii = static_cast<const float2 *>(in);
+    float2 *oo = static_cast<float2 *>(out);
+    // 16, 24, 32, 48, 64 RHS: compile-time RHS count and site-major links / clover;
+    // fewer: a warp spans several sites, whose link-major loads coalesce
+    auto go = [&](auto resid, auto nc, auto aos) {
+        constexpr bool R = decltype(resid)::value;
+        constexpr int NC = decltype(nc)::value;
+        constexpr bool AO = decltype(aos)::value;
+        const float2 *U = AO ? lat.U32a.as<float2>() : lat.U32.as<float2>();
+        const float2 *C = AO ? lat.C32a.as<float2>() : lat.C32.as<float2>();
+        k_dslash_x2<R, NC, AO><<<blocks, threads, 0, s>>>(U, C, ii, oo, yy, a);
+    };
+    auto pick = [&](auto resid) {
+        using T = std::true_type;
+        using F = std::false_type;
+        switch (n) {
+            case 16: go(resid, std::integral_constant<int, 16>{}, T{}); break;
+            case 24: go(resid, std::integral_constant<int, 24>{}, T{}); break;
+            case 32: go(resid, std::integral_constant<int, 32>{}, T{}); break;
+            case 48: go(resid, std::integral_constant<int, 48>{}, T{}); break;
+            case 64: go(resid, std::integral_constant<int, 64>{}, T{}); break;
+            default: go(resid, std::integral_constant<int, 0>{}, F{}); break;
+        }
+    };
+    if (y) pick(std::true_type{});
+    else pick(std::false_type{});
     MRHS_LAUNCHED("k_dslash_x2");
     return true;
 }
@@ -443,8 +476,8 @@ struct KArgsEO {
     int V2;      // V / 2
 };
 
-template <int MODE>
-__global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, const float2 *__restrict__ M,
+template <int MODE, int N, bool AOS>
+__global__ void __launch_bounds__(128, 3) k_eo_x2(const float2 *__restrict__ U, const float2 *__restrict__ M,
                                                    const float2 *__restrict__ in, const float2 *__restrict__ self,
                                                    float2 *__restrict__ out, KArgsEO e) {
     const KArgs32 &a = e.k;
@@ -488,23 +521,24 @@ __global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, 
         const bool flipB = mu == 3 && wrapB && a.tb < 0;
         // neighbours live in the other parity's half field, at index site / 2
         if (mu == 0) {
-            hop_x2<0, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
-            hop_x2<0, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+            hop_x2<0, true, N, AOS>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<0, false, N, AOS>(acc, U, in, a, sb >> 1, sb, flipB, r0);
         } else if (mu == 1) {
-            hop_x2<1, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
-            hop_x2<1, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+            hop_x2<1, true, N, AOS>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<1, false, N, AOS>(acc, U, in, a, sb >> 1, sb, flipB, r0);
         } else if (mu == 2) {
-            hop_x2<2, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
-            hop_x2<2, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+            hop_x2<2, true, N, AOS>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<2, false, N, AOS>(acc, U, in, a, sb >> 1, sb, flipB, r0);
         } else {
-            hop_x2<3, true>(acc, U, in, a, sf >> 1, site, flipF, r0);
-            hop_x2<3, false>(acc, U, in, a, sb >> 1, sb, flipB, r0);
+            hop_x2<3, true, N, AOS>(acc, U, in, a, sf >> 1, site, flipF, r0);
+            hop_x2<3, false, N, AOS>(acc, U, in, a, sb >> 1, sb, flipB, r0);
         }
     }
-    const int64_t base = (int64_t)cb * 12 * a.n + r0;
+    const int n = rhs_count<N>(a);
+    const int64_t base = (int64_t)cb * 12 * n + r0;
     if constexpr (MODE == EO_HOP) {
 #pragma unroll
-        for (int i = 0; i < 12; ++i) st_p2(out, base + (int64_t)i * a.n, acc[i]);
+        for (int i = 0; i < 12; ++i) st_p2(out, base + i * n, acc[i]);
     } else if constexpr (MODE == EO_AXPY_HOP || MODE == EO_CINV_AXPY_HOP) {
         const float2 half = make_float2(0.5f, 0.5f);
 #pragma unroll
@@ -512,14 +546,14 @@ __global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, 
             P2 v[6], o[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                const P2 y = ld_p2(self, base + (int64_t)(6 * chi + i) * a.n);
+                const P2 y = ld_p2(self, base + (6 * chi + i) * n);
                 const P2 ai = acc[6 * chi + i];
                 v[i] = {__ffma2_rn(half, ai.re, y.re), __ffma2_rn(half, ai.im, y.im)};
             }
-            if constexpr (MODE == EO_CINV_AXPY_HOP) site_mat_x2(M, a.V, site, chi, v, o);
+            if constexpr (MODE == EO_CINV_AXPY_HOP) site_mat_x2<AOS>(M, a.V, site, chi, v, o);
 #pragma unroll
             for (int i = 0; i < 6; ++i)
-                st_p2(out, base + (int64_t)(6 * chi + i) * a.n, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
+                st_p2(out, base + (6 * chi + i) * n, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
         }
     } else {
         const float2 quarter = make_float2(-0.25f, -0.25f);
@@ -528,8 +562,8 @@ __global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, 
             P2 v[6], o[6];
 #pragma unroll
             for (int i = 0; i < 6; ++i)
-                v[i] = MODE == EO_CINV_HOP ? acc[6 * chi + i] : ld_p2(self, base + (int64_t)(6 * chi + i) * a.n);
-            site_mat_x2(M, a.V, site, chi, v, o);
+                v[i] = MODE == EO_CINV_HOP ? acc[6 * chi + i] : ld_p2(self, base + (6 * chi + i) * n);
+            site_mat_x2<AOS>(M, a.V, site, chi, v, o);
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
                 P2 res = o[i];
@@ -537,7 +571,7 @@ __global__ void __launch_bounds__(128, 4) k_eo_x2(const float2 *__restrict__ U, 
                     const P2 ai = acc[6 * chi + i];
                     res = {__ffma2_rn(quarter, ai.re, o[i].re), __ffma2_rn(quarter, ai.im, o[i].im)};
                 }
-                st_p2(out, base + (int64_t)(6 * chi + i) * a.n, res);
+                st_p2(out, base + (6 * chi + i) * n, res);
             }
         }
     }
@@ -579,19 +613,40 @@ static void check_eo(const mrhs_lattice &lat, int n) {
     if (lat.g.V * 6LL * n >= (1LL << 31)) fail(MRHS_ERR_INVALID, "half-lattice field too large for 32-bit indexing");
 }
 
+enum { EO_NOMAT = 0, EO_MAT_C = 1, EO_MAT_CINV = 2 };
+
 template <int MODE>
-static void launch_eo(const mrhs_lattice &lat, const float2 *M, const float2 *in, const float2 *self, float2 *out,
-                      int n, int parity, cudaStream_t s) {
+static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const float2 *self, float2 *out, int n,
+                      int parity, cudaStream_t s) {
     const KArgsEO e = eo_args(lat, n, parity);
     const int64_t items = (int64_t)e.V2 * e.k.G;
+    const unsigned blocks = (unsigned)((items + 127) / 128);
     MRHS_TIMED("k_eo_x2", s);
-    k_eo_x2<MODE><<<(unsigned)((items + 127) / 128), 128, 0, s>>>(lat.U32.as<float2>(), M, in, self, out, e);
+    // as the full-lattice stencil: compile-time RHS count and site-major links /
+    // site matrices from 16 RHS on
+    auto go = [&](auto nc, auto aos) {
+        constexpr int NC = decltype(nc)::value;
+        constexpr bool AO = decltype(aos)::value;
+        const float2 *U = AO ? lat.U32a.as<float2>() : lat.U32.as<float2>();
+        const float2 *M = mat == EO_MAT_C      ? (AO ? lat.C32a.as<float2>() : lat.C32.as<float2>())
+                          : mat == EO_MAT_CINV ? (AO ? lat.Cinv32a.as<float2>() : lat.Cinv32.as<float2>())
+                                               : nullptr;
+        k_eo_x2<MODE, NC, AO><<<blocks, 128, 0, s>>>(U, M, in, self, out, e);
+    };
+    switch (n) {
+        case 16: go(std::integral_constant<int, 16>{}, std::true_type{}); break;
+        case 24: go(std::integral_constant<int, 24>{}, std::true_type{}); break;
+        case 32: go(std::integral_constant<int, 32>{}, std::true_type{}); break;
+        case 48: go(std::integral_constant<int, 48>{}, std::true_type{}); break;
+        case 64: go(std::integral_constant<int, 64>{}, std::true_type{}); break;
+        default: go(std::integral_constant<int, 0>{}, std::false_type{}); break;
+    }
     MRHS_LAUNCHED("k_eo_x2");
 }
 
 void hop_eo(const mrhs_lattice &lat, int out_parity, const void *in, void *out, int n, cudaStream_t s) {
     check_eo(lat, n);
-    launch_eo<EO_HOP>(lat, nullptr, static_cast<const float2 *>(in), nullptr, static_cast<float2 *>(out), n,
+    launch_eo<EO_HOP>(lat, EO_NOMAT, static_cast<const float2 *>(in), nullptr, static_cast<float2 *>(out), n,
                       out_parity, s);
 }
 
@@ -601,8 +656,8 @@ void schur_apply(const mrhs_lattice &lat, const void *in_odd, void *out_odd, int
     if (lat.cinv_singular) fail(MRHS_ERR_INVALID, "a block of the clover term is singular: no even-odd inverse");
     float2 *t_e = static_cast<float2 *>(tmp_even);
     // t_e = C_ee^-1 H_eo psi_o, then out_o = C_oo psi_o - 1/4 H_oe t_e
-    launch_eo<EO_CINV_HOP>(lat, lat.Cinv32.as<float2>(), static_cast<const float2 *>(in_odd), nullptr, t_e, n, 0, s);
-    launch_eo<EO_SCHUR>(lat, lat.C32.as<float2>(), t_e, static_cast<const float2 *>(in_odd),
+    launch_eo<EO_CINV_HOP>(lat, EO_MAT_CINV, static_cast<const float2 *>(in_odd), nullptr, t_e, n, 0, s);
+    launch_eo<EO_SCHUR>(lat, EO_MAT_C, t_e, static_cast<const float2 *>(in_odd),
                         static_cast<float2 *>(out_odd), n, 1, s);
 }
 
@@ -690,10 +745,10 @@ void eo_axpy_hop(const mrhs_lattice &lat, int out_parity, const void *self, cons
                  int n, cudaStream_t s) {
     check_eo(lat, n);
     if (cinv)
-        launch_eo<EO_CINV_AXPY_HOP>(lat, lat.Cinv32.as<float2>(), static_cast<const float2 *>(in),
+        launch_eo<EO_CINV_AXPY_HOP>(lat, EO_MAT_CINV, static_cast<const float2 *>(in),
                                     static_cast<const float2 *>(self), static_cast<float2 *>(out), n, out_parity, s);
     else
-        launch_eo<EO_AXPY_HOP>(lat, nullptr, static_cast<const float2 *>(in), static_cast<const float2 *>(self),
+        launch_eo<EO_AXPY_HOP>(lat, EO_NOMAT, static_cast<const float2 *>(in), static_cast<const float2 *>(self),
                                static_cast<float2 *>(out), n, out_parity, s);
 }
 
@@ -790,6 +845,20 @@ __global__ void k_gauge_to_soa(const double2 *__restrict__ aos, double2 *__restr
     u32[(int64_t)e * V + site] = make_float2((float)v.x, (float)v.y);
 }
 
+// site-major copy of an entry-major FP32 array: aos[x * E + e] = soa[e * V + x]
+__global__ void k_site_major32(const float2 *__restrict__ soa, float2 *__restrict__ aos, int64_t V, int E) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= V * E) return;
+    const int64_t x = i / E;
+    const int e = (int)(i - x * E);
+    aos[i] = soa[(int64_t)e * V + x];
+}
+
+static void site_major32(const DeviceBuffer &soa, DeviceBuffer &aos, int64_t V, cudaStream_t s) {
+    k_site_major32<<<ceil_div(V * 36, 256), 256, 0, s>>>(soa.as<float2>(), aos.as<float2>(), V, 36);
+    MRHS_LAUNCHED("k_site_major32");
+}
+
 void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s) {
     const int64_t V = lat.g.V;
     const int64_t n = V * 36;
@@ -797,6 +866,7 @@ void gauge_to_soa(mrhs_lattice &lat, const double *aos_dev, cudaStream_t s) {
                                                      lat.U64.as<double2>(), lat.U32.as<float2>(), V);
     MRHS_LAUNCHED("k_gauge_to_soa");
     split_df(lat.U64.ptr, lat.Udf.ptr, n, s);
+    site_major32(lat.U32, lat.U32a, V, s);
 }
 
 // ------------------------------------------------------------ clover build
@@ -1018,6 +1088,8 @@ void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s) {
     k_clover_inverse<<<ceil_div(2 * V, 128), 128, 0, s>>>(lat.C64.as<double2>(), V, lat.Cinv64.as<double2>(),
                                                           lat.Cinv32.as<float2>(), lat.CinvErr.as<int>());
     MRHS_LAUNCHED("k_clover_inverse");
+    site_major32(lat.C32, lat.C32a, V, s);
+    site_major32(lat.Cinv32, lat.Cinv32a, V, s);
 }
 
 }  // namespace mrhs

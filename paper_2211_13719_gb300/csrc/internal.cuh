@@ -22,6 +22,9 @@ struct mrhs_lattice {
     // inverse of the site matrix C per site, same compact layout as C (for the
     // even-odd decomposition); CinvErr: int, set when a block was singular
     mrhs::DeviceBuffer Cinv64, Cinv32, CinvErr;
+    // site-major FP32 copies for the paired-FP32 stencils at 16 RHS and more:
+    // links [V][4][9], clover and its inverse [V][36] (entry chi * 18 + q)
+    mrhs::DeviceBuffer U32a, C32a, Cinv32a;
     mrhs::DeviceBuffer EOtmp;  // half-lattice scratch of the Schur operator
     mrhs::DeviceBuffer SAPtmp; // full-lattice residual scratch of mrhs_sap_smooth
     bool has_gauge = false, has_clover = false;

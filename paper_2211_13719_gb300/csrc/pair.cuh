@@ -47,12 +47,18 @@ __device__ __forceinline__ void p2mac_conj(P2 &acc, float2 u, P2 h) {
 }
 
 // o = M v for chirality block chi of a compact Hermitian site matrix M (the
-// clover term C or its inverse): 3 diagonal pairs, then the 15 lower entries
+// clover term C or its inverse): 3 diagonal pairs, then the 15 lower entries.
+// AOS = false: entry (chi * 18 + q) of site x at M[(chi * 18 + q) * V + x]
+// (entry-major); AOS = true: at M[x * 36 + chi * 18 + q] (site-major, so the
+// 18 loads of a block are immediate offsets from one address).
+template <bool AOS = false>
 __device__ __forceinline__ void site_mat_x2(const float2 *__restrict__ M, int V, int site, int chi,
                                             const P2 (&v)[6], P2 (&o)[6]) {
+    const float2 *Mp = AOS ? M + (int64_t)site * 36 + chi * 18 : M + (int64_t)chi * 18 * V + site;
+    const int64_t st = AOS ? 1 : V;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const float2 d = __ldg(M + (int64_t)(chi * 18 + q) * V + site);
+        const float2 d = __ldg(Mp + q * st);
         const float2 d0 = make_float2(d.x, d.x), d1 = make_float2(d.y, d.y);
         o[2 * q] = {__fmul2_rn(d0, v[2 * q].re), __fmul2_rn(d0, v[2 * q].im)};
         o[2 * q + 1] = {__fmul2_rn(d1, v[2 * q + 1].re), __fmul2_rn(d1, v[2 * q + 1].im)};
@@ -62,7 +68,7 @@ __device__ __forceinline__ void site_mat_x2(const float2 *__restrict__ M, int V,
     for (int i = 1; i < 6; ++i) {
 #pragma unroll
         for (int j = 0; j < i; ++j, ++q) {
-            const float2 l = __ldg(M + (int64_t)(chi * 18 + q) * V + site);
+            const float2 l = __ldg(Mp + q * st);
             p2mac(o[i], l, v[j]);
             p2mac_conj(o[j], l, v[i]);
         }

@@ -23,6 +23,10 @@ CASES = [
     ((8, 4, 4, 6), 12, 1, True),
     ((2, 2, 2, 2), 2, -1, True),     # extent 2: the +-mu neighbours coincide
     ((4, 2, 6, 4), 48, -1, True),
+    ((4, 4, 4, 4), 16, -1, True),
+    ((6, 4, 2, 8), 24, 1, False),
+    ((4, 4, 2, 4), 32, -1, True),
+    ((2, 4, 2, 4), 64, -1, True),
 ]
 
 

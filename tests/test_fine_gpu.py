@@ -33,6 +33,11 @@ def _problem(dims, seed, hot=True):
     ((8, 8, 4, 4), 12, -1, False),
     ((4, 4, 2, 4), 64, -1, True),
     ((1, 2, 1, 4), 2, -1, True),     # extent 1: the +-mu neighbours are the site itself
+    # RHS counts with a compile-time kernel and site-major links / clover
+    ((4, 4, 4, 4), 16, -1, True),
+    ((6, 4, 2, 8), 24, 1, False),
+    ((4, 4, 2, 4), 32, -1, True),
+    ((4, 2, 6, 4), 48, -1, True),
 ])
 def test_apply_D_fp32_fp64_parity(dims, nrhs, tb, hot):
     mass, csw = -0.2, 1.0
