@@ -12,14 +12,19 @@
 //     rho = r_B;  q = D_BB rho;  alpha = <q, rho> / <q, q>;
 //     e_B += alpha rho;  rho -= alpha q.
 //
-// GB300 design: one CTA per (block of colour c, RHS pair) runs all MR steps
-// of its block system in shared memory.  rho and e of the block (bvol sites x
-// 12 components x 2 RHS, 48 KB each for a 4^4 block) never leave the SM; a
-// step is one in-block stencil pass (neighbours from shared memory, links and
-// clover from L2 / HBM, paired-FP32 arithmetic as the fine stencil) and one
-// block reduction of <q, rho> and <q, q> for the two RHS.  A hop that leaves
-// the block is dropped (D_BB), so no antiperiodic sign ever applies inside a
-// block: block boundaries sit on multiples of B and the time wrap is one.
+// GB300 design: one CTA per (block of colour c, group of RHS pairs) runs all
+// MR steps of its block systems on chip.  The block's forward links and clover
+// matrices (2 x 72 KB for a 4^4 block) are staged in shared memory once and
+// serve every RHS pair and step of the CTA; per pair, rho (48 KB) lives in
+// shared memory and e in registers.  A step is one in-block stencil pass
+// (neighbours and links from shared memory, paired-FP32 arithmetic as in the
+// fine stencil) and one block reduction of <q, rho> and <q, q> for the two RHS
+// of the pair.  A hop that leaves the block is dropped (D_BB), so no
+// antiperiodic sign ever applies inside a block: block boundaries sit on
+// multiples of B and the time wrap is one; the backward hop inside the block
+// uses the forward link of the in-block neighbour.
+#include <algorithm>
+
 #include "internal.cuh"
 #include "pair.cuh"
 #include "spin.cuh"
@@ -40,6 +45,8 @@ struct SapArgs {
     int bvol;
     int color;
     int steps;
+    int pair0;          // first RHS pair of the launch (0)
+    int pairs_per_cta;  // RHS pairs each CTA runs one after the other
 };
 
 // shared-memory field [12][bvol] of RHS pairs stored as (re r0, re r1, im r0, im r1)
@@ -51,10 +58,12 @@ __device__ __forceinline__ void sm_st(float4 *f, int bvol, int k, int t, P2 v) {
     f[k * bvol + t] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y);
 }
 
-// acc += (1 -+ gamma_mu) U h  for the in-block neighbour at local index nb
+// acc += (1 -+ gamma_mu) U h for the in-block neighbour at local index nb; the
+// block's forward links are staged in shared memory as Us[(mu * 9 + e) * bvol + s]
+// (the backward hop from t uses the forward link of its in-block neighbour nb)
 template <int MU, bool FWD>
-__device__ __forceinline__ void sap_hop(P2 (&acc)[12], const float2 *__restrict__ U, int V, const float4 *rho,
-                                        int bvol, int nb, int link_site) {
+__device__ __forceinline__ void sap_hop(P2 (&acc)[12], const float2 *Us, const float4 *rho, int bvol, int nb,
+                                        int link_s) {
     using P = Proj<MU>;
     constexpr int F0 = FWD ? P::F0 : neg_f<P::F0>::v;
     constexpr int F1 = FWD ? P::F1 : neg_f<P::F1>::v;
@@ -70,17 +79,18 @@ __device__ __forceinline__ void sap_hop(P2 (&acc)[12], const float2 *__restrict_
         h0[c] = p2add(p0, p2f<F0>(pa));
         h1[c] = p2add(p1, p2f<F1>(pb));
     }
+    const float2 *Ul = Us + MU * 9 * bvol + link_s;
 #pragma unroll
     for (int row = 0; row < 3; ++row) {
         P2 s0 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, s1 = s0;
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             if (FWD) {
-                const float2 u = __ldg(U + (int64_t)(MU * 9 + row * 3 + b) * V + link_site);
+                const float2 u = Ul[(row * 3 + b) * bvol];
                 p2mac(s0, u, h0[b]);
                 p2mac(s1, u, h1[b]);
             } else {
-                const float2 u = __ldg(U + (int64_t)(MU * 9 + b * 3 + row) * V + link_site);
+                const float2 u = Ul[(b * 3 + row) * bvol];
                 p2mac_conj(s0, u, h0[b]);
                 p2mac_conj(s1, u, h1[b]);
             }
@@ -93,11 +103,34 @@ __device__ __forceinline__ void sap_hop(P2 (&acc)[12], const float2 *__restrict_
 }
 
 template <int MU>
-__device__ __forceinline__ void sap_hop_pair(P2 (&acc)[12], const float2 *__restrict__ U, const SapArgs &a,
-                                             const float4 *rho, int t, const int lc[4], int lstride, int site,
-                                             int gstride) {
-    if (lc[MU] < a.B[MU] - 1) sap_hop<MU, true>(acc, U, a.V, rho, a.bvol, t + lstride, site);
-    if (lc[MU] > 0) sap_hop<MU, false>(acc, U, a.V, rho, a.bvol, t - lstride, site - gstride);
+__device__ __forceinline__ void sap_hop_pair(P2 (&acc)[12], const float2 *Us, const SapArgs &a, const float4 *rho,
+                                             int t, const int lc[4], int lstride) {
+    if (lc[MU] < a.B[MU] - 1) sap_hop<MU, true>(acc, Us, rho, a.bvol, t + lstride, t);
+    if (lc[MU] > 0) sap_hop<MU, false>(acc, Us, rho, a.bvol, t - lstride, t - lstride);
+}
+
+// o = C v for chirality block chi of the site matrix staged in shared memory as
+// Cs[(chi * 18 + q) * bvol + s] (3 diagonal pairs, then the 15 lower entries)
+__device__ __forceinline__ void sap_site_mat(const float2 *Cs, int bvol, int t, int chi, const P2 (&v)[6],
+                                             P2 (&o)[6]) {
+    const float2 *Mp = Cs + chi * 18 * bvol + t;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float2 d = Mp[q * bvol];
+        const float2 d0 = make_float2(d.x, d.x), d1 = make_float2(d.y, d.y);
+        o[2 * q] = {__fmul2_rn(d0, v[2 * q].re), __fmul2_rn(d0, v[2 * q].im)};
+        o[2 * q + 1] = {__fmul2_rn(d1, v[2 * q + 1].re), __fmul2_rn(d1, v[2 * q + 1].im)};
+    }
+    int q = 3;
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j < i; ++j, ++q) {
+            const float2 l = Mp[q * bvol];
+            p2mac(o[i], l, v[j]);
+            p2mac_conj(o[j], l, v[i]);
+        }
+    }
 }
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -106,16 +139,20 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_mr(const float2 *__restrict__ U, const float2 *__restrict__ C,
+// One CTA per (block of colour a.color, group of RHS pairs).  The block's
+// forward links and clover matrices are staged in shared memory once and serve
+// every RHS pair and MR step of the CTA; per pair, rho lives in shared memory,
+// e in registers.
+__global__ void __launch_bounds__(SAP_THREADS, 1) k_sap_mr(const float2 *__restrict__ U, const float2 *__restrict__ C,
                                                              const float2 *__restrict__ r, float2 *__restrict__ z,
                                                              SapArgs a) {
     extern __shared__ float4 sap_sm[];
-    float4 *rho = sap_sm;                       // [12][bvol]
-    float4 *esm = sap_sm + 12 * a.bvol;         // [12][bvol]
+    float4 *rho = sap_sm;                                         // [12][bvol]
+    float2 *Us = reinterpret_cast<float2 *>(sap_sm + 12 * a.bvol);  // [36][bvol]
+    float2 *Cs = Us + 36 * a.bvol;                                // [36][bvol]
     __shared__ float red[SAP_THREADS / 32][6];
     __shared__ float2 alpha_sm[2];
 
-    const int r0 = 2 * blockIdx.y;
     // the blockIdx.x-th block of colour a.color, blocks ordered (bx / 2, by, bz, bt)
     int q = blockIdx.x;
     const int hx = a.NB[0] / 2;
@@ -142,109 +179,124 @@ __global__ void __launch_bounds__(SAP_THREADS, 2) k_sap_mr(const float2 *__restr
     const int x = bx * a.B[0] + lc[0], y = by * a.B[1] + lc[1], zc = bz * a.B[2] + lc[2], tc = bt * a.B[3] + lc[3];
     const int site = x + a.L[0] * (y + a.L[1] * (zc + a.L[2] * tc));
     const int ls1 = a.B[0], ls2 = a.B[0] * a.B[1], ls3 = a.B[0] * a.B[1] * a.B[2];
-    const int gs1 = a.L[0], gs2 = a.L[0] * a.L[1], gs3 = a.L[0] * a.L[1] * a.L[2];
-    const int64_t base = (int64_t)site * 12 * a.n + r0;
     const P2 zero = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 
     if (active) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            sm_st(rho, a.bvol, k, t, ld_p2(r, base + (int64_t)k * a.n));
-            sm_st(esm, a.bvol, k, t, zero);
+#pragma unroll 4
+        for (int e = 0; e < 36; ++e) {
+            Us[e * a.bvol + t] = __ldg(U + (int64_t)e * a.V + site);
+            Cs[e * a.bvol + t] = __ldg(C + (int64_t)e * a.V + site);
         }
     }
-    __syncthreads();
 
     const float2 mhalf = make_float2(-0.5f, -0.5f);
-    for (int step = 0; step < a.steps; ++step) {
-        P2 qv[12];
-        float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int pair = a.pair0 + blockIdx.y * a.pairs_per_cta; pair < min(a.pair0 + (int)(blockIdx.y + 1) * a.pairs_per_cta, a.n / 2);
+         ++pair) {
+        const int64_t base = (int64_t)site * 12 * a.n + 2 * pair;
+        P2 e[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) e[k] = zero;
         if (active) {
-            P2 acc[12];
 #pragma unroll
-            for (int i = 0; i < 12; ++i) acc[i] = zero;
-            sap_hop_pair<0>(acc, U, a, rho, t, lc, 1, site, 1);
-            sap_hop_pair<1>(acc, U, a, rho, t, lc, ls1, site, gs1);
-            sap_hop_pair<2>(acc, U, a, rho, t, lc, ls2, site, gs2);
-            sap_hop_pair<3>(acc, U, a, rho, t, lc, ls3, site, gs3);
+            for (int k = 0; k < 12; ++k) sm_st(rho, a.bvol, k, t, ld_p2(r, base + (int64_t)k * a.n));
+        }
+        __syncthreads();  // rho of this pair (and, on the first pair, the staged links / clover) complete
+
+        for (int step = 0; step < a.steps; ++step) {
+            P2 qv[12];
+            float part[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (active) {
+                P2 acc[12];
 #pragma unroll
-            for (int chi = 0; chi < 2; ++chi) {
-                P2 v[6], o[6];
+                for (int i = 0; i < 12; ++i) acc[i] = zero;
+                sap_hop_pair<0>(acc, Us, a, rho, t, lc, 1);
+                sap_hop_pair<1>(acc, Us, a, rho, t, lc, ls1);
+                sap_hop_pair<2>(acc, Us, a, rho, t, lc, ls2);
+                sap_hop_pair<3>(acc, Us, a, rho, t, lc, ls3);
 #pragma unroll
-                for (int i = 0; i < 6; ++i) v[i] = sm_ld(rho, a.bvol, 6 * chi + i, t);
-                site_mat_x2(C, a.V, site, chi, v, o);
+                for (int chi = 0; chi < 2; ++chi) {
+                    P2 v[6], o[6];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const P2 ai = acc[6 * chi + i];
-                    const P2 qi = {__ffma2_rn(mhalf, ai.re, o[i].re), __ffma2_rn(mhalf, ai.im, o[i].im)};
-                    qv[6 * chi + i] = qi;
-                    // <q, rho> = sum conj(q) rho, and |q|^2, for both RHS of the pair
-                    part[0] += qi.re.x * v[i].re.x + qi.im.x * v[i].im.x;
-                    part[1] += qi.re.x * v[i].im.x - qi.im.x * v[i].re.x;
-                    part[2] += qi.re.y * v[i].re.y + qi.im.y * v[i].im.y;
-                    part[3] += qi.re.y * v[i].im.y - qi.im.y * v[i].re.y;
-                    part[4] += qi.re.x * qi.re.x + qi.im.x * qi.im.x;
-                    part[5] += qi.re.y * qi.re.y + qi.im.y * qi.im.y;
+                    for (int i = 0; i < 6; ++i) v[i] = sm_ld(rho, a.bvol, 6 * chi + i, t);
+                    sap_site_mat(Cs, a.bvol, t, chi, v, o);
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        const P2 ai = acc[6 * chi + i];
+                        const P2 qi = {__ffma2_rn(mhalf, ai.re, o[i].re), __ffma2_rn(mhalf, ai.im, o[i].im)};
+                        qv[6 * chi + i] = qi;
+                        // <q, rho> = sum conj(q) rho, and |q|^2, for both RHS of the pair
+                        part[0] += qi.re.x * v[i].re.x + qi.im.x * v[i].im.x;
+                        part[1] += qi.re.x * v[i].im.x - qi.im.x * v[i].re.x;
+                        part[2] += qi.re.y * v[i].re.y + qi.im.y * v[i].im.y;
+                        part[3] += qi.re.y * v[i].im.y - qi.im.y * v[i].re.y;
+                        part[4] += qi.re.x * qi.re.x + qi.im.x * qi.im.x;
+                        part[5] += qi.re.y * qi.re.y + qi.im.y * qi.im.y;
+                    }
                 }
             }
-        }
 #pragma unroll
-        for (int i = 0; i < 6; ++i) part[i] = warp_sum(part[i]);
-        if ((t & 31) == 0) {
+            for (int i = 0; i < 6; ++i) part[i] = warp_sum(part[i]);
+            if ((t & 31) == 0) {
 #pragma unroll
-            for (int i = 0; i < 6; ++i) red[t >> 5][i] = part[i];
-        }
-        __syncthreads();  // every read of rho for this step is done
-        if (t == 0) {
-            float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int w = 0; w < SAP_THREADS / 32; ++w)
+                for (int i = 0; i < 6; ++i) red[t >> 5][i] = part[i];
+            }
+            __syncthreads();  // every read of rho for this step is done
+            if (t == 0) {
+                float sm[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int w = 0; w < SAP_THREADS / 32; ++w)
 #pragma unroll
-                for (int i = 0; i < 6; ++i) s[i] += red[w][i];
-            // a block that has converged to zero keeps alpha = 0
-            const float tiny = 1.17549435e-38f;
-            alpha_sm[0] = s[4] > tiny ? make_float2(s[0] / s[4], s[1] / s[4]) : make_float2(0.f, 0.f);
-            alpha_sm[1] = s[5] > tiny ? make_float2(s[2] / s[5], s[3] / s[5]) : make_float2(0.f, 0.f);
+                    for (int i = 0; i < 6; ++i) sm[i] += red[w][i];
+                // a block that has converged to zero keeps alpha = 0
+                const float tiny = 1.17549435e-38f;
+                alpha_sm[0] = sm[4] > tiny ? make_float2(sm[0] / sm[4], sm[1] / sm[4]) : make_float2(0.f, 0.f);
+                alpha_sm[1] = sm[5] > tiny ? make_float2(sm[2] / sm[5], sm[3] / sm[5]) : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            if (active) {
+                const float2 al0 = alpha_sm[0], al1 = alpha_sm[1];
+                const float2 ar = make_float2(al0.x, al1.x), ai = make_float2(al0.y, al1.y);
+                const float2 nai = make_float2(-al0.y, -al1.y);
+                const float2 nar = make_float2(-al0.x, -al1.x);
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    P2 rk = sm_ld(rho, a.bvol, k, t);
+                    // e += alpha rho
+                    e[k].re = __ffma2_rn(ar, rk.re, e[k].re);
+                    e[k].re = __ffma2_rn(nai, rk.im, e[k].re);
+                    e[k].im = __ffma2_rn(ar, rk.im, e[k].im);
+                    e[k].im = __ffma2_rn(ai, rk.re, e[k].im);
+                    // rho -= alpha q
+                    const P2 qk = qv[k];
+                    rk.re = __ffma2_rn(nar, qk.re, rk.re);
+                    rk.re = __ffma2_rn(ai, qk.im, rk.re);
+                    rk.im = __ffma2_rn(nar, qk.im, rk.im);
+                    rk.im = __ffma2_rn(nai, qk.re, rk.im);
+                    sm_st(rho, a.bvol, k, t, rk);
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
         if (active) {
-            const float2 al0 = alpha_sm[0], al1 = alpha_sm[1];
-            const float2 ar = make_float2(al0.x, al1.x), ai = make_float2(al0.y, al1.y);
-            const float2 nai = make_float2(-al0.y, -al1.y);
-            const float2 nar = make_float2(-al0.x, -al1.x);
 #pragma unroll
             for (int k = 0; k < 12; ++k) {
-                P2 rk = sm_ld(rho, a.bvol, k, t);
-                P2 ek = sm_ld(esm, a.bvol, k, t);
-                // e += alpha rho
-                ek.re = __ffma2_rn(ar, rk.re, ek.re);
-                ek.re = __ffma2_rn(nai, rk.im, ek.re);
-                ek.im = __ffma2_rn(ar, rk.im, ek.im);
-                ek.im = __ffma2_rn(ai, rk.re, ek.im);
-                // rho -= alpha q
-                const P2 qk = qv[k];
-                rk.re = __ffma2_rn(nar, qk.re, rk.re);
-                rk.re = __ffma2_rn(ai, qk.im, rk.re);
-                rk.im = __ffma2_rn(nar, qk.im, rk.im);
-                rk.im = __ffma2_rn(nai, qk.re, rk.im);
-                sm_st(rho, a.bvol, k, t, rk);
-                sm_st(esm, a.bvol, k, t, ek);
+                const int64_t off = base + (int64_t)k * a.n;
+                const P2 zk = ld_p2(z, off);
+                const float4 o = make_float4(zk.re.x + e[k].re.x, zk.im.x + e[k].im.x, zk.re.y + e[k].re.y,
+                                             zk.im.y + e[k].im.y);
+                *reinterpret_cast<float4 *>(z + off) = o;
             }
         }
-        __syncthreads();
-    }
-    if (active) {
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-            const int64_t off = base + (int64_t)k * a.n;
-            const P2 zk = ld_p2(z, off);
-            const P2 ek = sm_ld(esm, a.bvol, k, t);
-            const float4 o = make_float4(zk.re.x + ek.re.x, zk.im.x + ek.im.x, zk.re.y + ek.re.y, zk.im.y + ek.im.y);
-            *reinterpret_cast<float4 *>(z + off) = o;
-        }
+        __syncthreads();  // the next pair overwrites rho
     }
 }
 
 }  // namespace
+
+static int current_sm_count_sap() {
+    int dev = 0;
+    MRHS_CUDA(cudaGetDevice(&dev));
+    return sm_count(dev);
+}
 
 bool sap_supported(const mrhs_lattice &lat, const int B[4], int n) {
     if (n < 2 || n % 2) return false;
@@ -278,16 +330,26 @@ void sap_smooth(const mrhs_lattice &lat, const void *v, void *z, int n, const in
         a.bvol *= B[mu];
     }
     a.steps = mr_steps;
-    const size_t smem = sizeof(float4) * 24 * (size_t)a.bvol;
+    a.pair0 = 0;
+    // per site: 12 RHS-pair entries of rho (16 B), 36 link and 36 clover entries (8 B)
+    const size_t smem = (sizeof(float4) * 12 + sizeof(float2) * 72) * (size_t)a.bvol;
     static thread_local int configured_dev = -1;
     int dev = 0;
     MRHS_CUDA(cudaGetDevice(&dev));
     if (configured_dev != dev) {
         MRHS_CUDA(cudaFuncSetAttribute(k_sap_mr, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)(sizeof(float4) * 24 * SAP_MAX_BVOL)));
+                                       (int)((sizeof(float4) * 12 + sizeof(float2) * 72) * SAP_MAX_BVOL)));
         configured_dev = dev;
     }
-    const dim3 grid((unsigned)(a.NB[0] * a.NB[1] * a.NB[2] * a.NB[3] / 2), (unsigned)(n / 2));
+    // one CTA per SM (192 KB of shared memory for a 4^4 block): split the RHS pairs
+    // of a block over CTAs so that the grid covers the SMs several times over
+    const int nblk = a.NB[0] * a.NB[1] * a.NB[2] * a.NB[3] / 2;
+    const int npairs = n / 2;
+    int groups = 1;
+    while (groups < npairs && (int64_t)nblk * groups < 16LL * current_sm_count_sap()) groups *= 2;
+    groups = std::min(groups, npairs);
+    a.pairs_per_cta = (npairs + groups - 1) / groups;
+    const dim3 grid((unsigned)nblk, (unsigned)((npairs + a.pairs_per_cta - 1) / a.pairs_per_cta));
     const float2 *vv = static_cast<const float2 *>(v);
     float2 *zz = static_cast<float2 *>(z);
     float2 *rr = static_cast<float2 *>(r_tmp);
