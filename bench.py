@@ -574,14 +574,14 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------- profiling cases
-def run_case(name, reps):
+def run_case(name, reps, args=None):
     """Small launches of one kernel family, for ncu captures (a few GB on the device).
 
     stencil:   FP32 fine operator, 24^4 lattice, 48 RHS
     stencil-sweep: FP32 fine operator, 24^4 lattice, nRHS 1 .. 64
     schur:     even-odd hop and Schur operator (FP32), 24^4 lattice, 48 RHS
     intergrid: tensor-core restriction + prolongation, 16^4 lattice, 4^4 aggregates, 32 vectors, 48 RHS
-    blas:      the FP32 batched multi-dot and linear combination, 16^4 x 12 rows, 48 RHS, 4 vectors
+    blas:      the FP32 batched multi-dot and linear combination, 16^4 x 12 rows (--blas-rows), 48 RHS, 4 vectors
     Prints one JSON line with the CUDA-event time per launch."""
     import numpy as np
     import torch
@@ -608,7 +608,7 @@ def run_case(name, reps):
 
     out = {"case": name, "nrhs": n, "reps": reps}
     if name == "blas":
-        rows = 16 ** 4 * 12
+        rows = args.blas_rows
         k = 4
         basis = torch.randn((k + 1, rows, n), dtype=torch.complex64, device="cuda")
         h = torch.empty((k + 1, n), dtype=torch.complex128, device="cuda")
@@ -695,9 +695,11 @@ def main():
     ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas"],
                     help="run a small profiling case of one kernel family instead of the benchmark")
     ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--blas-rows", type=int, default=16 ** 4 * 12,
+                    help="rows of the blas case (221184: the intermediate level, 3456 sites x 64 dof)")
     args = ap.parse_args()
     if args.case:
-        run_case(args.case, args.case_reps)
+        run_case(args.case, args.case_reps, args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
