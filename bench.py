@@ -556,6 +556,9 @@ def run_ours(args, rank, world, local_rank):
             extra["cpu_baseline"] = oracle_in_subprocess(1, 0)
         extra["clocks"] = clk.summary()
         extra["gpu_launches"] = launches
+        # the autotuner's choices (tile shapes of the FP32 stencils), made in the warm-up steps
+        extra["autotune"] = [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
+                             for e in mrhs.mrhs_tune_entries() if e["dims"] == tuple(dims)]
         line = {
             "metric": "MG solves/s at 1e-10", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,

@@ -101,6 +101,34 @@ uint64_t mrhs_kernel_launch_count(void);
 mrhs_status mrhs_kernel_timer_start(const char *kernel_name);
 mrhs_status mrhs_kernel_timer_stop(double *total_ms, int64_t *timed_launches, int64_t *captured_launches);
 
+/* Autotuner (no counterpart in the paper; it only changes how work is mapped
+ * onto the GPU, never an output value).  Kernels with launch variants (the
+ * site-tile shapes of the FP32 fine and even-odd stencils) time every variant
+ * with CUDA events on their stream at the first eager launch for a (kernel,
+ * lattice extents, nrhs) key and keep the fastest for the process; a launch
+ * made while its stream is captured into a CUDA graph never tunes (cached
+ * choice or the default variant 0).  Tuning is on unless the environment sets
+ * MRHS_AUTOTUNE=0 or mrhs_tune_set_enabled(0) is called.  mrhs_tune_save /
+ * mrhs_tune_load write / read the cache as text lines "kernel Lx Ly Lz Lt nrhs
+ * variant nvariants best_ms default_ms" (a load keeps the lines before a
+ * malformed one and returns MRHS_ERR_INVALID; a missing file gives
+ * MRHS_ERR_NOT_FOUND). */
+typedef struct {
+    char kernel[32];
+    int dims[4];
+    int nrhs;
+    int variant;       /* chosen variant, 0 = default            */
+    int nvariants;
+    float best_ms;     /* event time per launch of the choice    */
+    float default_ms;  /* event time per launch of variant 0     */
+} mrhs_tune_entry;
+void mrhs_tune_set_enabled(int enabled);
+void mrhs_tune_clear(void);
+int mrhs_tune_count(void);
+mrhs_status mrhs_tune_get(int index, mrhs_tune_entry *out);
+mrhs_status mrhs_tune_save(const char *path);
+mrhs_status mrhs_tune_load(const char *path);
+
 /* ------------------------------------------------------------------ */
 /* Lattice, gauge field, clover term                                   */
 /* ------------------------------------------------------------------ */

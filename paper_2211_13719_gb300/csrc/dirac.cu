@@ -15,6 +15,7 @@
 // forms a 2-spin half spinor h = psi_up -+ A psi_dn, multiplies it by the
 // link, and rebuilds the lower spins from the two products.
 #include <type_traits>
+#include <vector>
 
 #include "internal.cuh"
 #include "pair.cuh"
@@ -389,11 +390,9 @@ __global__ void __launch_bounds__(128, 3) k_dslash_x2(const float2 *__restrict__
     }
 }
 
-static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n,
-                             cudaStream_t s) {
-    if (n % 2 || lat.g.V * 12LL * n >= (1LL << 31) || lat.g.V * (int64_t)(n / 2) >= (1LL << 31)) return false;
-    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
-    if (!al(in) || !al(out) || (y && !al(y))) return false;
+// geometry of the paired stencil with tiles of the largest powers of two up to
+// pref[mu] that divide L[mu] (pref[0] may be L[0]: whole x rows)
+static KArgs32 x2_args(const mrhs_lattice &lat, int n, const int pref[4]) {
     KArgs32 a;
     for (int mu = 0; mu < 4; ++mu) a.L[mu] = lat.g.L[mu];
     a.V = (int)lat.g.V;
@@ -404,10 +403,6 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
     a.stride[2] = a.L[0] * a.L[1];
     a.stride[3] = a.L[0] * a.L[1] * a.L[2];
     a.tb = lat.g.tb;
-    // tile extents: the largest powers of two up to 1 x 4 x 8 x 8 that divide L;
-    // with fewer than 16 RHS a warp spans several sites, which must then be
-    // consecutive in x for coalesced loads: whole x rows
-    const int pref[4] = {n < 16 ? a.L[0] : 1, 4, 8, 8};
     a.tsites = 1;
     for (int mu = 0; mu < 4; ++mu) {
         int t = pref[mu];
@@ -416,37 +411,67 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
         a.tsites *= t;
     }
     for (int mu = 0; mu < 3; ++mu) a.NT[mu] = a.L[mu] / a.T[mu];
-    const int64_t items = (int64_t)a.V * a.G;
+    return a;
+}
+
+static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n,
+                             cudaStream_t s) {
+    if (n % 2 || lat.g.V * 12LL * n >= (1LL << 31) || lat.g.V * (int64_t)(n / 2) >= (1LL << 31)) return false;
+    auto al = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+    if (!al(in) || !al(out) || (y && !al(y))) return false;
+    // tile extents: the largest powers of two up to the preferred extents that
+    // divide L; with fewer than 16 RHS a warp spans several sites, which must
+    // then be consecutive in x for coalesced loads: whole x rows.  Variant 0 is
+    // 1 x 4 x 8 x 8 (measured best at 24^3 x 64, 48 RHS); the autotuner also
+    // tries the others per (lattice, n).
+    const int X = n < 16 ? lat.g.L[0] : 1;
+    const int prefs[][4] = {{X, 4, 8, 8}, {X, 4, 4, 8}, {X, 2, 8, 8}, {X, 8, 8, 8}, {X, 4, 8, 4}};
+    std::vector<KArgs32> args;
+    for (const auto &pref : prefs) {
+        const KArgs32 a = x2_args(lat, n, pref);
+        bool dup = false;
+        for (const KArgs32 &b : args) dup = dup || (b.T[0] == a.T[0] && b.T[1] == a.T[1] && b.T[2] == a.T[2] && b.T[3] == a.T[3]);
+        if (!dup) args.push_back(a);
+    }
+    const int64_t items = (int64_t)args[0].V * args[0].G;
     const int threads = 128;
     const unsigned blocks = (unsigned)((items + threads - 1) / threads);
-    MRHS_TIMED("k_dslash_x2", s);
     const float2 *yy = static_cast<const float2 *>(y);
     const float2 *ii = static_cast<const float2 *>(in);
     float2 *oo = static_cast<float2 *>(out);
     // 16, 24, 32, 48, 64 RHS: compile-time RHS count and site-major links / clover;
     // fewer: a warp spans several sites, whose link-major loads coalesce
-    auto go = [&](auto resid, auto nc, auto aos) {
-        constexpr bool R = decltype(resid)::value;
-        constexpr int NC = decltype(nc)::value;
-        constexpr bool AO = decltype(aos)::value;
-        const float2 *U = AO ? lat.U32a.as<float2>() : lat.U32.as<float2>();
-        const float2 *C = AO ? lat.C32a.as<float2>() : lat.C32.as<float2>();
-        k_dslash_x2<R, NC, AO><<<blocks, threads, 0, s>>>(U, C, ii, oo, yy, a);
+    auto launch = [&](int v) {
+        const KArgs32 &a = args[(size_t)v];
+        auto go = [&](auto resid, auto nc, auto aos) {
+            constexpr bool R = decltype(resid)::value;
+            constexpr int NC = decltype(nc)::value;
+            constexpr bool AO = decltype(aos)::value;
+            const float2 *U = AO ? lat.U32a.as<float2>() : lat.U32.as<float2>();
+            const float2 *C = AO ? lat.C32a.as<float2>() : lat.C32.as<float2>();
+            k_dslash_x2<R, NC, AO><<<blocks, threads, 0, s>>>(U, C, ii, oo, yy, a);
+        };
+        auto pick = [&](auto resid) {
+            using T = std::true_type;
+            using F = std::false_type;
+            switch (n) {
+                case 16: go(resid, std::integral_constant<int, 16>{}, T{}); break;
+                case 24: go(resid, std::integral_constant<int, 24>{}, T{}); break;
+                case 32: go(resid, std::integral_constant<int, 32>{}, T{}); break;
+                case 48: go(resid, std::integral_constant<int, 48>{}, T{}); break;
+                case 64: go(resid, std::integral_constant<int, 64>{}, T{}); break;
+                default: go(resid, std::integral_constant<int, 0>{}, F{}); break;
+            }
+        };
+        if (y) pick(std::true_type{});
+        else pick(std::false_type{});
+        MRHS_CUDA(cudaGetLastError());
     };
-    auto pick = [&](auto resid) {
-        using T = std::true_type;
-        using F = std::false_type;
-        switch (n) {
-            case 16: go(resid, std::integral_constant<int, 16>{}, T{}); break;
-            case 24: go(resid, std::integral_constant<int, 24>{}, T{}); break;
-            case 32: go(resid, std::integral_constant<int, 32>{}, T{}); break;
-            case 48: go(resid, std::integral_constant<int, 48>{}, T{}); break;
-            case 64: go(resid, std::integral_constant<int, 64>{}, T{}); break;
-            default: go(resid, std::integral_constant<int, 0>{}, F{}); break;
-        }
-    };
-    if (y) pick(std::true_type{});
-    else pick(std::false_type{});
+    // y == out (an in-place residual) would not survive repeated launches: no tuning then
+    const int v = y == out ? 0 : tune_pick(y ? "k_dslash_x2_resid" : "k_dslash_x2", lat.g.L, n, (int)args.size(),
+                                           launch, s);
+    MRHS_TIMED("k_dslash_x2", s);
+    launch(v);
     MRHS_LAUNCHED("k_dslash_x2");
     return true;
 }
@@ -577,7 +602,7 @@ __global__ void __launch_bounds__(128, 3) k_eo_x2(const float2 *__restrict__ U, 
     }
 }
 
-static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity) {
+static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity, const int pref[4] = nullptr) {
     KArgsEO e;
     KArgs32 &a = e.k;
     for (int mu = 0; mu < 4; ++mu) a.L[mu] = lat.g.L[mu];
@@ -589,9 +614,10 @@ static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity) {
     a.stride[2] = a.L[0] * a.L[1];
     a.stride[3] = a.L[0] * a.L[1] * a.L[2];
     a.tb = lat.g.tb;
-    // tiles: one x pair times the largest powers of two up to 4 x 8 x 8 that divide L
-    // (tsites counts output sites: one per x pair)
-    const int pref[4] = {2, 4, 8, 8};
+    // tiles: one x pair times the largest powers of two up to 4 x 8 x 8 (or `pref`)
+    // that divide L (tsites counts output sites: one per x pair)
+    static const int pref0[4] = {2, 4, 8, 8};
+    if (!pref) pref = pref0;
     a.T[0] = 2;
     a.tsites = 1;
     for (int mu = 1; mu < 4; ++mu) {
@@ -618,29 +644,47 @@ enum { EO_NOMAT = 0, EO_MAT_C = 1, EO_MAT_CINV = 2 };
 template <int MODE>
 static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const float2 *self, float2 *out, int n,
                       int parity, cudaStream_t s) {
-    const KArgsEO e = eo_args(lat, n, parity);
-    const int64_t items = (int64_t)e.V2 * e.k.G;
-    const unsigned blocks = (unsigned)((items + 127) / 128);
-    MRHS_TIMED("k_eo_x2", s);
-    // as the full-lattice stencil: compile-time RHS count and site-major links /
-    // site matrices from 16 RHS on
-    auto go = [&](auto nc, auto aos) {
-        constexpr int NC = decltype(nc)::value;
-        constexpr bool AO = decltype(aos)::value;
-        const float2 *U = AO ? lat.U32a.as<float2>() : lat.U32.as<float2>();
-        const float2 *M = mat == EO_MAT_C      ? (AO ? lat.C32a.as<float2>() : lat.C32.as<float2>())
-                          : mat == EO_MAT_CINV ? (AO ? lat.Cinv32a.as<float2>() : lat.Cinv32.as<float2>())
-                                               : nullptr;
-        k_eo_x2<MODE, NC, AO><<<blocks, 128, 0, s>>>(U, M, in, self, out, e);
-    };
-    switch (n) {
-        case 16: go(std::integral_constant<int, 16>{}, std::true_type{}); break;
-        case 24: go(std::integral_constant<int, 24>{}, std::true_type{}); break;
-        case 32: go(std::integral_constant<int, 32>{}, std::true_type{}); break;
-        case 48: go(std::integral_constant<int, 48>{}, std::true_type{}); break;
-        case 64: go(std::integral_constant<int, 64>{}, std::true_type{}); break;
-        default: go(std::integral_constant<int, 0>{}, std::false_type{}); break;
+    // tile variants for the autotuner (variant 0: one x pair x 4 x 8 x 8)
+    const int prefs[][4] = {{2, 4, 8, 8}, {2, 4, 4, 8}, {2, 2, 8, 8}, {2, 8, 8, 8}, {2, 4, 8, 4}};
+    std::vector<KArgsEO> args;
+    for (const auto &pref : prefs) {
+        const KArgsEO e = eo_args(lat, n, parity, pref);
+        bool dup = false;
+        for (const KArgsEO &b : args) dup = dup || (b.k.T[1] == e.k.T[1] && b.k.T[2] == e.k.T[2] && b.k.T[3] == e.k.T[3]);
+        if (!dup) args.push_back(e);
     }
+    const int64_t items = (int64_t)args[0].V2 * args[0].k.G;
+    const unsigned blocks = (unsigned)((items + 127) / 128);
+    // as the full-lattice stencil: compile-time RHS count and site-major links /
+    // site matrices for 16, 24, 32, 48, 64 RHS
+    auto launch = [&](int v) {
+        const KArgsEO &e = args[(size_t)v];
+        auto go = [&](auto nc, auto aos) {
+            constexpr int NC = decltype(nc)::value;
+            constexpr bool AO = decltype(aos)::value;
+            const float2 *U = AO ? lat.U32a.as<float2>() : lat.U32.as<float2>();
+            const float2 *M = mat == EO_MAT_C      ? (AO ? lat.C32a.as<float2>() : lat.C32.as<float2>())
+                              : mat == EO_MAT_CINV ? (AO ? lat.Cinv32a.as<float2>() : lat.Cinv32.as<float2>())
+                                                   : nullptr;
+            k_eo_x2<MODE, NC, AO><<<blocks, 128, 0, s>>>(U, M, in, self, out, e);
+        };
+        switch (n) {
+            case 16: go(std::integral_constant<int, 16>{}, std::true_type{}); break;
+            case 24: go(std::integral_constant<int, 24>{}, std::true_type{}); break;
+            case 32: go(std::integral_constant<int, 32>{}, std::true_type{}); break;
+            case 48: go(std::integral_constant<int, 48>{}, std::true_type{}); break;
+            case 64: go(std::integral_constant<int, 64>{}, std::true_type{}); break;
+            default: go(std::integral_constant<int, 0>{}, std::false_type{}); break;
+        }
+        MRHS_CUDA(cudaGetLastError());
+    };
+    static const char *names[] = {"k_eo_x2_hop", "k_eo_x2_cinv_hop", "k_eo_x2_schur", "k_eo_x2_axpy_hop",
+                                  "k_eo_x2_cinv_axpy_hop"};
+    // an output that aliases an input would not survive repeated launches: no tuning then
+    const bool alias = out == in || (self && out == self);
+    const int v = alias ? 0 : tune_pick(names[MODE], lat.g.L, n, (int)args.size(), launch, s);
+    MRHS_TIMED("k_eo_x2", s);
+    launch(v);
     MRHS_LAUNCHED("k_eo_x2");
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -33,6 +34,11 @@ struct mrhs_lattice {
 };
 
 namespace mrhs {
+
+// Autotuner: the variant (0 .. nvariants-1) to launch for this key; at the first
+// eager call it runs launch(v) for every variant, timed with events on s.
+int tune_pick(const char *kernel, const int dims[4], int n, int nvariants, const std::function<void(int)> &launch,
+              cudaStream_t s);
 
 // --------------------------------------------------------- fine operator
 // Selection of terms for the Galerkin construction (setup only).

@@ -103,6 +103,18 @@ class RequestStats(C.Structure):
     ]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [
+        ("kernel", C.c_char * 32),
+        ("dims", C.c_int * 4),
+        ("nrhs", C.c_int),
+        ("variant", C.c_int),
+        ("nvariants", C.c_int),
+        ("best_ms", C.c_float),
+        ("default_ms", C.c_float),
+    ]
+
+
 _P = C.c_void_p
 _I = C.c_int
 _I64 = C.c_int64
@@ -145,6 +157,12 @@ PROTOTYPES = {
     "mrhs_poll": (_I, [_P, C.c_uint64, C.POINTER(RequestStats)]),
     "mrhs_server_drain": (_I, [_P]),
     "mrhs_server_destroy": (None, [_P]),
+    "mrhs_tune_set_enabled": (None, [_I]),
+    "mrhs_tune_clear": (None, []),
+    "mrhs_tune_count": (_I, []),
+    "mrhs_tune_get": (_I, [_I, C.POINTER(TuneEntry)]),
+    "mrhs_tune_save": (_I, [C.c_char_p]),
+    "mrhs_tune_load": (_I, [C.c_char_p]),
 }
 
 _lib = None
@@ -232,6 +250,33 @@ def mrhs_get_clover(lat, out_host):
 
 def mrhs_apply_hop_eo(lat, out_parity, in_dev, out_dev, nrhs, stream=None):
     _check(lib().mrhs_apply_hop_eo(lat, int(out_parity), _ptr(in_dev), _ptr(out_dev), int(nrhs), _stream(stream)))
+
+
+def mrhs_tune_set_enabled(enabled: bool):
+    lib().mrhs_tune_set_enabled(1 if enabled else 0)
+
+
+def mrhs_tune_clear():
+    lib().mrhs_tune_clear()
+
+
+def mrhs_tune_entries():
+    """The autotuner's cached choices as dicts (kernel, dims, nrhs, variant, nvariants, best_ms, default_ms)."""
+    out = []
+    for i in range(lib().mrhs_tune_count()):
+        e = TuneEntry()
+        _check(lib().mrhs_tune_get(i, C.byref(e)))
+        out.append({"kernel": e.kernel.decode(), "dims": tuple(e.dims), "nrhs": e.nrhs, "variant": e.variant,
+                    "nvariants": e.nvariants, "best_ms": e.best_ms, "default_ms": e.default_ms})
+    return out
+
+
+def mrhs_tune_save(path: str):
+    _check(lib().mrhs_tune_save(path.encode()))
+
+
+def mrhs_tune_load(path: str):
+    _check(lib().mrhs_tune_load(path.encode()))
 
 
 def mrhs_apply_schur(lat, in_dev, out_dev, nrhs, stream=None):

@@ -65,3 +65,32 @@ def test_kernel_timer_state_without_gpu(lib):
     mrhs.mrhs_kernel_timer_start("k_dslash_x2")
     assert lib.mrhs_kernel_timer_start(b"k_dots_norm") == mrhs.MRHS_ERR_INVALID
     assert mrhs.mrhs_kernel_timer_stop() == (0.0, 0, 0)
+
+
+def test_tune_cache_file_roundtrip_without_gpu(lib, tmp_path):
+    """The autotuner's cache file: load, list, save and reload (no kernel runs)."""
+    mrhs.mrhs_tune_clear()
+    assert mrhs.mrhs_tune_entries() == []
+    src = tmp_path / "tune.txt"
+    src.write_text("# kernel Lx Ly Lz Lt nrhs variant nvariants best_ms default_ms\n"
+                   "k_dslash_x2 24 24 24 64 48 2 5 2.900000 3.000000\n"
+                   "k_eo_x2_schur 24 24 24 64 48 0 5 1.600000 1.600000\n")
+    mrhs.mrhs_tune_load(str(src))
+    ents = mrhs.mrhs_tune_entries()
+    assert [(e["kernel"], e["dims"], e["nrhs"], e["variant"], e["nvariants"]) for e in ents] == [
+        ("k_dslash_x2", (24, 24, 24, 64), 48, 2, 5), ("k_eo_x2_schur", (24, 24, 24, 64), 48, 0, 5)]
+    dst = tmp_path / "tune2.txt"
+    mrhs.mrhs_tune_save(str(dst))
+    mrhs.mrhs_tune_clear()
+    mrhs.mrhs_tune_load(str(dst))
+    assert [(e["kernel"], e["variant"], round(e["best_ms"], 3)) for e in mrhs.mrhs_tune_entries()] == [
+        ("k_dslash_x2", 2, 2.9), ("k_eo_x2_schur", 0, 1.6)]
+    bad = tmp_path / "bad.txt"
+    bad.write_text("k_dslash_x2 24 24 24 64 48 7 5 1.0 1.0\n")   # variant beyond nvariants
+    with pytest.raises(mrhs.MrhsError) as e:
+        mrhs.mrhs_tune_load(str(bad))
+    assert e.value.status == mrhs.MRHS_ERR_INVALID
+    with pytest.raises(mrhs.MrhsError) as e:
+        mrhs.mrhs_tune_load(str(tmp_path / "missing.txt"))
+    assert e.value.status == mrhs.MRHS_ERR_NOT_FOUND
+    mrhs.mrhs_tune_clear()
