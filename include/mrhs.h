@@ -105,7 +105,8 @@ mrhs_status mrhs_kernel_timer_stop(double *total_ms, int64_t *timed_launches, in
  * onto the GPU, never an output value).  Kernels with launch variants (the
  * site-tile shapes of the FP32 fine and even-odd stencils) time every variant
  * with CUDA events on their stream at the first eager launch for a (kernel,
- * lattice extents, nrhs) key and keep the fastest for the process; a launch
+ * lattice extents, nrhs) key and keep the fastest for the process (the
+ * default variant 0 unless another is more than 3 % faster); a launch
  * made while its stream is captured into a CUDA graph never tunes (cached
  * choice or the default variant 0).  Tuning is on unless the environment sets
  * MRHS_AUTOTUNE=0 or mrhs_tune_set_enabled(0) is called.  mrhs_tune_save /

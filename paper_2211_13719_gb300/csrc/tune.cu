@@ -1,11 +1,12 @@
 // Autotuner for launch variants that change only how work is mapped onto the
 // GPU, never the arithmetic of an output element: a kernel family offers a
-// few variants (here the site-tile shapes of the FP32 stencils), the first
+// few variants (here the site-tile shapes of the FP32 stencils), and the first
 // eager launch for a (kernel, lattice extents, RHS count) key times each
-// variant with CUDA events on the launching stream and the fastest is cached
-// for the rest of the process (and can be saved to / loaded from a text
-// file).  Launches made while the stream is being captured into a CUDA graph
-// never tune: they use the cached choice or variant 0.
+// variant with CUDA events on the launching stream.  The choice, cached for
+// the rest of the process and savable to / loadable from a text file, is the
+// fastest variant if it beats the default (variant 0) by more than 3 %, else
+// the default.  Launches made while the stream is being captured into a CUDA
+// graph never tune: they use the cached choice or variant 0.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -108,6 +109,10 @@ int tune_pick(const char *kernel, const int dims[4], int n, int nvariants, const
     cudaEventDestroy(e1);
     for (int i = 1; i < nvariants; ++i)
         if (ms[i] < ms[v.variant]) v.variant = i;
+    // keep the default unless another variant is clearly faster: differences
+    // within the run-to-run spread of a few launches are not a reason to switch
+    constexpr float kMargin = 0.03f;
+    if (ms[v.variant] > (1.f - kMargin) * ms[0]) v.variant = 0;
     v.best_ms = ms[v.variant];
     v.default_ms = ms[0];
     std::lock_guard<std::mutex> lk(t.mu);
