@@ -22,6 +22,7 @@ krylov       per-RHS GMRES / flexible GMRES with batched inner products (Sec. 7,
 mg           null-vector setup, V-cycle, MG-preconditioned FGMRES solve (Sec. 8)
 evenodd      checkerboard decomposition, Schur complement D_hat (Sec. 4, M_eooe)
 sap          Schwarz alternating procedure smoother (Sec. 9 outlook)
+gcrodr       GCRO-DR coarsest-level solver with subspace recycling (Sec. 9 outlook)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against a closed form, an invariant or a brute-force

@@ -10,8 +10,11 @@ the setup or the cycle, so the oracle fixes these readings:
 * V-cycle on level l for a residual v:
     c = R_l v;
     e = approximate A_{l+1}^{-1} c: GMRES(`coarse_m`) for `coarse_cycles`
-        cycles if l+1 is the coarsest level, otherwise one FGMRES(`inter_m`)
-        cycle preconditioned by the V-cycle of level l+1;
+        cycles if l+1 is the coarsest level (with `coarse_solver` "gcrodr":
+        GCRO-DR(`coarse_m`, `coarse_recycle`) cycles whose recycle space, one
+        per RHS, carries over from one V-cycle's coarsest solve to the next),
+        otherwise one FGMRES(`inter_m`) cycle preconditioned by the V-cycle of
+        level l+1;
     z0 = P_l e;
     z = `smooth_m` iterations of GMRES on A_l v from z0 (post-smoothing only);
   with `smoother_evenodd` the fine level's post-smoothing is instead
@@ -27,7 +30,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import coarse, evenodd, krylov, sap, wilson
+from . import coarse, evenodd, gcrodr, krylov, sap, wilson
 from .conventions import FINE_CHIRALITY
 
 
@@ -49,6 +52,8 @@ class MGParams:
     sap_block: tuple = (4, 4, 4, 4)
     sap_cycles: int = 1
     sap_mr: int = 4
+    coarse_solver: str = "gmres"   # or "gcrodr": GCRO-DR(coarse_m, coarse_recycle) with a recycle space
+    coarse_recycle: int = 0        # kept per RHS across the coarsest solves of all V-cycles
 
 
 @dataclass
@@ -61,6 +66,7 @@ class Level:
     P: np.ndarray = None         # prolongator to the next level
     block: tuple = None
     eo: tuple = None             # fine level: (U, site matrix C, dims, antiperiodic) for the even-odd smoother
+    recycle: list = None         # coarsest level with GCRO-DR: one recycle space per RHS
 
 
 def setup_nullvecs(apply_A, v0: np.ndarray, sweeps: int, m: int) -> np.ndarray:
@@ -113,7 +119,10 @@ def vcycle(levels, l: int, v: np.ndarray, params: MGParams) -> np.ndarray:
     last = len(levels) - 1
     c = coarse.restrict(lev.P, v, lev.dims, lev.block)
     nxt = levels[l + 1]
-    if l + 1 == last:
+    if l + 1 == last and params.coarse_solver == "gcrodr":
+        e, nxt.recycle, _ = gcrodr.solve(nxt.apply, c, np.zeros_like(c), params.coarse_m, params.coarse_recycle,
+                                         0.0, params.coarse_cycles, nxt.recycle)
+    elif l + 1 == last:
         e = krylov.gmres(nxt.apply, c, np.zeros_like(c), params.coarse_m, params.coarse_cycles)
     else:
         e = krylov.fgmres_fixed(nxt.apply, c, lambda u: vcycle(levels, l + 1, u, params),
