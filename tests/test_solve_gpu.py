@@ -159,3 +159,30 @@ def test_repeated_solve_is_deterministic(problem):
     (x1, r1, s1), (x2, r2, s2) = outs
     assert s1.inner_iters == s2.inner_iters and s1.outer_iters == s2.outer_iters
     assert np.array_equal(x1, x2)
+
+
+def test_not_converged_returns_the_partial_solution(problem):
+    """An outer iteration cap below what the tolerance needs: the solve returns
+    MRHS_ERR_NOT_CONVERGED with x holding the iterate reached and rel its true
+    FP64 relative residual (failure detection by status, not by abort)."""
+    U, b, v0 = problem
+    params = dict(n_levels=2, blocks=BLOCKS, nvec=NVEC, setup_sweeps=4, setup_m=8, smooth_m=4, coarse_m=16,
+                  coarse_cycles=2, inner_m=8, inner_tol=1e-5, outer_m=4, max_outer_iters=1, max_rhs=NRHS,
+                  coarse_precision=mrhs.MRHS_FP32)
+    lat = make_lattice(U, DIMS, MASS, CSW)
+    mg = make_mg(lat, params, [v0])
+    try:
+        d_b, d_x = to_dev(b), to_dev(np.zeros_like(b))
+        rel = np.zeros(NRHS)
+        status, st = mrhs.mrhs_solve(mg, d_b, d_x, NRHS, 1e-14, rel, allow_not_converged=True)
+        x = to_host(d_x)
+    finally:
+        mrhs.mrhs_destroy_mg(mg)
+        mrhs.mrhs_destroy_lattice(lat)
+    assert status == mrhs.MRHS_ERR_NOT_CONVERGED
+    assert np.all(np.isfinite(x))
+    C = wilson.clover_term(U, DIMS, CSW)
+    true_rel = krylov.norms(b - wilson.apply_D(U, C, x, DIMS, MASS)) / krylov.norms(b)
+    assert np.all(rel > 1e-14)
+    assert np.all(true_rel < 1e-2)     # one outer step, preconditioned by an inner solve to 1e-5
+    assert np.allclose(rel, true_rel, rtol=1e-3, atol=1e-13)
