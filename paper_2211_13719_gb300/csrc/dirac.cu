@@ -8,7 +8,10 @@
 // FP32) while every gauge link and clover entry is a single broadcast load
 // shared by all RHS of the site: the MRHS reuse of Sec. 2.  With few RHS a
 // warp spans many sites and the link-major (site-innermost) layout of U and
-// of the clover keeps those loads coalesced as well.
+// of the clover keeps those loads coalesced as well; from 16 RHS on, where a
+// warp covers one or two sites, the paired FP32 kernels read site-major
+// copies instead, so the entries of one link or clover block are immediate
+// offsets from one address.
 //
 // Spin projection (chiral basis, gamma_mu = [[0, A_mu], [A_mu^+, 0]] with
 // A_k = -i sigma_k, A_t = 1): (1 -+ gamma_mu) psi has rank 2, so each hop
