@@ -268,7 +268,10 @@ def gauge_field(w):
     import numpy as np
 
     import synth
-    cache = f"/tmp/mrhs_bench_gauge_{w['dims']}_{w['eps']}_{w['gauge_seed']}.npy".replace(" ", "")
+    # keyed on the generator's source, so a change to synth never reuses a stale field
+    with open(os.path.join(ROOT, "synth", "fields.py"), "rb") as f:
+        gen = hashlib.sha256(f.read()).hexdigest()[:12]
+    cache = f"/tmp/mrhs_bench_gauge_{w['dims']}_{w['eps']}_{w['gauge_seed']}_{gen}.npy".replace(" ", "")
     if os.path.exists(cache):
         try:
             return np.load(cache)

@@ -231,10 +231,12 @@ mrhs_status mrhs_blas_lincomb(void *w_dev, const void *basis_dev, int k,
  * hosts that reserve all device memory up front, programs whose memory
  * belongs to another allocator): it never calls cudaMalloc or cudaFree.
  * Its reduction scratch is a statically allocated 4.1 MiB device array shared
- * by all calls; nrhs is limited to 1..64 (MRHS_ERR_INVALID beyond).  The
- * first call on a device looks the array up (cudaGetSymbolAddress) with that
- * device current: make it before any stream capture.  Calls that overlap on
- * the GPU race on the shared scratch; order them on one stream. */
+ * by all calls; nrhs is limited to 1..64 (MRHS_ERR_INVALID beyond).  Every
+ * call looks the array up (cudaGetSymbolAddress, no allocation) on the
+ * caller's current device, so a device reset does not leave a stale address.
+ * The first call on a device may load the library's module there: make it
+ * before any stream capture.  Calls that overlap on the GPU race on the
+ * shared scratch; order them on one stream. */
 mrhs_status mrhs_blas_multi_dot_noalloc(const void *basis_dev, int k, const void *w_dev,
                                         int64_t rows, int nrhs, mrhs_precision prec,
                                         void *out_dev, void *stream);
@@ -312,6 +314,11 @@ mrhs_status mrhs_mg_get_coarse_links(mrhs_mg *mg, int level, double *host_out);
  * on CUDA cores. */
 mrhs_status mrhs_restrict(mrhs_mg *mg, int level, const void *fine_dev,
                           void *coarse_dev, int nrhs, void *stream);
+/* The tensor-core forms of mrhs_restrict, mrhs_prolong and mrhs_coarse_apply,
+ * and mrhs_vcycle, read the kernels' bounded-wait flag after the launch, so
+ * they return only after their GPU work on `stream` is done; a wait that
+ * gave up (an operand copy that never landed) returns MRHS_ERR_TIMEOUT and
+ * clears the flag, the output then being incomplete. */
 
 /* Prolongation psi = P c from level+1 to level `level` (Sec. 5), FP32
  * fields, on the tensor cores or CUDA cores as for mrhs_restrict. */
@@ -354,6 +361,19 @@ typedef struct {
  * breakdown of the paper's Sec. 8 table. */
 mrhs_status mrhs_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, double tol,
                        double *rel_res_host, mrhs_solve_stats *stats, void *stream);
+/* A solve also returns MRHS_ERR_TIMEOUT when a tensor-core kernel's bounded
+ * mbarrier wait gave up (the flags are read after every inner FGMRES cycle
+ * and at the end); x then holds an incomplete iterate.  The flags are
+ * cleared, so the next call on the same hierarchy starts clean. */
+
+/* Testing hook, not part of the paper's method: the next `launches` launches
+ * of the 16-bit tensor-core coarse stencil that are not being recorded into
+ * a CUDA graph give up their first operand wait at once (zero try_wait
+ * rounds) instead of after the normal bound.  The kernel still waits for
+ * every copy it has issued before it frees its tensor memory and returns,
+ * so nothing is left in flight; the call that launched it returns
+ * MRHS_ERR_TIMEOUT.  0 cancels.  MRHS_ERR_INVALID for launches < 0. */
+mrhs_status mrhs_debug_expire_waits(int launches);
 
 /* ------------------------------------------------------------------ */
 /* Serving: continuous batching of solve requests                      */

@@ -10,13 +10,13 @@
 // allocates.
 //
 // Scratch: one file-scope array shared by every call in the process (each
-// GPU that loads the library holds its own copy until exit).  Its device
-// address is looked up once per device, with that device current, by the
-// first call on that device; make that first call before any stream capture.
-// Calls that overlap on the GPU (other streams, other host threads) race on
-// the shared scratch: order them on one stream.
-#include <mutex>
-
+// GPU that loads the library holds its own copy until exit).  Every call
+// looks its device address up (cudaGetSymbolAddress, which allocates
+// nothing) with the caller's device current, so the address stays right
+// after a device reset or a new primary context.  The first call on a
+// device may also load the library's module onto it: make that first call
+// before any stream capture.  Calls that overlap on the GPU (other streams,
+// other host threads) race on the shared scratch: order them on one stream.
 #include "internal.cuh"
 
 namespace mrhs {
@@ -40,28 +40,22 @@ struct DevScratch {
     unsigned int *counter = nullptr;
 };
 
-std::mutex g_noalloc_mu;
-DevScratch g_noalloc_dev[64];
-
-DevScratch noalloc_scratch(int device) {
-    if (device < 0 || device >= 64) fail(MRHS_ERR_INVALID, "device index out of range");
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    DevScratch &d = g_noalloc_dev[device];
-    if (!d.partials) {
-        void *p = nullptr, *c = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            fail(MRHS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
-        }
-        e = cudaGetSymbolAddress(&c, g_noalloc_counter);
-        if (e != cudaSuccess) {
-            (void)cudaGetLastError();
-            fail(MRHS_ERR_CUDA, std::string("cudaGetSymbolAddress(counter): ") + cudaGetErrorString(e));
-        }
-        d.partials = static_cast<double2 *>(p);
-        d.counter = static_cast<unsigned int *>(c);
+// the device addresses of the two arrays on the current device
+DevScratch noalloc_scratch() {
+    DevScratch d;
+    void *p = nullptr, *c = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        fail(MRHS_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
     }
+    e = cudaGetSymbolAddress(&c, g_noalloc_counter);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        fail(MRHS_ERR_CUDA, std::string("cudaGetSymbolAddress(counter): ") + cudaGetErrorString(e));
+    }
+    d.partials = static_cast<double2 *>(p);
+    d.counter = static_cast<unsigned int *>(c);
     return d;
 }
 
@@ -76,9 +70,7 @@ extern "C" mrhs_status mrhs_blas_multi_dot_noalloc(const void *basis_dev, int k,
         if (nrhs < 1 || nrhs > NOALLOC_MAX_RHS)
             fail(MRHS_ERR_INVALID, "nrhs must be in 1..64 for the no-allocation multi-dot (static scratch limit)");
         if (prec != MRHS_FP32 && prec != MRHS_FP64) fail(MRHS_ERR_INVALID, "precision must be FP32 or FP64");
-        int dev = 0;
-        MRHS_CUDA(cudaGetDevice(&dev));
-        const DevScratch d = noalloc_scratch(dev);
+        const DevScratch d = noalloc_scratch();
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         // the completion counter must start at zero (a previous call that failed
         // part-way could have left it set)

@@ -30,15 +30,24 @@
 //
 // Every wait on an mbarrier is bounded; on expiry the kernel records an
 // error flag, drains its outstanding copies (bounded), frees its tensor
-// memory and returns.  The host reads the flag at the end of a solve.
+// memory and returns.  The host reads the flag after every standalone apply
+// and during a solve, and turns it into MRHS_ERR_TIMEOUT.  For tests,
+// mrhs_debug_expire_waits makes the first operand wait of the next launches
+// give up at once (zero try_wait rounds); the drain then still waits for
+// every copy already issued, so nothing is left in flight.
 #include <algorithm>
+#include <atomic>
 
 #include "mg.cuh"
 #include "tc_common.cuh"
 
 namespace mrhs {
+mrhs_status api_record(mrhs_status code, const std::string &msg);
 
 namespace {
+
+// launches (outside stream capture) whose first operand wait is to expire at once
+std::atomic<int> g_expire_waits{0};
 
 using namespace tc;
 
@@ -53,6 +62,7 @@ struct TcArgs {
     int n, npad;
     uint32_t idesc;
     uint32_t tmem_cols;
+    uint32_t first_limit;  // try_wait rounds of the first operand wait (SPIN_LIMIT; 0 when a test expires it)
 };
 
 __device__ __forceinline__ int64_t nb_site(int64_t site, const int L[4], int d) {
@@ -119,7 +129,7 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ A
             const int e = step - (STAGES - 1);
             if (e >= 0 && e < 9) {
                 const int s = e % STAGES;
-                ok = mbar_wait(full0 + 8 * s, (e / STAGES) & 1);
+                ok = mbar_wait_n(full0 + 8 * s, (e / STAGES) & 1, e == 0 ? a.first_limit : SPIN_LIMIT);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sa = sbase + s * stage_bytes, sb = sa + A_TILE;
@@ -325,6 +335,17 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
     a.npad = npad;
     a.idesc = idesc_16bit(MROWS, npad, c.tc_fmt == MRHS_FP16 ? 0u : 1u);
     a.tmem_cols = npad <= 32 ? 32 : (npad <= 64 ? 64 : 128);
+    a.first_limit = SPIN_LIMIT;
+    {
+        // a launch recorded into a graph would keep the expired limit for every replay: only eager launches
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        MRHS_CUDA(cudaStreamIsCapturing(s, &cap));
+        int left = g_expire_waits.load();
+        while (cap == cudaStreamCaptureStatusNone && left > 0 &&
+               !g_expire_waits.compare_exchange_weak(left, left - 1)) {
+        }
+        if (cap == cudaStreamCaptureStatusNone && left > 0) a.first_limit = 0;
+    }
     const size_t smem = tc_smem_bytes(npad);
     static bool attr = false;
     if (!attr) {
@@ -337,11 +358,18 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
     MRHS_LAUNCHED("k_coarse_tc");
 }
 
-int coarse_tc_error(const Level &c) {
+int coarse_tc_error(const Level &c, cudaStream_t s) {
     if (!c.TcErr.ptr) return 0;
     int e = 0;
-    MRHS_CUDA(cudaMemcpy(&e, c.TcErr.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    MRHS_CUDA(cudaMemcpyAsync(&e, c.TcErr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA(cudaStreamSynchronize(s));
     return e;
 }
 
 }  // namespace mrhs
+
+extern "C" mrhs_status mrhs_debug_expire_waits(int launches) {
+    if (launches < 0) return mrhs::api_record(MRHS_ERR_INVALID, "launches must be >= 0");
+    mrhs::g_expire_waits.store(launches);
+    return mrhs::api_record(MRHS_OK, "");
+}

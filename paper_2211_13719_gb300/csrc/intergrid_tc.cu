@@ -599,10 +599,11 @@ void prolong_fields_tc(const Level &f, const Level &c, const float2 *coarse, flo
     MRHS_LAUNCHED("k_prolong_tc");
 }
 
-int intergrid_tc_error(const Level &f) {
+int intergrid_tc_error(const Level &f, cudaStream_t s) {
     if (!f.IgErr.ptr) return 0;
     int e = 0;
-    MRHS_CUDA(cudaMemcpy(&e, f.IgErr.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    MRHS_CUDA(cudaMemcpyAsync(&e, f.IgErr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA(cudaStreamSynchronize(s));
     return e;
 }
 

@@ -57,8 +57,9 @@ void coarse_apply_fp32(const Level &c, const float2 *in, float2 *out, const floa
 // BF16 tensor-core stencil (dof == 64): out = A in (or y - A in)
 void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const float2 *y, int n, cudaStream_t s);
 bool coarse_bf16_supported(const Level &c);
-// nonzero if a tensor-core stencil launch on this level gave up waiting (reads device memory)
-int coarse_tc_error(const Level &c);
+// nonzero if a tensor-core stencil launch on this level gave up waiting (reads the
+// flag after the work queued on s, synchronising s)
+int coarse_tc_error(const Level &c, cudaStream_t s);
 void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s);
 // tensor-core restriction / prolongation (FP16, <= 32 null vectors, <= 64 RHS)
 bool intergrid_tc_supported(const Level &f);
@@ -67,7 +68,7 @@ void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s);
 void restrict_fields_tc(const Level &f, const Level &c, const float2 *fine, float2 *coarse, int n, int64_t ostride,
                         bool unit_norm, cudaStream_t s);
 void prolong_fields_tc(const Level &f, const Level &c, const float2 *coarse, float2 *fine, int n, cudaStream_t s);
-int intergrid_tc_error(const Level &f);
+int intergrid_tc_error(const Level &f, cudaStream_t s);
 // FP64 modified Gram-Schmidt (twice) of the chiral halves of `vecs` per aggregate, in place
 void block_orthonormalize(const Level &f, double2 *vecs, cudaStream_t s);
 // P [V][dof][N] -> Pexp [V][dof][2N] with column K = chi*N + k nonzero only on chirality chi

@@ -31,6 +31,11 @@ mrhs_status api_record(mrhs_status code, const std::string &msg);
 
 using namespace mrhs;
 
+namespace mrhs {
+void check_wait_flags(const Level &L, cudaStream_t s);
+void check_all_wait_flags(const mrhs_mg &mg, cudaStream_t s);
+}
+
 namespace {
 
 int current_sm_count() {
@@ -399,6 +404,8 @@ int inner_solve(mrhs_mg &mg, const float2 *b, float2 *x, int n, const std::vecto
         const int m = std::min(mg.p.inner_m, mg.p.inner_max_iters - total);
         total += krylov_cycle(A, &M, b, x, n, m, mg.inner, s, first, &chk);
         first = false;
+        // a tensor-core wait that gave up leaves a V-cycle without an operand: stop here
+        check_all_wait_flags(mg, s);
     }
     return total;
 }
@@ -531,6 +538,34 @@ void alloc_workspace(mrhs_mg &mg) {
 // ------------------------------------------------------------- solve
 namespace mrhs {
 
+// The tensor-core kernels record a bounded mbarrier wait that gave up in a
+// per-level flag (their result then lacks an operand).  Read the flags of
+// level l's coarse stencil and of its transfer to level l + 1 after the work
+// queued on s, clear them, and fail with MRHS_ERR_TIMEOUT if one was set.
+void check_wait_flags(const Level &L, cudaStream_t s) {
+    if (coarse_tc_error(L, s)) {
+        MRHS_CUDA(cudaMemsetAsync(L.TcErr.ptr, 0, sizeof(int), s));
+        MRHS_CUDA(cudaStreamSynchronize(s));
+        fail(MRHS_ERR_TIMEOUT, "tensor-core coarse stencil gave up waiting for its operands");
+    }
+    if (intergrid_tc_error(L, s)) {
+        MRHS_CUDA(cudaMemsetAsync(L.IgErr.ptr, 0, sizeof(int), s));
+        MRHS_CUDA(cudaStreamSynchronize(s));
+        fail(MRHS_ERR_TIMEOUT, "tensor-core restriction / prolongation gave up waiting");
+    }
+}
+
+void check_all_wait_flags(const mrhs_mg &mg, cudaStream_t s) {
+    for (int l = 0; l < mg.nlev; ++l) check_wait_flags(mg.lev[l], s);
+}
+
+void clear_all_wait_flags(const mrhs_mg &mg, cudaStream_t s) {
+    for (int l = 0; l < mg.nlev; ++l) {
+        if (mg.lev[l].TcErr.ptr) MRHS_CUDA(cudaMemsetAsync(mg.lev[l].TcErr.ptr, 0, sizeof(int), s));
+        if (mg.lev[l].IgErr.ptr) MRHS_CUDA(cudaMemsetAsync(mg.lev[l].IgErr.ptr, 0, sizeof(int), s));
+    }
+}
+
 // Outer FP64 FGMRES; returns true if every RHS r reached tols[r].
 // max_outer > 0 caps the outer iterations of this call (else the params' cap);
 // stop(res, n) is asked after every outer iteration with the per-RHS residual
@@ -548,6 +583,7 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
     std::vector<double> target(n), rel(n, 0.0), relest(n, 0.0), cur_res(n, 0.0), inner_rel(n, 0.0);
     mg.vcycles = 0;
     int outer = 0, inner_total = 0;
+    clear_all_wait_flags(mg, s);
     norm2(MRHS_FP64, b, rows, n, mg.obn2.as<double>(), mg.osc, s);
     MRHS_CUDA(cudaMemcpyAsync(hbn2, mg.obn2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
     MRHS_CUDA(cudaStreamSynchronize(s));
@@ -631,20 +667,7 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
         krylov_solve(mg.oks, steps, n, s);
         lincomb(MRHS_FP64, x, MRHS_FP32, Z0, F, steps, mg.oks.y.as<double2>(), 1.0, rows, n, s);
     }
-    for (int l = 0; l + 1 < mg.nlev; ++l) {
-        if (intergrid_tc_error(mg.lev[l])) {
-            MRHS_CUDA(cudaMemsetAsync(mg.lev[l].IgErr.ptr, 0, sizeof(int), s));
-            MRHS_CUDA(cudaStreamSynchronize(s));
-            fail(MRHS_ERR_TIMEOUT, "tensor-core restriction / prolongation gave up waiting");
-        }
-    }
-    for (int l = 1; l < mg.nlev; ++l) {
-        if (coarse_tc_error(mg.lev[l])) {
-            MRHS_CUDA(cudaMemsetAsync(mg.lev[l].TcErr.ptr, 0, sizeof(int), s));
-            MRHS_CUDA(cudaStreamSynchronize(s));
-            fail(MRHS_ERR_TIMEOUT, "tensor-core coarse stencil gave up waiting for its operands");
-        }
-    }
+    check_all_wait_flags(mg, s);
     if (rel_out)
         for (int r = 0; r < n; ++r) rel_out[r] = rel[r];
     if (st) {
@@ -864,10 +887,11 @@ mrhs_status mrhs_restrict(mrhs_mg *mg, int level, const void *fine_dev, void *co
     DevGuard dg(mg->lat->device);
     const Level &C = mg->lev[level + 1];
     const Level &F = mg->lev[level];
-    if (F.tc_intergrid)
+    if (F.tc_intergrid) {
         restrict_fields_tc(F, C, static_cast<const float2 *>(fine_dev), static_cast<float2 *>(coarse_dev), nrhs,
                            (int64_t)C.dof * nrhs, false, static_cast<cudaStream_t>(stream));
-    else
+        check_wait_flags(F, static_cast<cudaStream_t>(stream));
+    } else
         restrict_fields(F, C, static_cast<const float2 *>(fine_dev), static_cast<float2 *>(coarse_dev), nrhs,
                         (int64_t)C.dof * nrhs, static_cast<cudaStream_t>(stream));
     return ok();
@@ -880,10 +904,11 @@ mrhs_status mrhs_prolong(mrhs_mg *mg, int level, const void *coarse_dev, void *f
     check_n(mg, nrhs);
     if (!fine_dev || !coarse_dev) fail(MRHS_ERR_INVALID, "fields must be non-null");
     DevGuard dg(mg->lat->device);
-    if (mg->lev[level].tc_intergrid)
+    if (mg->lev[level].tc_intergrid) {
         prolong_fields_tc(mg->lev[level], mg->lev[level + 1], static_cast<const float2 *>(coarse_dev),
                           static_cast<float2 *>(fine_dev), nrhs, static_cast<cudaStream_t>(stream));
-    else
+        check_wait_flags(mg->lev[level], static_cast<cudaStream_t>(stream));
+    } else
         prolong_fields(mg->lev[level], mg->lev[level + 1], static_cast<const float2 *>(coarse_dev),
                        static_cast<float2 *>(fine_dev), nrhs, static_cast<cudaStream_t>(stream));
     return ok();
@@ -905,6 +930,7 @@ mrhs_status mrhs_coarse_apply(mrhs_mg *mg, int level, const void *in_dev, void *
         if (!C.Abf.ptr || C.tc_fmt != links_prec)
             fail(MRHS_ERR_INVALID, "no 16-bit links of this format on this level (needs nc = 64 and that coarse_precision)");
         coarse_apply_bf16(C, static_cast<const float2 *>(in_dev), static_cast<float2 *>(out_dev), nullptr, nrhs, s);
+        check_wait_flags(C, s);
     } else {
         fail(MRHS_ERR_INVALID, "links precision must be FP32 or BF16");
     }
@@ -920,6 +946,7 @@ mrhs_status mrhs_vcycle(mrhs_mg *mg, const void *v_dev, void *z_dev, int nrhs, v
     DevGuard dg(mg->lat->device);
     vcycle(*mg, 0, static_cast<const float2 *>(v_dev), static_cast<float2 *>(z_dev), nrhs,
            static_cast<cudaStream_t>(stream), false);
+    check_all_wait_flags(*mg, static_cast<cudaStream_t>(stream));
     return ok();
     API_CATCH
 }

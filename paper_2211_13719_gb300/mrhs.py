@@ -150,6 +150,7 @@ PROTOTYPES = {
     "mrhs_prolong": (_I, [_P, _I, _P, _P, _I, _P]),
     "mrhs_coarse_apply": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "mrhs_vcycle": (_I, [_P, _P, _P, _I, _P]),
+    "mrhs_debug_expire_waits": (_I, [_I]),
     "mrhs_solve": (_I, [_P, _P, _P, _I, _D, _P, C.POINTER(SolveStats), _P]),
     "mrhs_server_create": (_I, [C.POINTER(ServerParams), C.POINTER(_P)]),
     "mrhs_server_add_config": (_I, [_P, _P, _I, C.POINTER(C.c_int)]),
@@ -365,6 +366,10 @@ def mrhs_coarse_apply(mg, level, in_dev, out_dev, nrhs, links_prec=MRHS_FP32, st
 
 def mrhs_vcycle(mg, v_dev, z_dev, nrhs, stream=None):
     _check(lib().mrhs_vcycle(mg, _ptr(v_dev), _ptr(z_dev), int(nrhs), _stream(stream)))
+
+
+def mrhs_debug_expire_waits(launches):
+    _check(lib().mrhs_debug_expire_waits(int(launches)))
 
 
 def mrhs_solve(mg, b_dev, x_dev, nrhs, tol, rel_res_host=None, stream=None, allow_not_converged=False):

@@ -47,6 +47,8 @@ def test_argument_validation_without_gpu(lib):
     assert lib.mrhs_apply_D(None, None, None, 1, 0, None) == mrhs.MRHS_ERR_INVALID
     assert lib.mrhs_blas_norm2(None, 10, 1, 0, None, None) == mrhs.MRHS_ERR_INVALID
     assert lib.mrhs_setup_mg(None, None, ctypes.byref(out)) == mrhs.MRHS_ERR_INVALID
+    assert lib.mrhs_debug_expire_waits(-1) == mrhs.MRHS_ERR_INVALID
+    assert lib.mrhs_debug_expire_waits(0) == mrhs.MRHS_OK
 
 
 def test_default_params_are_sane(lib):
