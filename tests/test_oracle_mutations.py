@@ -7,6 +7,7 @@ Nothing on disk changes.
 """
 import importlib.util
 import os
+import sys
 
 import numpy as np
 import pytest
@@ -22,9 +23,12 @@ def _mutant(modname, old, new):
     src = open(path).read()
     assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
     src = src.replace(old, new, 1)
-    spec = importlib.util.spec_from_loader(f"oracle._mutant_{modname}", loader=None)
+    name = f"oracle._mutant_{modname}"
+    spec = importlib.util.spec_from_loader(name, loader=None)
     mod = importlib.util.module_from_spec(spec)
     mod.__package__ = "oracle"
+    # registered so that dataclasses defined in the mutant can resolve their module
+    sys.modules[name] = mod
     exec(compile(src, path, "exec"), mod.__dict__)
     return mod
 
@@ -129,3 +133,53 @@ def test_coarse_pins_catch_planted_mistakes(old, new):
     assert _galerkin_error(coarse, wilson) < 1e-11
     mutant = _mutant("coarse", old, new)
     assert _galerkin_error(mutant, wilson) > 1e-6
+
+
+def _pin_or_inf(fn, mod):
+    """A mutant that makes the oracle raise (e.g. a shape mismatch) is caught too."""
+    try:
+        return fn(mod)
+    except (ValueError, IndexError):
+        return float("inf")
+
+
+def _mg_pins():
+    from tests import test_oracle_vcycle as tv
+    return {
+        "two_level": tv.two_level_error,
+        "evenodd": lambda m: tv.two_level_error(m, evenodd_smoother=True),
+        "three_level": tv.three_level_error,
+        "identity": tv.identity_prolongator_error,
+        "setup_cycle": tv.setup_cycle_error,
+        "hierarchy_setup": tv.hierarchy_setup_error,
+    }
+
+
+MG_MUTANTS = [
+    # (old, new, pin): the V-cycle and the setup of oracle/mg.py
+    ("z0 = coarse.prolong(lev.P, e, lev.dims, lev.block)",
+     "z0 = 0 * coarse.prolong(lev.P, e, lev.dims, lev.block)", "two_level"),          # dropped coarse correction
+    ("return krylov.gmres(lev.apply, v, z0, params.smooth_m, 1)",
+     "return z0 + krylov.gmres(lev.apply, v, 0 * z0, params.smooth_m, 1)", "two_level"),  # smoothing from 0
+    ("z0 = coarse.prolong(lev.P, e, lev.dims, lev.block)",
+     "z0 = coarse.prolong(np.conj(lev.P), e, lev.dims, lev.block)", "identity"),     # prolongation with conj(P)
+    ("c = coarse.restrict(lev.P, v, lev.dims, lev.block)",
+     "c = coarse.restrict(levels[0].P, v, levels[0].dims, levels[0].block)", "three_level"),  # wrong level's P
+    ("lambda u: vcycle(levels, l + 1, u, params)", "lambda u: u", "three_level"),    # no intermediate V-cycle
+    ("return z0 + evenodd_smooth(lev, v - lev.apply(z0), params.smooth_m)",
+     "return z0 + evenodd_smooth(lev, v, params.smooth_m)", "evenodd"),              # stale residual
+    ("v = krylov.gmres(apply_A, zero, v, m, 1)",
+     "v = krylov.gmres(apply_A, v, v, m, 1)", "setup_cycle"),                        # relaxes A v = v
+    ("vecs = setup_nullvecs(lev.apply, init_vecs[l]",
+     "vecs = setup_nullvecs(lambda f: lev.apply(f) - np.einsum('vij,vjn->vin', clover, f), init_vecs[l]",
+     "hierarchy_setup"),                                                             # D without the clover
+]
+
+
+@pytest.mark.parametrize("old,new,pin", MG_MUTANTS)
+def test_mg_pins_catch_planted_mistakes(old, new, pin):
+    from oracle import mg
+    fn = _mg_pins()[pin]
+    assert fn(mg) < 1e-9
+    mutant = _mutant("mg", old, new)
+    assert _pin_or_inf(fn, mutant) > 1e-6
