@@ -5,8 +5,10 @@ no setup relaxation, so both build the prolongator from the same vectors:
 * prolongator (FP64 block Gram-Schmidt) to 1e-12,
 * Galerkin links (FP32 on the GPU) to 2e-6 relative per stencil block,
 * restriction / prolongation (FP32) to 2e-6 relative per site,
-* coarse stencil (FP32 links, FP32 fields) to 1e-5 relative per site,
-  on coarse extents 2 and 1 where +mu and -mu neighbours coincide,
+* coarse stencil (FP32 links, FP32 fields) to 1e-6 relative per site
+  against the oracle's FP64 stencil on the same (GPU-built FP32) links, so
+  that only the stencil's own rounding is measured, on coarse extents 2 and
+  1 where +mu and -mu neighbours coincide,
 * the second-level Galerkin of a three-level hierarchy,
 * the V-cycle (fixed-iteration Krylov pieces) against the oracle's V-cycle.
 """
@@ -74,11 +76,11 @@ def test_two_level_rows(dims, blocks, nvec):
         mrhs.mrhs_prolong(mg, 0, to_dev(cin), d_f, n)
         f_ref = coarse.prolong(Po, cin.astype(np.complex128), dims, blocks[0])
         assert site_rel_err(to_host(d_f).astype(np.complex128), f_ref) < 2e-6
-        # coarse stencil
+        # coarse stencil: the oracle's stencil on the GPU's own FP32 links
         d_o = to_dev(np.full((Vc, nc, n), np.nan, np.complex64))
         mrhs.mrhs_coarse_apply(mg, 1, to_dev(cin), d_o, n, mrhs.MRHS_FP32)
-        o_ref = coarse.apply_coarse(Ao, cin.astype(np.complex128), cd)
-        assert site_rel_err(to_host(d_o).astype(np.complex128), o_ref) < 1e-5
+        o_ref = coarse.apply_coarse(Ag, cin.astype(np.complex128), cd)
+        assert site_rel_err(to_host(d_o).astype(np.complex128), o_ref) < 1e-6
     finally:
         mrhs.mrhs_destroy_mg(mg)
         mrhs.mrhs_destroy_lattice(lat)
