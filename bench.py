@@ -216,6 +216,104 @@ def oracle_in_subprocess(steps=1, warmup=0):
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
+# ------------------------------------------------------- oracle timing table
+# The CPU baseline items: the oracle (plain numpy, FP64) timed on the host
+# cores.  Fine apply on the 24^4 Haar lattice (c_sw = 1, m = -0.2); coarse
+# 9-point apply on 6^4 with nc = 64 (random links of the Galerkin shape: the
+# values do not change the work); the small plain solve (8^4, eps 0.4,
+# m = -0.2, 4 RHS, 2 levels, 4^4 aggregates, 8 null vectors); and one RHS of
+# the benchmarked 3-level / 32-vector structure on 8^4, the smallest lattice
+# its 4^4 and 2^4 aggregations divide (setup reported separately).
+def oracle_table_items(which=None):
+    import numpy as np
+
+    import synth
+    from oracle import coarse as oc, mg as omg, wilson as ow
+    out = {}
+
+    def timed(fn, reps=1):
+        fn()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        return (time.perf_counter() - t0) / reps
+
+    if which in (None, "fine"):
+        dims = (24, 24, 24, 24)
+        U = synth.gauge_haar(dims, 1101)
+        C = ow.clover_term(U, dims, 1.0)
+        V = volume(dims)
+        for n in (1, 12, 64):
+            psi = synth.gaussian_field(V, 12, n, 2101)
+            t = timed(lambda: ow.apply_D(U, C, psi, dims, -0.2))
+            out[f"fine_apply_24^4_n{n}_s"] = t
+            out[f"fine_apply_24^4_n{n}_GBs"] = V * (576 + 192 * n) / t / 1e9
+            del psi
+        del U, C
+    if which in (None, "coarse"):
+        cd = (6, 6, 6, 6)
+        Vc = volume(cd)
+        rng = np.random.default_rng(1201)
+        A = (rng.standard_normal((Vc, 9, 64, 64)) + 1j * rng.standard_normal((Vc, 9, 64, 64))) / 64
+        for n in (12, 48):
+            phi = synth.gaussian_field(Vc, 64, n, 2201)
+            t = timed(lambda: oc.apply_coarse(A, phi, cd), reps=2)
+            out[f"coarse_apply_6^4_nc64_n{n}_s"] = t
+        del A
+    if which in (None, "c0"):
+        dims = (8, 8, 8, 8)
+        U = synth.gauge_exp(dims, 0.4, 1001)
+        p = omg.MGParams(blocks=[(4, 4, 4, 4)], nvec=[8], setup_sweeps=4, setup_m=8, smooth_m=4, coarse_m=16,
+                         coarse_cycles=2, outer_m=8, tol=1e-10)
+        t0 = time.perf_counter()
+        levels = omg.build_hierarchy(U, dims, -0.2, 1.0, p, [synth.gaussian_field(volume(dims), 12, 8, 7)])
+        out["c0_setup_s"] = time.perf_counter() - t0
+        b = synth.gaussian_field(volume(dims), 12, 4, 2001)
+        t0 = time.perf_counter()
+        x, hist = omg.solve(levels, b, p)
+        out["c0_solve_4rhs_s"] = time.perf_counter() - t0
+        out["c0_outer_cycles"] = len(hist) - 1
+        out["c0_max_rel_residual"] = float(np.max(hist[-1]))
+    if which in (None, "c3"):
+        w = WORKLOAD
+        dims = (8, 8, 8, 8)
+        U = synth.gauge_exp(dims, w["eps"], w["gauge_seed"])
+        d1 = tuple(L // 4 for L in dims)
+        p = omg.MGParams(blocks=w["blocks"], nvec=w["nvec"], setup_sweeps=MG_PARAMS["setup_sweeps"],
+                         setup_m=MG_PARAMS["setup_m"], smooth_m=MG_PARAMS["smooth_m"],
+                         coarse_m=MG_PARAMS["coarse_m"], coarse_cycles=1, inter_m=MG_PARAMS["inter_m"],
+                         outer_m=MG_PARAMS["inner_m"], tol=w["tol"], smoother_evenodd=True)
+        t0 = time.perf_counter()
+        levels = omg.build_hierarchy(U, dims, w["mass"], w["csw"], p,
+                                     [synth.gaussian_field(volume(dims), 12, 32, 7),
+                                      synth.gaussian_field(volume(d1), 64, 32, 8)])
+        out["c3_structure_8^4_setup_s"] = time.perf_counter() - t0
+        b = synth.gaussian_field(volume(dims), 12, 1, w["source_seed"])
+        t0 = time.perf_counter()
+        x, hist = omg.solve(levels, b, p)
+        t = time.perf_counter() - t0
+        out["c3_structure_8^4_solve_1rhs_s"] = t
+        out["c3_structure_8^4_outer_cycles"] = len(hist) - 1
+        out["c3_per_rhs_scaled_to_24^3x64_s"] = t * volume(w["dims"]) / volume(dims)
+    return out
+
+
+def oracle_table(threads):
+    """Run oracle_table_items in a fresh process with `threads` BLAS / OpenMP threads."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads), CUDA_VISIBLE_DEVICES="")
+    res = {"threads": threads, "nproc": os.cpu_count()}
+    for item in ("fine", "coarse", "c0", "c3"):
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench.oracle_table_items(%r)))" % (ROOT, item))
+        p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=7200)
+        if p.returncode != 0:
+            res[item] = "failed: " + (p.stderr.strip().splitlines() or ["?"])[-1]
+        else:
+            res.update(json.loads(p.stdout.strip().splitlines()[-1]))
+    return res
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -626,6 +724,8 @@ def run_case(name, reps, args=None):
                                                                   mrhs.MRHS_FP32))
         out["GBs_lincomb_k4"] = (k + 2) * rows * n * 8 / out["ms_lincomb_k4"] / 1e6
         return print(json.dumps(out), flush=True)
+    if name == "coarse":
+        return print(json.dumps(run_coarse_case(mrhs, torch, reps)), flush=True)
     dims = (24, 24, 24, 24) if name in ("stencil", "schur", "stencil-sweep") else (16, 16, 16, 16)
     V = volume(dims)
     U = synth.gauge_exp(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
@@ -682,6 +782,100 @@ def run_case(name, reps, args=None):
     print(json.dumps(out), flush=True)
 
 
+def run_coarse_case(mrhs, torch, reps):
+    """Coarse level and intergrid operators on 24^4 (Haar gauge) with 4^4 aggregates and 32 null
+    vectors: the 6^4 coarse lattice with nc = 64.  Per nRHS in {12, 24, 48}: the coarse stencil with FP32
+    links on CUDA cores and with FP16 / BF16 links on the tensor cores (the kernel alone and the whole
+    apply including the input's scale and packing passes), restriction and prolongation, and the batched
+    multi-dot over 4 coarse vectors.  Algorithmic bytes per coarse site: links 9 x 64 x 64 complex
+    (294,912 B FP32, 147,456 B 16-bit) plus the input and output vectors 2 x 64 x n x 8 B; per fine site
+    for the transfers: P (32 vectors x 12 complex, 3072 B FP32 / 1536 B 16-bit) and the fine vector 96 n B."""
+    import numpy as np
+
+    import synth
+    peak, kind = read_peaks()
+    dims, block, N = (24, 24, 24, 24), (4, 4, 4, 4), 32
+    V = volume(dims)
+    U = synth.gauge_haar(dims, 1201)
+    lat = mrhs.mrhs_create_lattice(dims, -1, torch.cuda.current_device())
+    mrhs.mrhs_load_gauge(lat, U)
+    mrhs.mrhs_build_clover(lat, -0.2, 1.0)
+    vecs = np.ascontiguousarray(synth.gaussian_field(V, 12, N, 3201))
+    stream = torch.cuda.current_stream()
+    out = {"case": "coarse", "dims": list(dims), "coarse_dims": [6, 6, 6, 6], "nc": 64, "peak_GBs": peak,
+           "peak_source": kind, "rows": []}
+    Vc = V // 256
+
+    def ev(fn):
+        for _ in range(3):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def kernel_ms(name, fn):
+        mrhs.mrhs_kernel_timer_start(name)
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        ms, cnt, _ = mrhs.mrhs_kernel_timer_stop()
+        return ms / max(cnt, 1)
+
+    mgs = {}
+    for prec in (mrhs.MRHS_FP16, mrhs.MRHS_BF16):
+        p = mrhs.mrhs_mg_default_params()
+        p.n_levels = 2
+        for mu in range(4):
+            p.block[0][mu] = block[mu]
+        p.n_vec[0] = N
+        p.setup_sweeps = 0
+        p.max_rhs = 48
+        p.coarse_precision = prec
+        p.use_graph = 0
+        p.init_vecs[0] = vecs.ctypes.data
+        mgs[prec] = mrhs.mrhs_setup_mg(lat, p)
+    names = {mrhs.MRHS_FP32: "fp32", mrhs.MRHS_FP16: "fp16", mrhs.MRHS_BF16: "bf16"}
+    for n in (12, 24, 48):
+        phi = torch.randn((Vc, 64, n), dtype=torch.complex64, device="cuda")
+        o = torch.empty_like(phi)
+        row = {"nrhs": n}
+        vec_b = 2 * 64 * n * 8
+        for prec in (mrhs.MRHS_FP32, mrhs.MRHS_FP16, mrhs.MRHS_BF16):
+            mg = mgs[mrhs.MRHS_BF16 if prec == mrhs.MRHS_BF16 else mrhs.MRHS_FP16]
+            fn = lambda: mrhs.mrhs_coarse_apply(mg, 1, phi, o, n, prec, stream)  # noqa: E731
+            ms_apply = ev(fn)
+            link_b = 294912 if prec == mrhs.MRHS_FP32 else 147456
+            alg = Vc * (link_b + vec_b)
+            k = "k_coarse_fp32" if prec == mrhs.MRHS_FP32 else "k_coarse_tc"
+            ms_k = kernel_ms(k, fn)
+            row[names[prec]] = {"ms_apply": ms_apply, "ms_kernel": ms_k, "kernel": k,
+                                "alg_bytes": alg, "alg_GBs_kernel": alg / ms_k / 1e6,
+                                "frac_kernel": alg / ms_k / 1e6 / peak, "alg_GBs_apply": alg / ms_apply / 1e6,
+                                "tflops_kernel": Vc * 9 * 64 * 64 * n * 8 / ms_k / 1e9}
+        f = torch.randn((V, 12, n), dtype=torch.complex64, device="cuda")
+        mg = mgs[mrhs.MRHS_FP16]
+        ms_r = ev(lambda: mrhs.mrhs_restrict(mg, 0, f, phi, n, stream))
+        ms_p = ev(lambda: mrhs.mrhs_prolong(mg, 0, phi, f, n, stream))
+        tb = V * (1536 + 96 * n) + Vc * 64 * n * 8
+        row["restrict_tc"] = {"ms": ms_r, "alg_GBs": tb / ms_r / 1e6, "frac": tb / ms_r / 1e6 / peak}
+        row["prolong_tc"] = {"ms": ms_p, "alg_GBs": tb / ms_p / 1e6, "frac": tb / ms_p / 1e6 / peak}
+        basis = torch.randn((5, Vc * 64, n), dtype=torch.complex64, device="cuda")
+        h = torch.empty((4, n), dtype=torch.complex128, device="cuda")
+        ms_d = ev(lambda: mrhs.mrhs_blas_multi_dot(basis, 4, basis[4], Vc * 64, n, mrhs.MRHS_FP32, h, stream))
+        row["multi_dot_k4"] = {"ms": ms_d, "alg_GBs": 5 * Vc * 64 * n * 8 / ms_d / 1e6}
+        out["rows"].append(row)
+        del phi, o, f, basis
+    for mg in mgs.values():
+        mrhs.mrhs_destroy_mg(mg)
+    mrhs.mrhs_destroy_lattice(lat)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -698,12 +892,17 @@ def main():
                     help="fine post-smoother: GMRES on the even-odd Schur complement (default), SAP, or GMRES on D")
     ap.add_argument("--sap-mr", type=int, default=4)
     ap.add_argument("--sap-cycles", type=int, default=1)
-    ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas"],
+    ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas",
+                                                     "coarse", "oracle-table"],
                     help="run a small profiling case of one kernel family instead of the benchmark")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--blas-rows", type=int, default=16 ** 4 * 12,
                     help="rows of the blas case (221184: the intermediate level, 3456 sites x 64 dof)")
     args = ap.parse_args()
+    if args.case == "oracle-table":
+        for th in sorted({1, os.cpu_count() or 1}):
+            print(json.dumps(oracle_table(th)), flush=True)
+        return
     if args.case:
         run_case(args.case, args.case_reps, args)
         return

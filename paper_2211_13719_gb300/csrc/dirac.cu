@@ -256,8 +256,75 @@ struct KArgs32 {
     int tb;
     int T[4];     // tile extents (each divides L)
     int NT[3];    // tiles along x, y, z
-    int tsites;   // T[0] * T[1] * T[2] * T[3]
+    int tsites;   // sites per tile (mode 0) or per region (mode 1)
+    // visit order: 0 = tiles of T, tiles x-fastest; 1 = x-regions of RX sites
+    // (whole y, z, t extents), lexicographic inside a region (x fastest, t
+    // slowest); 2 = RHS slabs of GS pairs, each slab a lexicographic sweep of
+    // the whole lattice (t slowest).  Modes 1 and 2 keep the L2 window of a
+    // sweep at about two t-layers of the region or slab.
+    int mode;
+    int RX;
+    int GS;
 };
+
+// Coordinates of the site a thread visits and its first RHS (r0) under the
+// visit order of `a`; false for threads past the end.  `xpair`: the site
+// index counts x pairs (one output site of a given parity per pair, even-odd
+// kernels), the member of the pair is chosen by the caller.
+__device__ __forceinline__ bool visit_coords(const KArgs32 &a, int item, int nvisit, bool xpair, int c[4],
+                                             int &r0) {
+    int visit;
+    if (a.mode == 2) {
+        const int per_slab = nvisit * a.GS;
+        const int slab = item / per_slab;
+        const int rem = item - slab * per_slab;
+        visit = rem / a.GS;
+        if (slab * a.GS >= a.G) return false;
+        r0 = (slab * a.GS + rem - visit * a.GS) * 2;
+    } else {
+        visit = item / a.G;
+        if (visit >= nvisit) return false;
+        r0 = (item - visit * a.G) * 2;
+    }
+    const int X = xpair ? a.L[0] / 2 : a.L[0];
+    if (a.mode == 2) {
+        int q = visit;
+        c[0] = q % X;
+        q /= X;
+        c[1] = q % a.L[1];
+        q /= a.L[1];
+        c[2] = q % a.L[2];
+        c[3] = q / a.L[2];
+    } else if (a.mode == 1) {
+        const int RX = xpair ? a.RX / 2 : a.RX;
+        const int reg = visit / a.tsites;
+        int q = visit - reg * a.tsites;
+        c[0] = reg * RX + q % RX;
+        q /= RX;
+        c[1] = q % a.L[1];
+        q /= a.L[1];
+        c[2] = q % a.L[2];
+        c[3] = q / a.L[2];
+    } else {
+        const int tile = visit / a.tsites;
+        int q = visit - tile * a.tsites;
+        int tq = tile;
+        const int t0 = tq % a.NT[0];
+        tq /= a.NT[0];
+        const int t1 = tq % a.NT[1];
+        tq /= a.NT[1];
+        const int t2 = tq % a.NT[2];
+        const int t3 = tq / a.NT[2];
+        const int T0 = xpair ? 1 : a.T[0];
+        c[0] = t0 * T0 + q % T0;
+        q /= T0;
+        c[1] = t1 * a.T[1] + q % a.T[1];
+        q /= a.T[1];
+        c[2] = t2 * a.T[2] + q % a.T[2];
+        c[3] = t3 * a.T[3] + q / a.T[2];
+    }
+    return true;
+}
 
 // N: the RHS count as a compile-time constant (0: a.n at run time), so that
 // the 12 component loads of a neighbour are immediate offsets from one
@@ -339,27 +406,8 @@ __global__ void __launch_bounds__(128, 3) k_dslash_x2(const float2 *__restrict__
                                                        const float2 *__restrict__ in, float2 *__restrict__ out,
                                                        const float2 *__restrict__ y, KArgs32 a) {
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    const int visit = item / a.G;
-    if (visit >= a.V) return;
-    const int r0 = (item - visit * a.G) * 2;
-    int c[4];
-    {
-        const int tile = visit / a.tsites;
-        int q = visit - tile * a.tsites;
-        int tq = tile;
-        const int t0 = tq % a.NT[0];
-        tq /= a.NT[0];
-        const int t1 = tq % a.NT[1];
-        tq /= a.NT[1];
-        const int t2 = tq % a.NT[2];
-        const int t3 = tq / a.NT[2];
-        c[0] = t0 * a.T[0] + q % a.T[0];
-        q /= a.T[0];
-        c[1] = t1 * a.T[1] + q % a.T[1];
-        q /= a.T[1];
-        c[2] = t2 * a.T[2] + q % a.T[2];
-        c[3] = t3 * a.T[3] + q / a.T[2];
-    }
+    int c[4], r0;
+    if (!visit_coords(a, item, a.V, false, c, r0)) return;
     const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
     P2 acc[12];
 #pragma unroll
@@ -414,7 +462,31 @@ static KArgs32 x2_args(const mrhs_lattice &lat, int n, const int pref[4]) {
         a.tsites *= t;
     }
     for (int mu = 0; mu < 3; ++mu) a.NT[mu] = a.L[mu] / a.T[mu];
+    a.mode = 0;
+    a.RX = a.L[0];
+    a.GS = a.G;
     return a;
+}
+
+// the traversal variants beyond the tiles: x-regions (nr regions, nr dividing
+// L[0]; `xstep` 2 for the even-odd kernels, whose regions hold whole x pairs)
+// and RHS slabs (ns slabs of G / ns pairs)
+static void add_order_variants(std::vector<KArgs32> &v, const KArgs32 &base, int xstep) {
+    for (int nr : {1, 2, 3}) {
+        if (base.L[0] % (nr * xstep)) continue;
+        KArgs32 a = base;
+        a.mode = 1;
+        a.RX = a.L[0] / nr;
+        a.tsites = (a.RX / xstep) * a.L[1] * a.L[2] * a.L[3];
+        v.push_back(a);
+    }
+    for (int ns : {2, 3}) {
+        if (base.G % ns) continue;
+        KArgs32 a = base;
+        a.mode = 2;
+        a.GS = a.G / ns;
+        v.push_back(a);
+    }
 }
 
 static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n,
@@ -436,6 +508,7 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
         for (const KArgs32 &b : args) dup = dup || (b.T[0] == a.T[0] && b.T[1] == a.T[1] && b.T[2] == a.T[2] && b.T[3] == a.T[3]);
         if (!dup) args.push_back(a);
     }
+    add_order_variants(args, args[0], 1);
     const int64_t items = (int64_t)args[0].V * args[0].G;
     const int threads = 128;
     const unsigned blocks = (unsigned)((items + threads - 1) / threads);
@@ -510,30 +583,12 @@ __global__ void __launch_bounds__(128, 3) k_eo_x2(const float2 *__restrict__ U, 
                                                    float2 *__restrict__ out, KArgsEO e) {
     const KArgs32 &a = e.k;
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    const int visit = item / a.G;
-    if (visit >= e.V2) return;
-    const int r0 = (item - visit * a.G) * 2;
-    // visit order: tiles of 2 x T[1] x T[2] x T[3] sites (one output site per x
-    // pair), tiles x-fastest, as the full stencil's tile order; x = 2k or 2k + 1
-    // is the member of the pair with the output parity
-    int c[4];
-    {
-        const int tile = visit / a.tsites;
-        int q = visit - tile * a.tsites;
-        int tq = tile;
-        const int t0 = tq % a.NT[0];
-        tq /= a.NT[0];
-        const int t1 = tq % a.NT[1];
-        tq /= a.NT[1];
-        const int t2 = tq % a.NT[2];
-        const int t3 = tq / a.NT[2];
-        c[1] = t1 * a.T[1] + q % a.T[1];
-        q /= a.T[1];
-        c[2] = t2 * a.T[2] + q % a.T[2];
-        c[3] = t3 * a.T[3] + q / a.T[2];
-        c[0] = 2 * t0;
-        if (((c[0] + c[1] + c[2] + c[3]) & 1) != e.parity) ++c[0];
-    }
+    // visit order over x pairs (one output site per pair) as the full stencil's
+    // orders; x = 2k or 2k + 1 is the member of the pair with the output parity
+    int c[4], r0;
+    if (!visit_coords(a, item, e.V2, true, c, r0)) return;
+    c[0] *= 2;
+    if (((c[0] + c[1] + c[2] + c[3]) & 1) != e.parity) ++c[0];
     const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
     const int cb = site >> 1;
     P2 acc[12];
@@ -630,6 +685,10 @@ static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity, const int pre
         a.tsites *= t;
     }
     for (int mu = 0; mu < 3; ++mu) a.NT[mu] = a.L[mu] / a.T[mu];
+    a.NT[0] = a.L[0] / 2;
+    a.mode = 0;
+    a.RX = a.L[0];
+    a.GS = a.G;
     e.parity = parity;
     e.V2 = a.V / 2;
     return e;
@@ -655,6 +714,15 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
         bool dup = false;
         for (const KArgsEO &b : args) dup = dup || (b.k.T[1] == e.k.T[1] && b.k.T[2] == e.k.T[2] && b.k.T[3] == e.k.T[3]);
         if (!dup) args.push_back(e);
+    }
+    {
+        std::vector<KArgs32> orders;
+        add_order_variants(orders, args[0].k, 2);
+        for (const KArgs32 &k : orders) {
+            KArgsEO e = args[0];
+            e.k = k;
+            args.push_back(e);
+        }
     }
     const int64_t items = (int64_t)args[0].V2 * args[0].k.G;
     const unsigned blocks = (unsigned)((items + 127) / 128);

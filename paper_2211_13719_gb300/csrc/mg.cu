@@ -340,6 +340,7 @@ void coarse_apply_fp32(const Level &c, const float2 *in, float2 *out, const floa
     }
     StencilMask m{1, -1, 0, {1, 1, 1, 1}};
     if (mask) m = *mask;
+    MRHS_TIMED("k_coarse_fp32", s);
     k_coarse_fp32<<<(unsigned)c.V, T, smem, s>>>(c.A32.as<float2>(), in, out, y, a, m, mask ? 1 : 0);
     MRHS_LAUNCHED("k_coarse_fp32");
 }

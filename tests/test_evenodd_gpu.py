@@ -88,8 +88,8 @@ def test_full_size_hop_matches_the_full_stencil():
         h_e = torch.empty_like(psi_o)
         mrhs.mrhs_apply_hop_eo(lat, 0, psi_o, h_e, n)
         torch.cuda.synchronize()
-        ref = d_full[even].double()
-        got = (-0.5 * h_e).double()
+        ref = d_full[even].to(torch.complex128)
+        got = (-0.5 * h_e).to(torch.complex128)
         err = ((got - ref).abs().pow(2).sum(dim=1) / ref.abs().pow(2).sum(dim=1)).sqrt().max().item()
     finally:
         mrhs.mrhs_destroy_lattice(lat)
