@@ -395,11 +395,19 @@ typedef struct {
 mrhs_status mrhs_server_create(const mrhs_server_params *params, mrhs_server **out);
 /* Make a resident hierarchy servable with `slots` RHS slots (<= max_rhs of
  * its params); its Krylov workspace is sized for `slots`.  Admission fails
- * with MRHS_ERR_OOM if free HBM minus the reserve cannot hold it. */
+ * with MRHS_ERR_OOM if free HBM minus the reserve cannot hold the slot
+ * block (two FP64 fields of `slots` columns). */
 mrhs_status mrhs_server_add_config(mrhs_server *srv, mrhs_mg *mg, int slots, int *config_id);
 /* Queue nrhs sources b_host ([V][12][nrhs] FP64, copied before return);
  * x_host receives the solutions and must stay valid until mrhs_poll
- * reports completion. */
+ * reports completion.  Requests are admitted to free slots in FIFO order
+ * per config, and each only when its device staging (V * 12 * nrhs FP64
+ * complex, held until it completes) fits into free HBM above the reserve
+ * (cudaMemGetInfo at admission); otherwise it waits for running requests
+ * to release theirs.  MRHS_ERR_OOM at submit if the staging exceeds the
+ * device's memory above the reserve; a request that still cannot be
+ * staged while no other request holds staging completes with
+ * MRHS_ERR_OOM. */
 mrhs_status mrhs_submit(mrhs_server *srv, int config_id, const double *b_host, double *x_host,
                         int nrhs, double tol, uint64_t *req_id);
 /* MRHS_PENDING while queued or running, MRHS_OK when x_host is written,
@@ -407,6 +415,12 @@ mrhs_status mrhs_submit(mrhs_server *srv, int config_id, const double *b_host, d
 mrhs_status mrhs_poll(mrhs_server *srv, uint64_t req_id, mrhs_request_stats *stats);
 /* Block until every submitted request has completed. */
 mrhs_status mrhs_server_drain(mrhs_server *srv);
+/* Change the HBM the server keeps free when it admits requests (GB, >= 0);
+ * takes effect at the next admission. */
+mrhs_status mrhs_server_set_reserve(mrhs_server *srv, double hbm_reserve_gb);
+/* Admissions deferred or refused so far because free HBM above the reserve
+ * could not hold a request's staging. */
+mrhs_status mrhs_server_memory_waits(mrhs_server *srv, uint64_t *count);
 void mrhs_server_destroy(mrhs_server *srv);
 
 #ifdef __cplusplus

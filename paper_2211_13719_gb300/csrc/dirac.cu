@@ -470,8 +470,9 @@ static KArgs32 x2_args(const mrhs_lattice &lat, int n, const int pref[4]) {
 
 // the traversal variants beyond the tiles: x-regions (nr regions, nr dividing
 // L[0]; `xstep` 2 for the even-odd kernels, whose regions hold whole x pairs)
-// and RHS slabs (ns slabs of G / ns pairs)
-static void add_order_variants(std::vector<KArgs32> &v, const KArgs32 &base, int xstep) {
+// and RHS slabs (ns slabs of G / ns pairs).  `base` is taken by value: it may
+// be an element of `v`, which the push_back below can reallocate.
+static void add_order_variants(std::vector<KArgs32> &v, const KArgs32 base, int xstep) {
     for (int nr : {1, 2, 3}) {
         if (base.L[0] % (nr * xstep)) continue;
         KArgs32 a = base;

@@ -3,8 +3,12 @@
 // Each resident hierarchy (config) owns a fixed block of `slots` RHS columns
 // on the device and one worker thread with its own CUDA stream, so the
 // solves of different configs overlap on the GPU.  A worker repeatedly
-//   1. admits queued requests (FIFO) whose columns fit into free slots:
-//      their sources are copied into the slot columns, their x set to zero;
+//   1. admits queued requests (FIFO) whose columns fit into free slots and
+//      whose device staging (its sources, later its solution columns) fits
+//      into free HBM above the server's reserve (cudaMemGetInfo at each
+//      admission; the staging is allocated then and freed when the request
+//      completes): their sources are copied into the slot columns, their x
+//      set to zero;
 //   2. runs the MG-preconditioned FP64 FGMRES on the whole slot block for at
 //      most one restart cycle (outer_m iterations), stopping early once some
 //      column has converged while requests are waiting;
@@ -70,6 +74,7 @@ struct Request {
     double tol = 0;
     std::vector<double2> b;  // host copy of the sources [rows][nrhs]
     double *x_host = nullptr;
+    DeviceBuffer dev;        // device staging [rows][nrhs] FP64, held from admission to completion
     mrhs_status state = MRHS_PENDING;
     Clock::time_point t_submit, t_admit, t_done;
     bool admitted = false;
@@ -92,7 +97,6 @@ struct Config {
     int device = 0;
     cudaStream_t stream = nullptr;
     DeviceBuffer b, x;        // FP64 [rows][slots]
-    DeviceBuffer stage;       // FP64 [rows][slots] staging for one request's columns
     DeviceBuffer slot_map;    // int [slots]
     std::vector<Slot> table;
     std::deque<uint64_t> queue;
@@ -111,6 +115,8 @@ struct mrhs_server {
     std::atomic<bool> stop{false};
     uint64_t next_id = 1;
     int outstanding = 0;
+    uint64_t mem_waits = 0;  // admissions deferred (or refused) for lack of free HBM
+    int staged = 0;          // requests holding device staging
     static constexpr int kMaxCycles = 64;  // restart cycles a column may take before failing
 };
 
@@ -120,8 +126,12 @@ void finish_request(mrhs_server &srv, Request &r, mrhs_status st, const std::str
     r.state = st;
     r.error = err;
     r.t_done = Clock::now();
+    if (r.dev.ptr) srv.staged--;
+    r.dev.release();
+    std::vector<double2>().swap(r.b);
     srv.outstanding--;
     srv.done_cv.notify_all();
+    srv.cv.notify_all();
 }
 
 void worker_loop(mrhs_server *srv, Config *cfg) {
@@ -148,11 +158,40 @@ void worker_loop(mrhs_server *srv, Config *cfg) {
                 for (int s = 0; s < S && (int)free_slots.size() < r.nrhs; ++s)
                     if (!cfg->table[s].req) free_slots.push_back(s);
                 if ((int)free_slots.size() < r.nrhs) break;  // FIFO: wait for room
+                // memory admission: the request's device staging must fit into free HBM
+                // above the reserve; otherwise it waits for running requests to free
+                // theirs, and fails only if nothing else holds memory here
+                const size_t need = sizeof(double2) * (size_t)rows * r.nrhs;
+                size_t free_b = 0, total_b = 0;
+                bool fits = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess &&
+                            (double)free_b >= (double)need + srv->p.hbm_reserve_gb * 1e9;
+                if (fits) {
+                    try {
+                        r.dev.alloc(need);
+                    } catch (const std::exception &) {
+                        (void)cudaGetLastError();
+                        fits = false;
+                    }
+                }
+                if (!fits) {
+                    srv->mem_waits++;
+                    if (srv->staged > 0) break;  // memory held by running requests will come back
+                    cfg->queue.pop_front();
+                    finish_request(*srv, r, MRHS_ERR_OOM, "not enough free HBM to stage the request");
+                    continue;
+                }
+                srv->staged++;
                 for (int c = 0; c < r.nrhs; ++c) cfg->table[free_slots[c]] = Slot{r.id, c, 0};
                 r.admitted = true;
                 r.t_admit = Clock::now();
                 admitted.emplace_back(r.id, free_slots);
                 cfg->queue.pop_front();
+            }
+            if (admitted.empty() && !busy()) {
+                // nothing runs on this config: its head request waits for slots or HBM
+                // that requests of other configs hold; look again shortly
+                srv->cv.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
             }
         }
         try {
@@ -166,10 +205,10 @@ void worker_loop(mrhs_server *srv, Config *cfg) {
                 const int k = (int)a.second.size();
                 MRHS_CUDA(cudaMemcpyAsync(cfg->slot_map.ptr, a.second.data(), sizeof(int) * k, cudaMemcpyHostToDevice,
                                           cfg->stream));
-                MRHS_CUDA(cudaMemcpyAsync(cfg->stage.ptr, rq->b.data(), sizeof(double2) * rows * k,
+                MRHS_CUDA(cudaMemcpyAsync(rq->dev.ptr, rq->b.data(), sizeof(double2) * rows * k,
                                           cudaMemcpyHostToDevice, cfg->stream));
                 k_scatter_cols<<<ceil_div(rows * k, 256), 256, 0, cfg->stream>>>(
-                    cfg->b.as<double2>(), S, cfg->stage.as<double2>(), k, cfg->slot_map.as<int>(), rows);
+                    cfg->b.as<double2>(), S, rq->dev.as<double2>(), k, cfg->slot_map.as<int>(), rows);
                 k_zero_cols<<<ceil_div(rows * k, 256), 256, 0, cfg->stream>>>(cfg->x.as<double2>(), S,
                                                                               cfg->slot_map.as<int>(), k, rows);
                 MRHS_LAUNCHED("server scatter");
@@ -226,10 +265,10 @@ void worker_loop(mrhs_server *srv, Config *cfg) {
                 MRHS_CUDA(cudaMemcpyAsync(cfg->slot_map.ptr, tc.second.data(), sizeof(int) * k, cudaMemcpyHostToDevice,
                                           cfg->stream));
                 k_gather_cols<<<ceil_div(rows * k, 256), 256, 0, cfg->stream>>>(
-                    cfg->stage.as<double2>(), k, cfg->x.as<double2>(), S, cfg->slot_map.as<int>(), rows);
+                    rq->dev.as<double2>(), k, cfg->x.as<double2>(), S, cfg->slot_map.as<int>(), rows);
                 MRHS_LAUNCHED("server gather");
                 std::vector<double2> host((size_t)rows * k);
-                MRHS_CUDA(cudaMemcpyAsync(host.data(), cfg->stage.ptr, sizeof(double2) * rows * k,
+                MRHS_CUDA(cudaMemcpyAsync(host.data(), rq->dev.ptr, sizeof(double2) * rows * k,
                                           cudaMemcpyDeviceToHost, cfg->stream));
                 MRHS_CUDA(cudaStreamSynchronize(cfg->stream));
                 std::vector<int> cols(k);
@@ -304,12 +343,11 @@ mrhs_status mrhs_server_add_config(mrhs_server *srv, mrhs_mg *mg, int slots, int
     const size_t field = sizeof(double2) * (size_t)cfg->rows * slots;
     size_t free_b = 0, total_b = 0;
     MRHS_CUDA(cudaMemGetInfo(&free_b, &total_b));
-    const double need = 3.0 * field + srv->p.hbm_reserve_gb * 1e9;
+    const double need = 2.0 * field + srv->p.hbm_reserve_gb * 1e9;
     if ((double)free_b < need)
         fail(MRHS_ERR_OOM, "not enough free HBM to admit this configuration");
     cfg->b.alloc(field);
     cfg->x.alloc(field);
-    cfg->stage.alloc(field);
     cfg->slot_map.alloc(sizeof(int) * slots);
     MRHS_CUDA(cudaMemset(cfg->b.ptr, 0, field));
     MRHS_CUDA(cudaMemset(cfg->x.ptr, 0, field));
@@ -337,6 +375,15 @@ mrhs_status mrhs_submit(mrhs_server *srv, int config_id, const double *b_host, d
     Config *cfg = srv->configs[config_id].get();
     if (nrhs < 1 || nrhs > cfg->slots) fail(MRHS_ERR_INVALID, "nrhs must be in 1..slots of the config");
     if ((int)cfg->queue.size() >= srv->p.max_queue) fail(MRHS_ERR_BUSY, "request queue full");
+    {
+        // a request whose staging cannot fit even into the whole device above the reserve never will
+        size_t free_b = 0, total_b = 0;
+        MRHS_CUDA(cudaSetDevice(cfg->device));
+        MRHS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const double need = (double)sizeof(double2) * (double)cfg->rows * nrhs;
+        if (need + srv->p.hbm_reserve_gb * 1e9 > (double)total_b)
+            fail(MRHS_ERR_OOM, "request staging exceeds the device memory above the reserve");
+    }
     Request r;
     r.id = srv->next_id++;
     r.config = config_id;
@@ -356,6 +403,30 @@ mrhs_status mrhs_submit(mrhs_server *srv, int config_id, const double *b_host, d
     srv->outstanding++;
     *req_id = id;
     srv->cv.notify_all();
+    api_record(MRHS_OK, "");
+    return MRHS_OK;
+    S_CATCH
+}
+
+mrhs_status mrhs_server_set_reserve(mrhs_server *srv, double hbm_reserve_gb) {
+    S_TRY
+    if (!srv) fail(MRHS_ERR_INVALID, "server must be non-null");
+    if (!(hbm_reserve_gb >= 0)) fail(MRHS_ERR_INVALID, "hbm_reserve_gb must be >= 0");
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->p.hbm_reserve_gb = hbm_reserve_gb;
+    }
+    srv->cv.notify_all();
+    api_record(MRHS_OK, "");
+    return MRHS_OK;
+    S_CATCH
+}
+
+mrhs_status mrhs_server_memory_waits(mrhs_server *srv, uint64_t *count) {
+    S_TRY
+    if (!srv || !count) fail(MRHS_ERR_INVALID, "server and count must be non-null");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *count = srv->mem_waits;
     api_record(MRHS_OK, "");
     return MRHS_OK;
     S_CATCH

@@ -157,6 +157,8 @@ PROTOTYPES = {
     "mrhs_submit": (_I, [_P, _I, _P, _P, _I, _D, C.POINTER(C.c_uint64)]),
     "mrhs_poll": (_I, [_P, C.c_uint64, C.POINTER(RequestStats)]),
     "mrhs_server_drain": (_I, [_P]),
+    "mrhs_server_set_reserve": (_I, [_P, _D]),
+    "mrhs_server_memory_waits": (_I, [_P, C.POINTER(C.c_uint64)]),
     "mrhs_server_destroy": (None, [_P]),
     "mrhs_tune_set_enabled": (None, [_I]),
     "mrhs_tune_clear": (None, []),
@@ -408,6 +410,16 @@ def mrhs_poll(srv, req_id):
 
 def mrhs_server_drain(srv):
     _check(lib().mrhs_server_drain(srv))
+
+
+def mrhs_server_set_reserve(srv, hbm_reserve_gb):
+    _check(lib().mrhs_server_set_reserve(srv, float(hbm_reserve_gb)))
+
+
+def mrhs_server_memory_waits(srv):
+    c = C.c_uint64()
+    _check(lib().mrhs_server_memory_waits(srv, C.byref(c)))
+    return c.value
 
 
 def mrhs_server_destroy(srv):

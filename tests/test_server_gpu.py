@@ -77,3 +77,53 @@ def test_server_mix_equals_alone():
             mrhs.mrhs_destroy_mg(mg)
         for lat in lats:
             mrhs.mrhs_destroy_lattice(lat)
+
+
+def test_admission_waits_for_free_hbm():
+    """With the reserve set so that free HBM above it holds one request's staging
+    and not two, requests are staged one at a time (admissions deferred for
+    memory), and every one still completes to 1e-10; a request whose staging
+    exceeds the whole device above the reserve is refused at submit."""
+    import torch
+    dims, blocks, nvec, slots, seed = CONFIGS[0]
+    U = synth.gauge_exp(dims, 0.4, seed)
+    lat = make_lattice(U, dims, MASS, CSW)
+    V = wilson.volume(dims)
+    mg = make_mg(lat, _params(blocks, nvec, slots), [synth.gaussian_field(V, 12, nvec[0], seed + 7)])
+    srv = None
+    try:
+        srv = mrhs.mrhs_server_create(max_queue=64, hbm_reserve_gb=0.0)
+        cid = mrhs.mrhs_server_add_config(srv, mg, slots)
+        # warm the hierarchy's lazily sized buffers with one request at no reserve
+        b0 = synth.gaussian_field(V, 12, 1, 2500)
+        x0 = np.zeros_like(b0)
+        mrhs.mrhs_submit(srv, cid, b0, x0, 1, TOL)
+        mrhs.mrhs_server_drain(srv)
+        free_b, total_b = torch.cuda.mem_get_info()
+        need = V * 12 * 2 * 16  # staging of a 2-source request
+        mrhs.mrhs_server_set_reserve(srv, (free_b - 1.5 * need) / 1e9)
+        with pytest.raises(mrhs.MrhsError) as e:
+            big = np.zeros((V, 12, 1), np.complex128)
+            mrhs.mrhs_server_set_reserve(srv, total_b / 1e9)
+            mrhs.mrhs_submit(srv, cid, big, big.copy(), 1, TOL)
+        assert e.value.status == mrhs.MRHS_ERR_OOM
+        mrhs.mrhs_server_set_reserve(srv, (free_b - 1.5 * need) / 1e9)
+        w0 = mrhs.mrhs_server_memory_waits(srv)
+        reqs = []
+        for i in range(3):
+            b = synth.gaussian_field(V, 12, 2, 2510 + i)
+            x = np.zeros_like(b)
+            reqs.append((mrhs.mrhs_submit(srv, cid, b, x, 2, TOL), b, x))
+        mrhs.mrhs_server_drain(srv)
+        assert mrhs.mrhs_server_memory_waits(srv) > w0
+        C = wilson.clover_term(U, dims, CSW)
+        for rid, b, x in reqs:
+            status, _ = mrhs.mrhs_poll(srv, rid)
+            assert status == mrhs.MRHS_OK
+            rel = krylov.norms(b - wilson.apply_D(U, C, x, dims, MASS)) / krylov.norms(b)
+            assert np.all(rel <= TOL), rel
+    finally:
+        if srv is not None:
+            mrhs.mrhs_server_destroy(srv)
+        mrhs.mrhs_destroy_mg(mg)
+        mrhs.mrhs_destroy_lattice(lat)
