@@ -386,10 +386,14 @@ def gauge_field(w):
 SERVE_SMALL = dict(dims=(16, 16, 16, 32), gauge_seed=1402)
 
 
-def run_serving(mrhs, mg_big, w, saturated, args, torch, np):
+def run_serving(mrhs, mg_big, w, saturated, args, torch, np, load=None, nreq=None):
     """Poisson arrivals of 1..12-source requests, 50/50 over two resident
     hierarchies (the 24^3x64 one and a 16^3x32 one of the same recipe), at
-    `serve_load` times the measured saturated solves/s; p50 / p99 latency."""
+    `load` times the measured saturated solves/s; p50 / p99 latency, and the
+    time each request waited for admission (queue) against the time it then
+    spent in the batched solve."""
+    load = args.serve_load if load is None else load
+    nreq = args.serve_requests if nreq is None else nreq
     import synth
     dims_s = SERVE_SMALL["dims"]
     Us = synth.gauge_exp(dims_s, w["eps"], SERVE_SMALL["gauge_seed"])
@@ -408,11 +412,11 @@ def run_serving(mrhs, mg_big, w, saturated, args, torch, np):
         # offered load in requests/s: fraction of the RHS throughput, mean 6.5 RHS per request,
         # the small config costs about its volume ratio of a big solve
         mean_cost = 0.5 * (1.0 + vols[1] / vols[0]) * 6.5
-        rate = args.serve_load * saturated / mean_cost
+        rate = load * saturated / mean_cost
         reqs = []
         t0 = time.perf_counter()
         t_next = t0
-        for i in range(args.serve_requests):
+        for i in range(nreq):
             t_next += rng.exponential(1.0 / rate)
             while time.perf_counter() < t_next:
                 time.sleep(0.0005)
@@ -424,23 +428,45 @@ def run_serving(mrhs, mg_big, w, saturated, args, torch, np):
             reqs.append((rid, c, nr, x))
         mrhs.mrhs_server_drain(srv)
         wall = time.perf_counter() - t0
-        lat, ok, solves = [], 0, 0
+        lat, qt, ok, solves = [], [], 0, 0
         for rid, c, nr, x in reqs:
             st, rs = mrhs.mrhs_poll(srv, rid)
             lat.append(rs.latency_s)
+            qt.append(rs.queue_s)
             if st == mrhs.MRHS_OK:
                 ok += 1
                 solves += nr
         lat_ms = np.array(lat) * 1e3
+        q_ms = np.array(qt) * 1e3
+        s_ms = lat_ms - q_ms
         return {"requests": len(reqs), "completed_ok": ok, "solves": solves, "wall_s": wall,
-                "solves_per_s": solves / wall, "offered_load": args.serve_load,
+                "solves_per_s": solves / wall, "offered_load": load,
+                "offered_solves_per_s": load * saturated,
                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+                "queue_p50_ms": float(np.percentile(q_ms, 50)), "queue_p99_ms": float(np.percentile(q_ms, 99)),
+                "in_solve_p50_ms": float(np.percentile(s_ms, 50)), "in_solve_p99_ms": float(np.percentile(s_ms, 99)),
+                "memory_deferred_admissions": mrhs.mrhs_server_memory_waits(srv),
                 "configs": [w["dims"], dims_s], "slots_per_config": w["nrhs"],
                 "arrivals": "Poisson, seed 3001, 1..12 sources per request, 50/50 configs"}
     finally:
         mrhs.mrhs_server_destroy(srv)
         mrhs.mrhs_destroy_mg(mg_s)
         mrhs.mrhs_destroy_lattice(lat_s)
+
+
+def autotune_summary(mrhs):
+    out = []
+    for e in mrhs.mrhs_tune_entries():
+        d = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
+        if e["kernel"] in ("k_dots_norm", "k_norm2"):
+            dims = e["dims"]
+            d = {"kernel": e["kernel"], "rows": dims[0] + (dims[1] << 30), "k": dims[2], "nrhs": e["nrhs"],
+                 "variant": e["variant"], "rows_per_thread": (4, 16, 64)[e["variant"]],
+                 "nvariants": e["nvariants"], "best_ms": d["best_ms"], "default_ms": d["default_ms"]}
+        elif e["kernel"] == "k_coarse_tc":
+            d["ring_stages"] = (3, 2, 4)[e["variant"]]
+        out.append(d)
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -657,9 +683,10 @@ def run_ours(args, rank, world, local_rank):
             extra["cpu_baseline"] = oracle_in_subprocess(1, 0)
         extra["clocks"] = clk.summary()
         extra["gpu_launches"] = launches
-        # the autotuner's choices (tile shapes of the FP32 stencils), made in the warm-up steps
-        extra["autotune"] = [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in e.items()}
-                             for e in mrhs.mrhs_tune_entries() if e["dims"] == tuple(dims)]
+        # the autotuner's choices, made in the warm-up steps: visit orders of the FP32 fine stencils,
+        # ring depth of the tensor-core coarse stencil per level, grids of the batched reductions per
+        # field size (their key holds rows = dims[0] + 2^30 dims[1], k = dims[2])
+        extra["autotune"] = autotune_summary(mrhs)
         line = {
             "metric": "MG solves/s at 1e-10", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_dev / args.steps * 1e3,
@@ -782,6 +809,100 @@ def run_case(name, reps, args=None):
     print(json.dumps(out), flush=True)
 
 
+def run_c0_case(reps):
+    """The small plain solve on the GPU: 8^4, antiperiodic t, U = exp(i 0.4 H) (seed 1001), m = -0.2, c_sw = 1,
+    4 Gaussian sources, 2-level MG with 4^4 aggregates and 8 null vectors (nc = 16: the FP32 CUDA-core coarse
+    stencil), outer FP64 FGMRES to 1e-10; seconds per 4-RHS solve after setup."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2211_13719_gb300 import build as _build
+    from paper_2211_13719_gb300 import mrhs
+    _build.build()
+    dims, n = (8, 8, 8, 8), 4
+    V = volume(dims)
+    lat = mrhs.mrhs_create_lattice(dims, -1, torch.cuda.current_device())
+    mrhs.mrhs_load_gauge(lat, synth.gauge_exp(dims, 0.4, 1001))
+    mrhs.mrhs_build_clover(lat, -0.2, 1.0)
+    p = mrhs.mrhs_mg_default_params()
+    p.n_levels = 2
+    for mu in range(4):
+        p.block[0][mu] = 4
+    p.n_vec[0] = 8
+    p.setup_sweeps = 4
+    p.max_rhs = n
+    p.coarse_precision = mrhs.MRHS_FP32
+    p.coarse_m = 16
+    p.coarse_cycles = 2
+    p.smooth_m = 4
+    p.smoother_evenodd = 0
+    t0 = time.perf_counter()
+    mg = mrhs.mrhs_setup_mg(lat, p)
+    setup = time.perf_counter() - t0
+    b = torch.from_numpy(synth.gaussian_field(V, 12, n, 2001)).cuda()
+    x = torch.zeros_like(b)
+    rel = np.zeros(n)
+    times = []
+    for i in range(reps + 1):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        status, st = mrhs.mrhs_solve(mg, b, x, n, 1e-10, rel)
+        torch.cuda.synchronize()
+        if i:
+            times.append(time.perf_counter() - t0)
+    out = {"case": "c0", "setup_s": setup, "solve_4rhs_s": min(times), "outer_iters": st.outer_iters,
+           "inner_iters": st.inner_iters, "max_rel_residual": float(rel.max())}
+    mrhs.mrhs_destroy_mg(mg)
+    mrhs.mrhs_destroy_lattice(lat)
+    print(json.dumps(out), flush=True)
+
+
+def run_serving_case(args):
+    """The serving workload at several offered loads (--serve-loads, default 0.5, 0.8, 0.95 of the
+    saturated 48-RHS solve rate measured first), --serve-requests requests each (default here 500)."""
+    import numpy as np
+    import torch
+
+    from paper_2211_13719_gb300 import build as _build
+    from paper_2211_13719_gb300 import mrhs
+    _build.build()
+    w = dict(WORKLOAD)
+    n = w["nrhs"]
+    V = volume(w["dims"])
+    U = gauge_field(w)
+    lat = mrhs.mrhs_create_lattice(w["dims"], -1, torch.cuda.current_device())
+    mrhs.mrhs_load_gauge(lat, U)
+    mrhs.mrhs_build_clover(lat, w["mass"], w["csw"])
+    del U
+    mg = mrhs.mrhs_setup_mg(lat, make_params(mrhs, n, mrhs.MRHS_FP16, 1))
+    b = torch.randn((V, 12, n), dtype=torch.complex128, device="cuda")
+    x = torch.zeros_like(b)
+    rel = np.zeros(n)
+    for _ in range(2):
+        x.zero_()
+        mrhs.mrhs_solve(mg, b, x, n, w["tol"], rel)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        x.zero_()
+        mrhs.mrhs_solve(mg, b, x, n, w["tol"], rel)
+    torch.cuda.synchronize()
+    saturated = 2 * n / (time.perf_counter() - t0)
+    del b, x
+    out = {"case": "serving", "saturated_solves_per_s": saturated, "loads": []}
+    nreq = args.serve_requests if args.serve_requests != 24 else 500
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for load in [float(v) for v in args.serve_loads.split(",")]:
+            out["loads"].append(run_serving(mrhs, mg, w, saturated, args, torch, np, load=load, nreq=nreq))
+            print(json.dumps(out["loads"][-1]), flush=True)
+    out["clocks"] = clk.summary()
+    mrhs.mrhs_destroy_mg(mg)
+    mrhs.mrhs_destroy_lattice(lat)
+    print(json.dumps(out), flush=True)
+
+
 def run_coarse_case(mrhs, torch, reps):
     """Coarse level and intergrid operators on 24^4 (Haar gauge) with 4^4 aggregates and 32 null
     vectors: the 6^4 coarse lattice with nc = 64.  Per nRHS in {12, 24, 48}: the coarse stencil with FP32
@@ -888,17 +1009,24 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-loads", default="0.5,0.8,0.95", help="offered loads of --case serving")
     ap.add_argument("--smoother", default="evenodd", choices=["evenodd", "sap", "gmres"],
                     help="fine post-smoother: GMRES on the even-odd Schur complement (default), SAP, or GMRES on D")
     ap.add_argument("--sap-mr", type=int, default=4)
     ap.add_argument("--sap-cycles", type=int, default=1)
     ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas",
-                                                     "coarse", "oracle-table"],
+                                                     "coarse", "oracle-table", "serving", "c0"],
                     help="run a small profiling case of one kernel family instead of the benchmark")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--blas-rows", type=int, default=16 ** 4 * 12,
                     help="rows of the blas case (221184: the intermediate level, 3456 sites x 64 dof)")
     args = ap.parse_args()
+    if args.case == "c0":
+        run_c0_case(args.case_reps)
+        return
+    if args.case == "serving":
+        run_serving_case(args)
+        return
     if args.case == "oracle-table":
         for th in sorted({1, os.cpu_count() or 1}):
             print(json.dumps(oracle_table(th)), flush=True)

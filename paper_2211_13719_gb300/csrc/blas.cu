@@ -66,17 +66,18 @@ struct RedGeom {
 
 constexpr int RED_GROUP = 32;  // blocks per first-level group of the cross-block sum
 
-static RedGeom red_geom(int64_t rows, int n, int w = 1) {
+// rpt: at least this many rows per thread (the autotuner's grid variants below)
+static RedGeom red_geom(int64_t rows, int n, int w = 1, int rpt = 4) {
     RedGeom r;
     r.w = w;
     const int nw = n / w;
     const int target = w == 2 ? 128 : 256;
     r.rpb = nw >= target ? 1 : target / nw;
     r.threads = nw * r.rpb;
-    // at least 4 rows per thread, at most one wave of resident blocks (fit_wave):
+    // at least rpt rows per thread, at most one wave of resident blocks (fit_wave):
     // large fields run one full wave, small ones spread over many blocks so that
     // no thread walks a long chain of dependent row loads
-    const int64_t need = (rows + 4 * r.rpb - 1) / (4 * r.rpb);
+    const int64_t need = (rows + (int64_t)rpt * r.rpb - 1) / ((int64_t)rpt * r.rpb);
     const int64_t cap = (int64_t)current_sms() * (w == 2 ? 8 : 4);
     r.blocks = (int)std::max<int64_t>(1, std::min(need, cap));
     return r;
@@ -104,6 +105,21 @@ template <typename K> static void fit_wave(RedGeom &g, K kernel, size_t smem) {
         cache[key] = per_sm;
     }
     g.blocks = std::min(g.blocks, per_sm * current_sms());
+}
+
+// Grid variants of the reductions for the autotuner: the minimum rows per
+// thread.  4 (variant 0) spreads small fields over many blocks; on small
+// coarse-level fields (a few MB) that many blocks write per-block partial
+// sums nearly as large as the field, which 16 or 64 rows per thread avoid.
+constexpr int kRptVariants[] = {4, 16, 64};
+constexpr int kNumRpt = 3;
+
+// tuner key of a reduction over `rows` x n complex values (k basis vectors)
+static void blas_key(int64_t rows, int n, int k, int w, mrhs_precision p, int dims[4]) {
+    dims[0] = (int)(rows & 0x3fffffff);
+    dims[1] = (int)(rows >> 30);
+    dims[2] = k;
+    dims[3] = w * 16 + (int)p;
 }
 
 // FP32 fields take the paired path when n is even and every field pointer
@@ -683,7 +699,8 @@ void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const
 void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, int k, void *w, int64_t rows, int n,
                          double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s) {
     check_n(n);
-    const RedGeom g0 = red_geom(rows, n, pair_width(p, n, {basis, w}, stride));
+    const int pw = pair_width(p, n, {basis, w}, stride);
+    RedGeom g0 = red_geom(rows, n, pw);
     const bool f32 = p == MRHS_FP32;
     if (!f32 && p != MRHS_FP64) fail(MRHS_ERR_INVALID, "orthonormalize: FP32 or FP64 fields");
     const size_t esz = f32 ? 8 : 16;
@@ -696,21 +713,31 @@ void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, in
             continue;
         }
         const size_t smem = sizeof(double2) * (size_t)g0.rpb * (kk + 1) * n;
-        dispatch(p, g0.w, "orthonormalize", [&](auto tT, auto tW) {
-            RED_TYPES(tT, tW);
-            with_kmax(kk, [&](auto tK) {
-                constexpr int KM = decltype(tK)::value;
-                auto kern = k_dots_norm<T, W, KM, unroll_rows<T, KM>()>;
-                RedGeom g = g0;
-                fit_wave(g, kern, smem);
-                sc.ensure(g.blocks, (kk + 1) * n);
-                MRHS_TIMED("k_dots_norm", s);
-                kern<<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(basis) + 2 * j0 * stride, stride, kk,
-                                                       static_cast<const T *>(w), rows, n, g.rpb,
-                                                       sc.partials.as<double2>(), sc.counter.as<unsigned int>(),
-                                                       h + (int64_t)j0 * n, nrm2);
+        auto launch = [&](int v) {
+            dispatch(p, g0.w, "orthonormalize", [&](auto tT, auto tW) {
+                RED_TYPES(tT, tW);
+                with_kmax(kk, [&](auto tK) {
+                    constexpr int KM = decltype(tK)::value;
+                    auto kern = k_dots_norm<T, W, KM, unroll_rows<T, KM>()>;
+                    RedGeom g = red_geom(rows, n, pw, kRptVariants[v]);
+                    fit_wave(g, kern, smem);
+                    sc.ensure(g.blocks, (kk + 1) * n);
+                    kern<<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(basis) + 2 * j0 * stride, stride,
+                                                           kk, static_cast<const T *>(w), rows, n, g.rpb,
+                                                           sc.partials.as<double2>(), sc.counter.as<unsigned int>(),
+                                                           h + (int64_t)j0 * n, nrm2);
+                });
             });
-        });
+        };
+        // the dots and the norm only read their inputs: the autotuner may repeat the launch
+        int key[4];
+        blas_key(rows, n, kk, pw, p, key);
+        const int v = tune_pick("k_dots_norm", key, n, kNumRpt, launch, s);
+        g0 = red_geom(rows, n, pw, kRptVariants[v]);
+        {
+            MRHS_TIMED("k_dots_norm", s);
+            launch(v);
+        }
         MRHS_LAUNCHED("k_dots_norm");
         break;
     }
@@ -777,17 +804,26 @@ void multi_dot_fixed_scratch(mrhs_precision p, const void *basis, int64_t stride
 
 void norm2(mrhs_precision p, const void *w, int64_t rows, int n, double *out, Scratch &sc, cudaStream_t s) {
     check_n(n);
-    const RedGeom g0 = red_geom(rows, n, pair_width(p, n, {w}));
+    const int pw = pair_width(p, n, {w});
+    const RedGeom g0 = red_geom(rows, n, pw);
     const size_t smem = sizeof(double2) * (size_t)g0.rpb * n;
-    dispatch(p, g0.w, "norm2", [&](auto tT, auto tW) {
-        RED_TYPES(tT, tW);
-        RedGeom g = g0;
-        fit_wave(g, k_norm2<T, W>, smem);
-        sc.ensure(g.blocks, n);
-        MRHS_TIMED("k_norm2", s);
-        k_norm2<T, W><<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(w), rows, n, g.rpb,
-                                                        sc.partials.as<double2>(), sc.counter.as<unsigned int>(), out);
-    });
+    auto launch = [&](int v) {
+        dispatch(p, g0.w, "norm2", [&](auto tT, auto tW) {
+            RED_TYPES(tT, tW);
+            RedGeom g = red_geom(rows, n, pw, kRptVariants[v]);
+            fit_wave(g, k_norm2<T, W>, smem);
+            sc.ensure(g.blocks, n);
+            k_norm2<T, W><<<g.blocks, g.threads, smem, s>>>(static_cast<const T *>(w), rows, n, g.rpb,
+                                                            sc.partials.as<double2>(), sc.counter.as<unsigned int>(),
+                                                            out);
+        });
+    };
+    // an output that is also the input would not survive repeated launches
+    int key[4];
+    blas_key(rows, n, 0, pw, p, key);
+    const int v = (const void *)out == w ? 0 : tune_pick("k_norm2", key, n, kNumRpt, launch, s);
+    MRHS_TIMED("k_norm2", s);
+    launch(v);
     MRHS_LAUNCHED("k_norm2");
 }
 

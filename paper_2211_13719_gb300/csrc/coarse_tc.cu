@@ -53,8 +53,10 @@ using namespace tc;
 
 constexpr int NC = 64;                 // coarse dof handled by this kernel
 constexpr int MROWS = 128;             // 2 * NC real rows
-constexpr int STAGES = 3;
 constexpr int A_TILE = MROWS * NC * 2; // bytes of one BF16 link tile (16 KB)
+// depth of the bulk-copy ring (autotuner variants: 3, 2, 4 stages; fewer
+// stages leave room for more CTAs per SM)
+constexpr int kStageVariants[] = {3, 2, 4};
 
 struct TcArgs {
     int L[4];
@@ -75,6 +77,7 @@ __device__ __forceinline__ int64_t nb_site(int64_t site, const int L[4], int d) 
     return coords_to_site(c, L);
 }
 
+template <int STAGES>
 __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ Abf, const uint8_t *__restrict__ Phi,
                                                    float2 *__restrict__ out, const float2 *__restrict__ y, TcArgs a,
                                                    const float *__restrict__ link_scale,
@@ -277,11 +280,11 @@ __global__ void k_pack_links(const float2 *__restrict__ A, uint8_t *__restrict__
     *reinterpret_cast<uint16_t *>(img + tile * (int64_t)A_TILE + sw128_offset(m, k)) = to16<FMT>((m < NC ? v.x : v.y) / s);
 }
 
-size_t tc_smem_bytes(int npad) {
+size_t tc_smem_bytes(int npad, int stages) {
     const size_t b_tile = (size_t)npad * 128;
     const size_t stage = A_TILE + ((b_tile + 1023) & ~size_t(1023));
     const size_t epi = (size_t)MROWS * (npad + 1) * sizeof(float);
-    return std::max(stage * STAGES, epi) + 1024;
+    return std::max(stage * stages, epi) + 1024;
 }
 
 }  // namespace
@@ -346,15 +349,34 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
         }
         if (cap == cudaStreamCaptureStatusNone && left > 0) a.first_limit = 0;
     }
-    const size_t smem = tc_smem_bytes(npad);
     static bool attr = false;
     if (!attr) {
-        MRHS_CUDA(cudaFuncSetAttribute(k_coarse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(128)));
+        MRHS_CUDA(cudaFuncSetAttribute(k_coarse_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes(128, 2)));
+        MRHS_CUDA(cudaFuncSetAttribute(k_coarse_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes(128, 3)));
+        MRHS_CUDA(cudaFuncSetAttribute(k_coarse_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc_smem_bytes(128, 4)));
         attr = true;
     }
+    auto launch = [&](int v) {
+        const int stages = kStageVariants[v];
+        const size_t smem = tc_smem_bytes(npad, stages);
+        auto go = [&](auto kern) {
+            kern<<<(unsigned)c.V, 128, smem, s>>>(c.Abf.as<uint8_t>(), c.PhiBf.as<uint8_t>(), out, y, a,
+                                                   c.LinkScale.as<float>(), c.ColScale.as<float>(), c.TcErr.as<int>());
+        };
+        if (stages == 2) go(k_coarse_tc<2>);
+        else if (stages == 4) go(k_coarse_tc<4>);
+        else go(k_coarse_tc<3>);
+        MRHS_CUDA(cudaGetLastError());
+    };
+    // an output that aliases an input would not survive repeated launches; an expiring
+    // wait must happen in the launch that is not repeated: no tuning then
+    const bool alias = (const void *)out == (const void *)in || (y && (const void *)out == (const void *)y);
+    const int v = (alias || a.first_limit == 0) ? 0 : tune_pick("k_coarse_tc", c.L, n, 3, launch, s);
     MRHS_TIMED("k_coarse_tc", s);
-    k_coarse_tc<<<(unsigned)c.V, 128, smem, s>>>(c.Abf.as<uint8_t>(), c.PhiBf.as<uint8_t>(), out, y, a,
-                                                  c.LinkScale.as<float>(), c.ColScale.as<float>(), c.TcErr.as<int>());
+    launch(v);
     MRHS_LAUNCHED("k_coarse_tc");
 }
 

@@ -272,7 +272,7 @@ struct KArgs32 {
 // index counts x pairs (one output site of a given parity per pair, even-odd
 // kernels), the member of the pair is chosen by the caller.
 __device__ __forceinline__ bool visit_coords(const KArgs32 &a, int item, int nvisit, bool xpair, int c[4],
-                                             int &r0) {
+                                             int &r0, int per_thread = 2) {
     int visit;
     if (a.mode == 2) {
         const int per_slab = nvisit * a.GS;
@@ -280,11 +280,11 @@ __device__ __forceinline__ bool visit_coords(const KArgs32 &a, int item, int nvi
         const int rem = item - slab * per_slab;
         visit = rem / a.GS;
         if (slab * a.GS >= a.G) return false;
-        r0 = (slab * a.GS + rem - visit * a.GS) * 2;
+        r0 = (slab * a.GS + rem - visit * a.GS) * per_thread;
     } else {
         visit = item / a.G;
         if (visit >= nvisit) return false;
-        r0 = (item - visit * a.G) * 2;
+        r0 = (item - visit * a.G) * per_thread;
     }
     const int X = xpair ? a.L[0] / 2 : a.L[0];
     if (a.mode == 2) {
@@ -441,6 +441,145 @@ __global__ void __launch_bounds__(128, 3) k_dslash_x2(const float2 *__restrict__
     }
 }
 
+// ------------------------------------------------ one RHS per thread (FP32)
+// The same arithmetic as the paired kernels, one RHS per thread in scalar FMA:
+// every multiply-add, add and rounding happens in the order of the paired
+// code (p2mac = cmac, p2mac_conj = cmac_conj, p2add = add), so each output is
+// bitwise that of k_dslash_x2 / k_eo_x2.  No register pairs have to be built
+// (the paired code spends about a third of its instructions forming pairs
+// for FFMA2), and at half the registers twice the warps are resident to hide
+// the neighbour-load latency.  Links and site matrices from the site-major
+// copies; N: the RHS count compiled in.
+__device__ __forceinline__ cplx<float> ld_c1(const float2 *__restrict__ p, int64_t off) {
+    const float2 v = __ldg(p + off);
+    return {v.x, v.y};
+}
+__device__ __forceinline__ cplx<float> cadd_rn(cplx<float> a, cplx<float> b) {
+    return {__fadd_rn(a.re, b.re), __fadd_rn(a.im, b.im)};
+}
+
+template <int MU, bool FWD, int N>
+__device__ __forceinline__ void hop_r1(cplx<float> (&acc)[12], const float2 *__restrict__ U,
+                                      const float2 *__restrict__ in, int nb, int link_site, bool flip, int r) {
+    using P = Proj<MU>;
+    constexpr int F0 = FWD ? P::F0 : neg_f<P::F0>::v;
+    constexpr int F1 = FWD ? P::F1 : neg_f<P::F1>::v;
+    constexpr int G2 = FWD ? P::G2 : neg_f<P::G2>::v;
+    constexpr int G3 = FWD ? P::G3 : neg_f<P::G3>::v;
+    const float2 *pin = in + ((int64_t)nb * 12 * N + r);
+    cplx<float> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cplx<float> p0 = ld_c1(pin, (0 * 3 + c) * N);
+        const cplx<float> p1 = ld_c1(pin, (1 * 3 + c) * N);
+        const cplx<float> pa = ld_c1(pin, (P::P0 * 3 + c) * N);
+        const cplx<float> pb = ld_c1(pin, (P::P1 * 3 + c) * N);
+        h0[c] = cadd_rn(p0, fmul<F0>(pa));
+        h1[c] = cadd_rn(p1, fmul<F1>(pb));
+    }
+    if (flip) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            h0[c] = fmul<FM>(h0[c]);
+            h1[c] = fmul<FM>(h1[c]);
+        }
+    }
+    const float2 *Ul = U + ((int64_t)link_site * 4 + MU) * 9;
+#pragma unroll
+    for (int row = 0; row < 3; ++row) {
+        cplx<float> s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (FWD) {
+                const cplx<float> u = ld_c1(Ul, row * 3 + b);
+                cmac(s0, u, h0[b]);
+                cmac(s1, u, h1[b]);
+            } else {
+                const cplx<float> u = ld_c1(Ul, b * 3 + row);
+                cmac_conj(s0, u, h0[b]);
+                cmac_conj(s1, u, h1[b]);
+            }
+        }
+        acc[0 * 3 + row] = cadd_rn(acc[0 * 3 + row], s0);
+        acc[1 * 3 + row] = cadd_rn(acc[1 * 3 + row], s1);
+        acc[2 * 3 + row] = cadd_rn(acc[2 * 3 + row], fmul<G2>(P::Q2 == 0 ? s0 : s1));
+        acc[3 * 3 + row] = cadd_rn(acc[3 * 3 + row], fmul<G3>(P::Q3 == 0 ? s0 : s1));
+    }
+}
+
+// o = M v for chirality block chi of a site-major compact Hermitian site matrix (one RHS)
+__device__ __forceinline__ void site_mat_r1(const float2 *__restrict__ M, int site, int chi, const cplx<float> (&v)[6],
+                                            cplx<float> (&o)[6]) {
+    const float2 *Mp = M + (int64_t)site * 36 + chi * 18;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float2 d = __ldg(Mp + q);
+        o[2 * q] = {__fmul_rn(d.x, v[2 * q].re), __fmul_rn(d.x, v[2 * q].im)};
+        o[2 * q + 1] = {__fmul_rn(d.y, v[2 * q + 1].re), __fmul_rn(d.y, v[2 * q + 1].im)};
+    }
+    int q = 3;
+#pragma unroll
+    for (int i = 1; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j < i; ++j, ++q) {
+            const cplx<float> l = ld_c1(Mp, q);
+            cmac(o[i], l, v[j]);
+            cmac_conj(o[j], l, v[i]);
+        }
+    }
+}
+
+template <int MU, int N>
+__device__ __forceinline__ void hop_pair_r1(cplx<float> (&acc)[12], const float2 *__restrict__ U,
+                                           const float2 *__restrict__ in, const KArgs32 &a, int site, const int c[4],
+                                           int r) {
+    const int L = a.L[MU];
+    const int st = a.stride[MU];
+    const bool wrapF = (c[MU] == L - 1), wrapB = (c[MU] == 0);
+    const int sf = wrapF ? site - st * (L - 1) : site + st;
+    const int sb = wrapB ? site + st * (L - 1) : site - st;
+    const bool flipF = MU == 3 && wrapF && a.tb < 0;
+    const bool flipB = MU == 3 && wrapB && a.tb < 0;
+    hop_r1<MU, true, N>(acc, U, in, sf, site, flipF, r);
+    hop_r1<MU, false, N>(acc, U, in, sb, sb, flipB, r);
+}
+
+template <bool RESID, int N>
+__global__ void __launch_bounds__(128, 6) k_dslash_r1(const float2 *__restrict__ U, const float2 *__restrict__ C,
+                                                       const float2 *__restrict__ in, float2 *__restrict__ out,
+                                                       const float2 *__restrict__ y, KArgs32 a) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    int c[4], r;
+    if (!visit_coords(a, item, a.V, false, c, r, 1)) return;
+    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+    cplx<float> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = {0.f, 0.f};
+    hop_pair_r1<0, N>(acc, U, in, a, site, c, r);
+    hop_pair_r1<1, N>(acc, U, in, a, site, c, r);
+    hop_pair_r1<2, N>(acc, U, in, a, site, c, r);
+    hop_pair_r1<3, N>(acc, U, in, a, site, c, r);
+    const int64_t base = (int64_t)site * 12 * N + r;
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        cplx<float> v[6], o[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v[i] = ld_c1(in, base + (6 * chi + i) * N);
+        site_mat_r1(C, site, chi, v, o);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const cplx<float> ai = acc[6 * chi + i];
+            cplx<float> res = {__fmaf_rn(-0.5f, ai.re, o[i].re), __fmaf_rn(-0.5f, ai.im, o[i].im)};
+            const int64_t off = base + (6 * chi + i) * N;
+            if constexpr (RESID) {
+                const cplx<float> yy = ld_c1(y, off);
+                res = {__fadd_rn(yy.re, -res.re), __fadd_rn(yy.im, -res.im)};
+            }
+            __stcs(out + off, make_float2(res.re, res.im));
+        }
+    }
+}
+
 // geometry of the paired stencil with tiles of the largest powers of two up to
 // pref[mu] that divide L[mu] (pref[0] may be L[0]: whole x rows)
 static KArgs32 x2_args(const mrhs_lattice &lat, int n, const int pref[4]) {
@@ -510,9 +649,21 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
         if (!dup) args.push_back(a);
     }
     add_order_variants(args, args[0], 1);
+    // one-RHS-per-thread variants (compiled RHS counts only) on the first two tile shapes
+    const int nx2 = (int)args.size();
+    const bool r1 = n == 16 || n == 24 || n == 32 || n == 48 || n == 64;
+    if (r1)
+        for (int i = 0; i < 2 && i < nx2; ++i) {
+            KArgs32 b = args[(size_t)i];
+            if (b.mode != 0) continue;
+            b.G = n;
+            b.GS = n;
+            args.push_back(b);
+        }
     const int64_t items = (int64_t)args[0].V * args[0].G;
     const int threads = 128;
     const unsigned blocks = (unsigned)((items + threads - 1) / threads);
+    const unsigned blocks_r1 = (unsigned)(((int64_t)args[0].V * n + threads - 1) / threads);
     const float2 *yy = static_cast<const float2 *>(y);
     const float2 *ii = static_cast<const float2 *>(in);
     float2 *oo = static_cast<float2 *>(out);
@@ -520,12 +671,19 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
     // fewer: a warp spans several sites, whose link-major loads coalesce
     auto launch = [&](int v) {
         const KArgs32 &a = args[(size_t)v];
+        const bool one = v >= nx2;
         auto go = [&](auto resid, auto nc, auto aos) {
             constexpr bool R = decltype(resid)::value;
             constexpr int NC = decltype(nc)::value;
             constexpr bool AO = decltype(aos)::value;
             const float2 *U = AO ? lat.U32a.as<float2>() : lat.U32.as<float2>();
             const float2 *C = AO ? lat.C32a.as<float2>() : lat.C32.as<float2>();
+            if constexpr (NC > 0 && AO) {
+                if (one) {
+                    k_dslash_r1<R, NC><<<blocks_r1, threads, 0, s>>>(U, C, ii, oo, yy, a);
+                    return;
+                }
+            }
             k_dslash_x2<R, NC, AO><<<blocks, threads, 0, s>>>(U, C, ii, oo, yy, a);
         };
         auto pick = [&](auto resid) {
@@ -661,6 +819,83 @@ __global__ void __launch_bounds__(128, 3) k_eo_x2(const float2 *__restrict__ U, 
     }
 }
 
+// k_eo_x2 with one RHS per thread (scalar FMA in the paired code's order: bitwise equal results)
+template <int MODE, int N>
+__global__ void __launch_bounds__(128, 6) k_eo_r1(const float2 *__restrict__ U, const float2 *__restrict__ M,
+                                                   const float2 *__restrict__ in, const float2 *__restrict__ self,
+                                                   float2 *__restrict__ out, KArgsEO e) {
+    const KArgs32 &a = e.k;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    int c[4], r;
+    if (!visit_coords(a, item, e.V2, true, c, r, 1)) return;
+    c[0] *= 2;
+    if (((c[0] + c[1] + c[2] + c[3]) & 1) != e.parity) ++c[0];
+    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+    const int cb = site >> 1;
+    cplx<float> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = {0.f, 0.f};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const int L = a.L[mu], st = a.stride[mu];
+        const bool wrapF = (c[mu] == L - 1), wrapB = (c[mu] == 0);
+        const int sf = wrapF ? site - st * (L - 1) : site + st;
+        const int sb = wrapB ? site + st * (L - 1) : site - st;
+        const bool flipF = mu == 3 && wrapF && a.tb < 0;
+        const bool flipB = mu == 3 && wrapB && a.tb < 0;
+        if (mu == 0) {
+            hop_r1<0, true, N>(acc, U, in, sf >> 1, site, flipF, r);
+            hop_r1<0, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
+        } else if (mu == 1) {
+            hop_r1<1, true, N>(acc, U, in, sf >> 1, site, flipF, r);
+            hop_r1<1, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
+        } else if (mu == 2) {
+            hop_r1<2, true, N>(acc, U, in, sf >> 1, site, flipF, r);
+            hop_r1<2, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
+        } else {
+            hop_r1<3, true, N>(acc, U, in, sf >> 1, site, flipF, r);
+            hop_r1<3, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
+        }
+    }
+    const int64_t base = (int64_t)cb * 12 * N + r;
+    auto st1 = [&](int i, cplx<float> v) { __stcs(out + base + i * N, make_float2(v.re, v.im)); };
+    if constexpr (MODE == EO_HOP) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) st1(i, acc[i]);
+    } else if constexpr (MODE == EO_AXPY_HOP || MODE == EO_CINV_AXPY_HOP) {
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi) {
+            cplx<float> v[6], o[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const cplx<float> yv = ld_c1(self, base + (6 * chi + i) * N);
+                const cplx<float> ai = acc[6 * chi + i];
+                v[i] = {__fmaf_rn(0.5f, ai.re, yv.re), __fmaf_rn(0.5f, ai.im, yv.im)};
+            }
+            if constexpr (MODE == EO_CINV_AXPY_HOP) site_mat_r1(M, site, chi, v, o);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) st1(6 * chi + i, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
+        }
+    } else {
+#pragma unroll
+        for (int chi = 0; chi < 2; ++chi) {
+            cplx<float> v[6], o[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) v[i] = MODE == EO_CINV_HOP ? acc[6 * chi + i] : ld_c1(self, base + (6 * chi + i) * N);
+            site_mat_r1(M, site, chi, v, o);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                cplx<float> res = o[i];
+                if constexpr (MODE == EO_SCHUR) {
+                    const cplx<float> ai = acc[6 * chi + i];
+                    res = {__fmaf_rn(-0.25f, ai.re, o[i].re), __fmaf_rn(-0.25f, ai.im, o[i].im)};
+                }
+                st1(6 * chi + i, res);
+            }
+        }
+    }
+}
+
 static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity, const int pref[4] = nullptr) {
     KArgsEO e;
     KArgs32 &a = e.k;
@@ -725,12 +960,24 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
             args.push_back(e);
         }
     }
+    // one-RHS-per-thread variants (compiled RHS counts) on the first two tile shapes
+    const int nx2 = (int)args.size();
+    if (n == 16 || n == 24 || n == 32 || n == 48 || n == 64)
+        for (int i = 0; i < 2 && i < nx2; ++i) {
+            KArgsEO b = args[(size_t)i];
+            if (b.k.mode != 0) continue;
+            b.k.G = n;
+            b.k.GS = n;
+            args.push_back(b);
+        }
     const int64_t items = (int64_t)args[0].V2 * args[0].k.G;
     const unsigned blocks = (unsigned)((items + 127) / 128);
+    const unsigned blocks_r1 = (unsigned)(((int64_t)args[0].V2 * n + 127) / 128);
     // as the full-lattice stencil: compile-time RHS count and site-major links /
     // site matrices for 16, 24, 32, 48, 64 RHS
     auto launch = [&](int v) {
         const KArgsEO &e = args[(size_t)v];
+        const bool one = v >= nx2;
         auto go = [&](auto nc, auto aos) {
             constexpr int NC = decltype(nc)::value;
             constexpr bool AO = decltype(aos)::value;
@@ -738,6 +985,12 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
             const float2 *M = mat == EO_MAT_C      ? (AO ? lat.C32a.as<float2>() : lat.C32.as<float2>())
                               : mat == EO_MAT_CINV ? (AO ? lat.Cinv32a.as<float2>() : lat.Cinv32.as<float2>())
                                                    : nullptr;
+            if constexpr (NC > 0 && AO) {
+                if (one) {
+                    k_eo_r1<MODE, NC><<<blocks_r1, 128, 0, s>>>(U, M, in, self, out, e);
+                    return;
+                }
+            }
             k_eo_x2<MODE, NC, AO><<<blocks, 128, 0, s>>>(U, M, in, self, out, e);
         };
         switch (n) {
