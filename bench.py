@@ -809,6 +809,61 @@ def run_case(name, reps, args=None):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_case(reps):
+    """Uneven MRHS blocks (the serving mix: two resident volumes, requests of a few sources): the FP32 fine
+    operator in its residual form on each block by separate launches, against one fused persistent
+    launch (mrhs_apply_D_batch) over all of them.  Algorithmic bytes per block: V (576 + 192 n) + V 96 n (y)."""
+    import torch
+
+    import synth
+    from paper_2211_13719_gb300 import build as _build
+    from paper_2211_13719_gb300 import mrhs
+    _build.build()
+    mix = [((16, 16, 16, 32), 12), ((16, 16, 16, 32), 6), ((8, 8, 8, 16), 4), ((12, 12, 12, 24), 8),
+           ((16, 16, 16, 32), 2), ((8, 8, 8, 16), 12)]
+    stream = torch.cuda.current_stream()
+    lats, items, alg = {}, [], 0
+    for dims, n in mix:
+        if dims not in lats:
+            lat = mrhs.mrhs_create_lattice(dims, -1, torch.cuda.current_device())
+            mrhs.mrhs_load_gauge(lat, synth.gauge_exp(dims, WORKLOAD["eps"], 1402))
+            mrhs.mrhs_build_clover(lat, WORKLOAD["mass"], WORKLOAD["csw"])
+            lats[dims] = lat
+        V = volume(dims)
+        x = torch.randn((V, 12, n), dtype=torch.complex64, device="cuda")
+        y = torch.randn_like(x)
+        o = torch.empty_like(x)
+        items.append((lats[dims], x, o, y, n))
+        alg += V * (576 + 192 * n) + V * 96 * n
+
+    def separate():
+        for lat, x, o, y, n in items:
+            mrhs.mrhs_residual_D(lat, x, y, o, n, mrhs.MRHS_FP32, stream)
+
+    def fused():
+        mrhs.mrhs_apply_D_batch(items, stream)
+
+    def ev(fn):
+        for _ in range(5):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_sep, ms_fused = ev(separate), ev(fused)
+    out = {"case": "batch", "blocks": [[list(d), n] for d, n in mix], "alg_bytes": alg,
+           "ms_separate_launches": ms_sep, "ms_fused_launch": ms_fused, "speedup": ms_sep / ms_fused,
+           "alg_GBs_separate": alg / ms_sep / 1e6, "alg_GBs_fused": alg / ms_fused / 1e6}
+    for lat in lats.values():
+        mrhs.mrhs_destroy_lattice(lat)
+    print(json.dumps(out), flush=True)
+
+
 def run_c0_case(reps):
     """The small plain solve on the GPU: 8^4, antiperiodic t, U = exp(i 0.4 H) (seed 1001), m = -0.2, c_sw = 1,
     4 Gaussian sources, 2-level MG with 4^4 aggregates and 8 null vectors (nc = 16: the FP32 CUDA-core coarse
@@ -1015,12 +1070,15 @@ def main():
     ap.add_argument("--sap-mr", type=int, default=4)
     ap.add_argument("--sap-cycles", type=int, default=1)
     ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas",
-                                                     "coarse", "oracle-table", "serving", "c0"],
+                                                     "coarse", "oracle-table", "serving", "c0", "batch"],
                     help="run a small profiling case of one kernel family instead of the benchmark")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--blas-rows", type=int, default=16 ** 4 * 12,
                     help="rows of the blas case (221184: the intermediate level, 3456 sites x 64 dof)")
     args = ap.parse_args()
+    if args.case == "batch":
+        run_batch_case(max(args.case_reps, 20))
+        return
     if args.case == "c0":
         run_c0_case(args.case_reps)
         return

@@ -169,6 +169,26 @@ mrhs_status mrhs_apply_D(mrhs_lattice *lat, const void *in_dev, void *out_dev,
 mrhs_status mrhs_residual_D(mrhs_lattice *lat, const void *in_dev, const void *y_dev,
                             void *out_dev, int nrhs, mrhs_precision prec, void *stream);
 
+/* One problem of a fused batch: out = D in (y_dev NULL) or out = y - D in,
+ * FP32 device fields [V][12][nrhs] of `lat` (layout of mrhs_apply_D). */
+typedef struct {
+    mrhs_lattice *lat;
+    const void *in_dev;
+    void *out_dev;
+    const void *y_dev;      /* NULL or FP32 [V][12][nrhs] */
+    int nrhs;               /* 1..256 (the fused kernel compiles 16/24/32/48/64) */
+} mrhs_apply_item;
+
+/* The FP32 fine operator (hop + clover + axpy of the residual form, Sec. 4)
+ * on 1..8 problems of different lattice volumes and RHS counts in one
+ * persistent launch: the problems' work is concatenated and one occupancy
+ * wave of CTAs walks it, so small or uneven MRHS blocks share the GPU
+ * instead of each paying a launch and a partial wave.  Every output equals
+ * the single-problem mrhs_apply_D / mrhs_residual_D result of the same
+ * problem (the same arithmetic per element).  All lattices on one device;
+ * out must not alias in.  MRHS_ERR_INVALID on bad counts or arguments. */
+mrhs_status mrhs_apply_D_batch(const mrhs_apply_item *items, int count, void *stream);
+
 
 /* Even-odd decomposition (Sec. 4, M_eooe: the hopping term between the
  * checkerboarded lattices).  Half-lattice fields are [V/2][12][nrhs] complex

@@ -203,6 +203,23 @@ mrhs_status mrhs_residual_D(mrhs_lattice *lat, const void *in_dev, const void *y
     MRHS_API_END
 }
 
+mrhs_status mrhs_apply_D_batch(const mrhs_apply_item *items, int count, void *stream) {
+    MRHS_API_BEGIN
+    if (!items || count < 1 || count > 8) fail(MRHS_ERR_INVALID, "items must be non-null and count in 1..8");
+    std::vector<BatchItemHost> h((size_t)count);
+    for (int i = 0; i < count; ++i) {
+        const mrhs_apply_item &it = items[i];
+        if (!it.lat) fail(MRHS_ERR_INVALID, "every batch item needs a lattice");
+        check_apply(it.lat, it.in_dev, it.out_dev, it.nrhs, MRHS_FP32);
+        if (it.y_dev && (reinterpret_cast<uintptr_t>(it.y_dev) & 7u))
+            fail(MRHS_ERR_INVALID, "y must be 8-byte aligned");
+        h[(size_t)i] = BatchItemHost{it.lat, it.in_dev, it.out_dev, it.y_dev, it.nrhs};
+    }
+    DeviceGuard dg(items[0].lat->device);
+    dslash_batch(h.data(), count, static_cast<cudaStream_t>(stream));
+    MRHS_API_END
+}
+
 mrhs_status mrhs_apply_hop_eo(mrhs_lattice *lat, int out_parity, const void *in_dev, void *out_dev, int nrhs,
                               void *stream) {
     MRHS_API_BEGIN

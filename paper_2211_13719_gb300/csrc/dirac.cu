@@ -17,6 +17,7 @@
 // A_k = -i sigma_k, A_t = 1): (1 -+ gamma_mu) psi has rank 2, so each hop
 // forms a 2-spin half spinor h = psi_up -+ A psi_dn, multiplies it by the
 // link, and rebuilds the lower spins from the two products.
+#include <algorithm>
 #include <type_traits>
 #include <vector>
 
@@ -460,20 +461,22 @@ __device__ __forceinline__ cplx<float> cadd_rn(cplx<float> a, cplx<float> b) {
 
 template <int MU, bool FWD, int N>
 __device__ __forceinline__ void hop_r1(cplx<float> (&acc)[12], const float2 *__restrict__ U,
-                                      const float2 *__restrict__ in, int nb, int link_site, bool flip, int r) {
+                                      const float2 *__restrict__ in, int nb, int link_site, bool flip, int r,
+                                      int n_rt = 0) {
     using P = Proj<MU>;
     constexpr int F0 = FWD ? P::F0 : neg_f<P::F0>::v;
     constexpr int F1 = FWD ? P::F1 : neg_f<P::F1>::v;
     constexpr int G2 = FWD ? P::G2 : neg_f<P::G2>::v;
     constexpr int G3 = FWD ? P::G3 : neg_f<P::G3>::v;
-    const float2 *pin = in + ((int64_t)nb * 12 * N + r);
+    const int n = N ? N : n_rt;  // RHS count: compiled in, or at run time (N = 0)
+    const float2 *pin = in + ((int64_t)nb * 12 * n + r);
     cplx<float> h0[3], h1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const cplx<float> p0 = ld_c1(pin, (0 * 3 + c) * N);
-        const cplx<float> p1 = ld_c1(pin, (1 * 3 + c) * N);
-        const cplx<float> pa = ld_c1(pin, (P::P0 * 3 + c) * N);
-        const cplx<float> pb = ld_c1(pin, (P::P1 * 3 + c) * N);
+        const cplx<float> p0 = ld_c1(pin, (0 * 3 + c) * n);
+        const cplx<float> p1 = ld_c1(pin, (1 * 3 + c) * n);
+        const cplx<float> pa = ld_c1(pin, (P::P0 * 3 + c) * n);
+        const cplx<float> pb = ld_c1(pin, (P::P1 * 3 + c) * n);
         h0[c] = cadd_rn(p0, fmul<F0>(pa));
         h1[c] = cadd_rn(p1, fmul<F1>(pb));
     }
@@ -540,8 +543,45 @@ __device__ __forceinline__ void hop_pair_r1(cplx<float> (&acc)[12], const float2
     const int sb = wrapB ? site + st * (L - 1) : site - st;
     const bool flipF = MU == 3 && wrapF && a.tb < 0;
     const bool flipB = MU == 3 && wrapB && a.tb < 0;
-    hop_r1<MU, true, N>(acc, U, in, sf, site, flipF, r);
-    hop_r1<MU, false, N>(acc, U, in, sb, sb, flipB, r);
+    hop_r1<MU, true, N>(acc, U, in, sf, site, flipF, r, a.n);
+    hop_r1<MU, false, N>(acc, U, in, sb, sb, flipB, r, a.n);
+}
+
+// out(x) = (D in)(x) (RESID: y(x) - (D in)(x)) for RHS r of the site at coordinates c:
+// the hop, the clover term and the axpy of one thread (one RHS)
+template <bool RESID, int N>
+__device__ __forceinline__ void dslash_r1_site(const float2 *__restrict__ U, const float2 *__restrict__ C,
+                                               const float2 *__restrict__ in, float2 *__restrict__ out,
+                                               const float2 *__restrict__ y, const KArgs32 &a, const int c[4],
+                                               int r) {
+    const int n = N ? N : a.n;
+    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+    cplx<float> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = {0.f, 0.f};
+    hop_pair_r1<0, N>(acc, U, in, a, site, c, r);
+    hop_pair_r1<1, N>(acc, U, in, a, site, c, r);
+    hop_pair_r1<2, N>(acc, U, in, a, site, c, r);
+    hop_pair_r1<3, N>(acc, U, in, a, site, c, r);
+    const int64_t base = (int64_t)site * 12 * n + r;
+#pragma unroll
+    for (int chi = 0; chi < 2; ++chi) {
+        cplx<float> v[6], o[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) v[i] = ld_c1(in, base + (6 * chi + i) * n);
+        site_mat_r1(C, site, chi, v, o);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const cplx<float> ai = acc[6 * chi + i];
+            cplx<float> res = {__fmaf_rn(-0.5f, ai.re, o[i].re), __fmaf_rn(-0.5f, ai.im, o[i].im)};
+            const int64_t off = base + (6 * chi + i) * n;
+            if constexpr (RESID) {
+                const cplx<float> yy = ld_c1(y, off);
+                res = {__fadd_rn(yy.re, -res.re), __fadd_rn(yy.im, -res.im)};
+            }
+            __stcs(out + off, make_float2(res.re, res.im));
+        }
+    }
 }
 
 template <bool RESID, int N>
@@ -551,32 +591,52 @@ __global__ void __launch_bounds__(128, 6) k_dslash_r1(const float2 *__restrict__
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
     int c[4], r;
     if (!visit_coords(a, item, a.V, false, c, r, 1)) return;
-    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
-    cplx<float> acc[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) acc[i] = {0.f, 0.f};
-    hop_pair_r1<0, N>(acc, U, in, a, site, c, r);
-    hop_pair_r1<1, N>(acc, U, in, a, site, c, r);
-    hop_pair_r1<2, N>(acc, U, in, a, site, c, r);
-    hop_pair_r1<3, N>(acc, U, in, a, site, c, r);
-    const int64_t base = (int64_t)site * 12 * N + r;
-#pragma unroll
-    for (int chi = 0; chi < 2; ++chi) {
-        cplx<float> v[6], o[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) v[i] = ld_c1(in, base + (6 * chi + i) * N);
-        site_mat_r1(C, site, chi, v, o);
-#pragma unroll
-        for (int i = 0; i < 6; ++i) {
-            const cplx<float> ai = acc[6 * chi + i];
-            cplx<float> res = {__fmaf_rn(-0.5f, ai.re, o[i].re), __fmaf_rn(-0.5f, ai.im, o[i].im)};
-            const int64_t off = base + (6 * chi + i) * N;
-            if constexpr (RESID) {
-                const cplx<float> yy = ld_c1(y, off);
-                res = {__fadd_rn(yy.re, -res.re), __fadd_rn(yy.im, -res.im)};
-            }
-            __stcs(out + off, make_float2(res.re, res.im));
-        }
+    dslash_r1_site<RESID, N>(U, C, in, out, y, a, c, r);
+}
+
+// ------------------------------------- fused batch of uneven problems
+// One persistent launch applies D (or y - D x) to up to kMaxBatch problems of
+// different lattice volumes and RHS counts: the problems' work blocks (128
+// threads of one RHS each) are concatenated, and a grid of one occupancy wave
+// walks them grid-stride, so small problems share the GPU instead of each
+// paying a launch and a partial wave.  Per thread the arithmetic is that of
+// k_dslash_r1 (bitwise equal to the single-problem stencil).
+constexpr int kMaxBatch = 8;
+struct BatchItem {
+    const float2 *U, *C, *in;
+    float2 *out;
+    const float2 *y;  // nullptr: out = D in
+    KArgs32 a;        // one RHS per thread (G = n), site tiles
+    int first_block;  // first work block of this problem
+};
+struct BatchArgs {
+    BatchItem it[kMaxBatch];
+    int count;
+    int total_blocks;
+};
+
+template <bool RESID>
+__device__ __forceinline__ void batch_site(const BatchItem &w, const int c[4], int r) {
+    switch (w.a.n) {
+        case 16: dslash_r1_site<RESID, 16>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 24: dslash_r1_site<RESID, 24>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 32: dslash_r1_site<RESID, 32>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 48: dslash_r1_site<RESID, 48>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 64: dslash_r1_site<RESID, 64>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        default: dslash_r1_site<RESID, 0>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+    }
+}
+
+__global__ void __launch_bounds__(128, 6) k_dslash_batch(const __grid_constant__ BatchArgs b) {
+    for (int blk = blockIdx.x; blk < b.total_blocks; blk += gridDim.x) {
+        int p = 0;
+        while (p + 1 < b.count && blk >= b.it[p + 1].first_block) ++p;
+        const BatchItem &w = b.it[p];
+        const int item = (blk - w.first_block) * blockDim.x + threadIdx.x;
+        int c[4], r;
+        if (!visit_coords(w.a, item, w.a.V, false, c, r, 1)) continue;
+        if (w.y) batch_site<true>(w, c, r);
+        else batch_site<false>(w, c, r);
     }
 }
 
@@ -715,6 +775,47 @@ static bool launch_dslash_x2(const mrhs_lattice &lat, const void *in, void *out,
     launch(v);
     MRHS_LAUNCHED("k_dslash_x2");
     return true;
+}
+
+void dslash_batch(const BatchItemHost *items, int count, cudaStream_t s) {
+    if (count < 1 || count > kMaxBatch) fail(MRHS_ERR_INVALID, "batch holds 1..8 problems");
+    BatchArgs b{};
+    b.count = count;
+    int blocks = 0, dev = -1;
+    for (int i = 0; i < count; ++i) {
+        const BatchItemHost &h = items[i];
+        const mrhs_lattice *lat = h.lat;
+        if (!lat || !lat->has_clover) fail(MRHS_ERR_INVALID, "every batch item needs a lattice with its clover term");
+        if (dev >= 0 && lat->device != dev) fail(MRHS_ERR_INVALID, "batch items must share one device");
+        dev = lat->device;
+        if (h.n < 1 || h.n > 256) fail(MRHS_ERR_INVALID, "batch item nrhs must be in 1..256");
+        if (!h.in || !h.out || h.in == h.out) fail(MRHS_ERR_INVALID, "batch item needs distinct non-null in and out");
+        if (lat->g.V * 12LL * h.n >= (1LL << 31) || lat->g.V * (int64_t)h.n >= (1LL << 31))
+            fail(MRHS_ERR_INVALID, "batch item too large for 32-bit indexing");
+        static const int pref[4] = {1, 4, 8, 8};
+        KArgs32 a = x2_args(*lat, h.n, pref);
+        a.G = h.n;
+        a.GS = h.n;
+        BatchItem &w = b.it[i];
+        w.U = lat->U32a.as<float2>();
+        w.C = lat->C32a.as<float2>();
+        w.in = static_cast<const float2 *>(h.in);
+        w.out = static_cast<float2 *>(h.out);
+        w.y = static_cast<const float2 *>(h.y);
+        w.a = a;
+        w.first_block = blocks;
+        blocks += (int)ceil_div((int64_t)lat->g.V * h.n, 128);
+    }
+    b.total_blocks = blocks;
+    int per_sm = 0;
+    MRHS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dslash_batch, 128, 0));
+    int devc = 0;
+    MRHS_CUDA(cudaGetDevice(&devc));
+    const int grid = std::max(1, std::min(blocks, std::max(1, per_sm) * sm_count(devc)));
+    MRHS_TIMED("k_dslash_batch", s);
+    k_dslash_batch<<<grid, 128, 0, s>>>(b);
+    MRHS_CUDA(cudaGetLastError());
+    MRHS_LAUNCHED("k_dslash_batch");
 }
 
 // ------------------------------------------------ even-odd (M_eooe) kernels

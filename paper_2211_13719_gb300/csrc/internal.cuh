@@ -80,6 +80,18 @@ void split_df(const void *src_c128, void *dst_f4, int64_t count, cudaStream_t s)
 // out = D in (y == nullptr) or y - D in; `in` FP32, out and y FP64, float-float arithmetic
 void dslash_df(const mrhs_lattice &lat, const void *in, void *out, const void *y, int n, cudaStream_t s);
 void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s);
+// One problem of a fused batch: out = D in (y == nullptr) or y - D in, FP32
+// fields [V][12][n] of lattice `lat`.
+struct BatchItemHost {
+    const mrhs_lattice *lat;
+    const void *in;
+    void *out;
+    const void *y;
+    int n;
+};
+// The fine operator on up to 8 problems of different volumes and RHS counts
+// (same device) in one persistent launch.
+void dslash_batch(const BatchItemHost *items, int count, cudaStream_t s);
 // out = D in (y == nullptr) or out = y - D in; compute in `compute` precision,
 // input in `in_prec` (FP32 input allowed with FP64 compute); out and y in `compute`.
 void dslash(const mrhs_lattice &lat, mrhs_precision compute, mrhs_precision in_prec,

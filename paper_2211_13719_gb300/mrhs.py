@@ -103,6 +103,16 @@ class RequestStats(C.Structure):
     ]
 
 
+class ApplyItem(C.Structure):
+    _fields_ = [
+        ("lat", C.c_void_p),
+        ("in_dev", C.c_void_p),
+        ("out_dev", C.c_void_p),
+        ("y_dev", C.c_void_p),
+        ("nrhs", C.c_int),
+    ]
+
+
 class TuneEntry(C.Structure):
     _fields_ = [
         ("kernel", C.c_char * 32),
@@ -136,6 +146,7 @@ PROTOTYPES = {
     "mrhs_get_clover": (_I, [_P, _P]),
     "mrhs_apply_D": (_I, [_P, _P, _P, _I, _I, _P]),
     "mrhs_residual_D": (_I, [_P, _P, _P, _P, _I, _I, _P]),
+    "mrhs_apply_D_batch": (_I, [C.POINTER(ApplyItem), _I, _P]),
     "mrhs_blas_multi_dot": (_I, [_P, _I, _P, _I64, _I, _I, _P, _P]),
     "mrhs_blas_multi_dot_noalloc": (_I, [_P, _I, _P, _I64, _I, _I, _P, _P]),
     "mrhs_blas_norm2": (_I, [_P, _I64, _I, _I, _P, _P]),
@@ -299,6 +310,12 @@ def mrhs_apply_D(lat, in_dev, out_dev, nrhs, prec, stream=None):
 def mrhs_residual_D(lat, in_dev, y_dev, out_dev, nrhs, prec, stream=None):
     _check(lib().mrhs_residual_D(lat, _ptr(in_dev), _ptr(y_dev), _ptr(out_dev), int(nrhs), int(prec),
                                  _stream(stream)))
+
+
+def mrhs_apply_D_batch(items, stream=None):
+    """items: list of (lat, in_dev, out_dev, y_dev or None, nrhs)."""
+    arr = (ApplyItem * len(items))(*[ApplyItem(lat, _ptr(i), _ptr(o), _ptr(y), int(n)) for lat, i, o, y, n in items])
+    _check(lib().mrhs_apply_D_batch(arr, len(items), _stream(stream)))
 
 
 # --------------------------------------------------------------------- BLAS
