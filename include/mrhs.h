@@ -301,6 +301,11 @@ typedef struct {
     int sap_block[4];                      /* SAP block extents                   */
     int sap_cycles;                        /* SAP cycles per post-smoothing       */
     int sap_mr;                            /* MR steps per SAP block solve        */
+    int coarse_smoother_evenodd;           /* 1: intermediate levels post-smooth with
+                                              smooth_m GMRES steps on the coarse
+                                              even-odd Schur complement (16-bit
+                                              tensor-core levels with even extents;
+                                              otherwise GMRES on the level operator) */
 } mrhs_mg_params;
 
 /* Fill `p` with the defaults used for the 24^3x64 three-level workload. */
@@ -353,6 +358,18 @@ mrhs_status mrhs_prolong(mrhs_mg *mg, int level, const void *coarse_dev,
  * one scale per RHS column, so FP16 neither overflows nor underflows. */
 mrhs_status mrhs_coarse_apply(mrhs_mg *mg, int level, const void *in_dev, void *out_dev,
                               int nrhs, mrhs_precision links_prec, void *stream);
+
+/* Coarse even-odd Schur complement (Sec. 6, coarse M_eooe) on level `level`
+ * (>= 1, a 16-bit tensor-core level with even extents, prepared at setup with
+ * coarse_smoother_evenodd = 1): out_o = D_hat in_o = A_oo in_o - H_oe A_ee^-1
+ * H_eo in_o, with A the 9-point stencil's self blocks and H its hops, on odd
+ * half fields [Vc/2][64][nrhs] FP32 (the odd sites in lexicographic order).
+ * A_ee^-1 is inverted per site in FP64 at setup and applied, like A and H, on
+ * the tensor cores in the level's 16-bit format with FP32 accumulation.
+ * Allocates two even half fields of scratch per call; returns after the work
+ * on `stream` (it reads the kernels' bounded-wait flag). */
+mrhs_status mrhs_coarse_apply_schur(mrhs_mg *mg, int level, const void *in_dev, void *out_dev, int nrhs,
+                                    void *stream);
 
 /* One MG V-cycle z = M^{-1} v on the fine level (Sec. 8 preconditioner),
  * FP32 fields [V][12][nrhs]. */

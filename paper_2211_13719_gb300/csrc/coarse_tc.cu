@@ -65,7 +65,22 @@ struct TcArgs {
     uint32_t idesc;
     uint32_t tmem_cols;
     uint32_t first_limit;  // try_wait rounds of the first operand wait (SPIN_LIMIT; 0 when a test expires it)
+    // stencil terms and site set: directions d_first..d_last; link tile of (site, d) at
+    // site * links_per_site + d - d_first; parity < 0: every site, fields full-lattice;
+    // parity 0 / 1: the output sites are those of that parity and the output field and
+    // the packed input are half-lattice fields (a site s at index s / 2)
+    int d_first, d_last;
+    int links_per_site;
+    int parity;
 };
+
+// site of half-lattice index cb and parity p (even x extent: the sites 2 cb and
+// 2 cb + 1 form an x pair of opposite parities)
+__device__ __forceinline__ int64_t cb_site(int64_t cb, int p, const int L[4]) {
+    int c[4];
+    site_to_coords(2 * cb, L, c);
+    return ((c[0] + c[1] + c[2] + c[3]) & 1) == p ? 2 * cb : 2 * cb + 1;
+}
 
 __device__ __forceinline__ int64_t nb_site(int64_t site, const int L[4], int d) {
     if (d == 0) return site;
@@ -87,7 +102,9 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ A
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t site = blockIdx.x;
+    const int64_t cta = blockIdx.x;
+    const int64_t site = a.parity < 0 ? cta : cb_site(cta, a.parity, a.L);
+    const int ndir = a.d_last - a.d_first + 1;
     const uint32_t b_tile = (uint32_t)a.npad * 128u;
     const uint32_t stage_bytes = A_TILE + ((b_tile + 1023u) & ~1023u);
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -117,20 +134,22 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ A
         // producer + MMA issuer: loads run STAGES - 1 directions ahead of the MMAs
         bool ok = true;
         int issued = 0;
-        for (int step = 0; step < 9 + STAGES - 1 && ok; ++step) {
-            if (step < 9) {
-                const int d = step, s = d % STAGES;
-                if (d >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((d / STAGES) - 1) & 1);
+        for (int step = 0; step < ndir + STAGES - 1 && ok; ++step) {
+            if (step < ndir) {
+                const int q = step, s = q % STAGES;
+                if (q >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((q / STAGES) - 1) & 1);
                 if (!ok) break;
+                const int d = a.d_first + q;
                 const int64_t nb = nb_site(site, a.L, d);
+                const int64_t pin = a.parity < 0 ? nb : nb >> 1;
                 const uint32_t sa = sbase + s * stage_bytes;
                 mbar_expect_tx(full0 + 8 * s, A_TILE + b_tile);
-                bulk_g2s(sa, Abf + ((size_t)site * 9 + d) * A_TILE, A_TILE, full0 + 8 * s);
-                bulk_g2s(sa + A_TILE, Phi + (size_t)nb * b_tile, b_tile, full0 + 8 * s);
+                bulk_g2s(sa, Abf + ((size_t)site * a.links_per_site + q) * A_TILE, A_TILE, full0 + 8 * s);
+                bulk_g2s(sa + A_TILE, Phi + (size_t)pin * b_tile, b_tile, full0 + 8 * s);
                 ++issued;
             }
             const int e = step - (STAGES - 1);
-            if (e >= 0 && e < 9) {
+            if (e >= 0 && e < ndir) {
                 const int s = e % STAGES;
                 ok = mbar_wait_n(full0 + 8 * s, (e / STAGES) & 1, e == 0 ? a.first_limit : SPIN_LIMIT);
                 if (!ok) break;
@@ -179,7 +198,7 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ A
             const float sc = ls * col_scale[r];
             float re = sc * (Ds[K * ld + r] - Ds[(NC + K) * ld + n + r]);
             float im = sc * (Ds[(NC + K) * ld + r] + Ds[K * ld + n + r]);
-            const int64_t o = site * (int64_t)(NC * n) + idx;
+            const int64_t o = cta * (int64_t)(NC * n) + idx;
             if (y) {
                 const float2 yy = y[o];
                 re = yy.x - re;
@@ -246,13 +265,13 @@ __global__ void k_pack_phi(const float2 *__restrict__ phi, uint8_t *__restrict__
     for (int i = tid; i < words; i += blockDim.x) dst[i] = tile4[i];
 }
 
-// per-site scale of the links: max over the 9 blocks of max(|Re|, |Im|)
-__global__ void k_link_scale(const float2 *__restrict__ A, float *__restrict__ scale) {
+// per-site scale of the links: max over the site's `tps` blocks of max(|Re|, |Im|)
+__global__ void k_link_scale(const float2 *__restrict__ A, float *__restrict__ scale, int tps) {
     __shared__ float red[32];
     const int64_t site = blockIdx.x;
-    const float2 *a = A + site * 9 * NC * NC;
+    const float2 *a = A + site * tps * NC * NC;
     float m = 0.f;
-    for (int i = threadIdx.x; i < 9 * NC * NC; i += blockDim.x) {
+    for (int i = threadIdx.x; i < tps * NC * NC; i += blockDim.x) {
         const float2 v = a[i];
         m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
     }
@@ -266,17 +285,17 @@ __global__ void k_link_scale(const float2 *__restrict__ A, float *__restrict__ s
     }
 }
 
-// links [V][9][64][64] complex FP32 -> [V][9] swizzled 16-bit tiles of [Re A ; Im A] / scale (128 x 64)
+// links [V][tps][64][64] complex FP32 -> [V][tps] swizzled 16-bit tiles of [Re A ; Im A] / scale (128 x 64)
 template <int FMT>
 __global__ void k_pack_links(const float2 *__restrict__ A, uint8_t *__restrict__ img, int64_t V,
-                             const float *__restrict__ scale) {
+                             const float *__restrict__ scale, int tps) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= V * 9 * MROWS * NC) return;
+    if (i >= V * tps * MROWS * NC) return;
     const int64_t tile = i / (MROWS * NC);
     const int rem = (int)(i - tile * MROWS * NC);
     const int m = rem / NC, k = rem - m * NC;
     const float2 v = A[(tile * NC + (m % NC)) * NC + k];
-    const float s = scale[tile / 9];
+    const float s = scale[tile / tps];
     *reinterpret_cast<uint16_t *>(img + tile * (int64_t)A_TILE + sw128_offset(m, k)) = to16<FMT>((m < NC ? v.x : v.y) / s);
 }
 
@@ -301,35 +320,43 @@ void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s) {
     c.LinkScale.alloc(sizeof(float) * (size_t)c.V);
     c.ColScale.alloc(sizeof(float) * 64);
     MRHS_CUDA(cudaMemsetAsync(c.TcErr.ptr, 0, sizeof(int), s));
-    k_link_scale<<<(unsigned)c.V, 256, 0, s>>>(c.A32.as<float2>(), c.LinkScale.as<float>());
+    k_link_scale<<<(unsigned)c.V, 256, 0, s>>>(c.A32.as<float2>(), c.LinkScale.as<float>(), 9);
     MRHS_LAUNCHED("k_link_scale");
     const int64_t count = c.V * 9 * MROWS * NC;
     if (fmt == MRHS_FP16)
         k_pack_links<0><<<ceil_div(count, 256), 256, 0, s>>>(c.A32.as<float2>(), c.Abf.as<uint8_t>(), c.V,
-                                                             c.LinkScale.as<float>());
+                                                             c.LinkScale.as<float>(), 9);
     else
         k_pack_links<1><<<ceil_div(count, 256), 256, 0, s>>>(c.A32.as<float2>(), c.Abf.as<uint8_t>(), c.V,
-                                                             c.LinkScale.as<float>());
+                                                             c.LinkScale.as<float>(), 9);
     MRHS_LAUNCHED("k_pack_links");
 }
 
-void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const float2 *y, int n, cudaStream_t s) {
+// The tensor-core stencil in general form: out (n RHS, nc = 64) at the output
+// sites of `parity` (every site for parity < 0) = sum over directions
+// d_first..d_last of the link tiles `links` (links_per_site per site, scaled
+// per site by link_scale) times the input at the site's neighbours (or y minus
+// that).  `in` holds in_sites sites: the whole lattice for parity < 0, else the
+// half field whose sites are the neighbours' parity.
+void coarse_tc_general(const Level &c, const uint8_t *links, const float *link_scale, int links_per_site,
+                       int d_first, int d_last, int parity, const float2 *in, int64_t in_sites, float2 *out,
+                       const float2 *y, int n, cudaStream_t s) {
     if (!c.Abf.ptr) fail(MRHS_ERR_INVALID, "16-bit links not prepared");
     if (n < 1 || n > 64) fail(MRHS_ERR_INVALID, "tensor-core coarse stencil supports 1..64 RHS");
     const int npad = npad_of(n);
     MRHS_CUDA(cudaMemsetAsync(c.ColScale.ptr, 0, sizeof(float) * 64, s));
-    const int64_t rows = c.V * NC;
+    const int64_t rows = in_sites * NC;
     const int rpb = 256 / n;
     const int ablocks = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(0) * 4, ceil_div(rows, 8LL * rpb)));
     k_col_absmax<<<ablocks, 256, 0, s>>>(in, rows, n, c.ColScale.as<unsigned>());
     MRHS_LAUNCHED("k_col_absmax");
     const size_t tile_bytes = (size_t)npad * 128;
     if (c.tc_fmt == MRHS_FP16)
-        k_pack_phi<0><<<(unsigned)c.V, 256, tile_bytes, s>>>(in, c.PhiBf.as<uint8_t>(), n, npad,
-                                                             c.ColScale.as<float>());
+        k_pack_phi<0><<<(unsigned)in_sites, 256, tile_bytes, s>>>(in, c.PhiBf.as<uint8_t>(), n, npad,
+                                                                  c.ColScale.as<float>());
     else
-        k_pack_phi<1><<<(unsigned)c.V, 256, tile_bytes, s>>>(in, c.PhiBf.as<uint8_t>(), n, npad,
-                                                             c.ColScale.as<float>());
+        k_pack_phi<1><<<(unsigned)in_sites, 256, tile_bytes, s>>>(in, c.PhiBf.as<uint8_t>(), n, npad,
+                                                                  c.ColScale.as<float>());
     MRHS_LAUNCHED("k_pack_phi");
     TcArgs a;
     for (int mu = 0; mu < 4; ++mu) a.L[mu] = c.L[mu];
@@ -339,6 +366,10 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
     a.idesc = idesc_16bit(MROWS, npad, c.tc_fmt == MRHS_FP16 ? 0u : 1u);
     a.tmem_cols = npad <= 32 ? 32 : (npad <= 64 ? 64 : 128);
     a.first_limit = SPIN_LIMIT;
+    a.d_first = d_first;
+    a.d_last = d_last;
+    a.links_per_site = links_per_site;
+    a.parity = parity;
     {
         // a launch recorded into a graph would keep the expired limit for every replay: only eager launches
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -359,12 +390,13 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
                                        (int)tc_smem_bytes(128, 4)));
         attr = true;
     }
+    const int64_t out_sites = parity < 0 ? c.V : c.V / 2;
     auto launch = [&](int v) {
         const int stages = kStageVariants[v];
         const size_t smem = tc_smem_bytes(npad, stages);
         auto go = [&](auto kern) {
-            kern<<<(unsigned)c.V, 128, smem, s>>>(c.Abf.as<uint8_t>(), c.PhiBf.as<uint8_t>(), out, y, a,
-                                                   c.LinkScale.as<float>(), c.ColScale.as<float>(), c.TcErr.as<int>());
+            kern<<<(unsigned)out_sites, 128, smem, s>>>(links, c.PhiBf.as<uint8_t>(), out, y, a, link_scale,
+                                                        c.ColScale.as<float>(), c.TcErr.as<int>());
         };
         if (stages == 2) go(k_coarse_tc<2>);
         else if (stages == 4) go(k_coarse_tc<4>);
@@ -372,12 +404,210 @@ void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const floa
         MRHS_CUDA(cudaGetLastError());
     };
     // an output that aliases an input would not survive repeated launches; an expiring
-    // wait must happen in the launch that is not repeated: no tuning then
+    // wait must happen in the launch that is not repeated: no tuning then.  The tuner
+    // key holds the level's extents; the even-odd forms tune under their own names.
     const bool alias = (const void *)out == (const void *)in || (y && (const void *)out == (const void *)y);
-    const int v = (alias || a.first_limit == 0) ? 0 : tune_pick("k_coarse_tc", c.L, n, 3, launch, s);
+    static const char *names[] = {"k_coarse_tc", "k_coarse_tc_eo_hop", "k_coarse_tc_eo_self"};
+    const char *name = parity < 0 ? names[0] : (d_first > 0 ? names[1] : names[2]);
+    const int v = (alias || a.first_limit == 0) ? 0 : tune_pick(name, c.L, n, 3, launch, s);
     MRHS_TIMED("k_coarse_tc", s);
     launch(v);
     MRHS_LAUNCHED("k_coarse_tc");
+}
+
+void coarse_apply_bf16(const Level &c, const float2 *in, float2 *out, const float2 *y, int n, cudaStream_t s) {
+    if (!c.Abf.ptr) fail(MRHS_ERR_INVALID, "16-bit links not prepared");
+    coarse_tc_general(c, c.Abf.as<uint8_t>(), c.LinkScale.as<float>(), 9, 0, 8, -1, in, c.V, out, y, n, s);
+}
+
+// ------------------------------------------- coarse even-odd (Sec. 6, M_eooe)
+namespace {
+
+// Inverse of the self block A_0(x) of every coarse site: Gauss-Jordan with
+// partial pivoting in FP64 on [A_0 | 1] in shared memory (64 x 128 complex), one
+// CTA per site; a pivot below 1e-300 (singular block) sets *singular.
+__global__ void __launch_bounds__(256) k_self_inverse(const float2 *__restrict__ A, float2 *__restrict__ inv,
+                                                      int *__restrict__ singular) {
+    extern __shared__ double2 M[];  // [64][128]
+    __shared__ double2 fac[NC];
+    __shared__ int piv_sh;
+    __shared__ double best_sh;
+    const int64_t site = blockIdx.x;
+    const float2 *a0 = A + site * 9 * NC * NC;  // direction 0
+    for (int e = threadIdx.x; e < NC * 2 * NC; e += blockDim.x) {
+        const int r = e / (2 * NC), j = e - r * 2 * NC;
+        if (j < NC) {
+            const float2 v = a0[r * NC + j];
+            M[e] = make_double2(v.x, v.y);
+        } else {
+            M[e] = make_double2(j - NC == r ? 1.0 : 0.0, 0.0);
+        }
+    }
+    __syncthreads();
+    for (int col = 0; col < NC; ++col) {
+        if (threadIdx.x == 0) {
+            int piv = col;
+            double best = -1.0;
+            for (int r = col; r < NC; ++r) {
+                const double2 v = M[r * 2 * NC + col];
+                const double m = v.x * v.x + v.y * v.y;
+                if (m > best) {
+                    best = m;
+                    piv = r;
+                }
+            }
+            piv_sh = piv;
+            best_sh = best;
+            if (!(best > 1e-300)) atomicExch(singular, 1);
+        }
+        __syncthreads();
+        if (!(best_sh > 1e-300)) return;
+        const int piv = piv_sh;
+        if (piv != col)
+            for (int j = threadIdx.x; j < 2 * NC; j += blockDim.x) {
+                const double2 t = M[col * 2 * NC + j];
+                M[col * 2 * NC + j] = M[piv * 2 * NC + j];
+                M[piv * 2 * NC + j] = t;
+            }
+        __syncthreads();
+        const double2 p = M[col * 2 * NC + col];
+        const double pm = p.x * p.x + p.y * p.y;
+        const double2 pinv = make_double2(p.x / pm, -p.y / pm);
+        __syncthreads();
+        for (int j = threadIdx.x; j < 2 * NC; j += blockDim.x) {
+            const double2 v = M[col * 2 * NC + j];
+            M[col * 2 * NC + j] = make_double2(v.x * pinv.x - v.y * pinv.y, v.x * pinv.y + v.y * pinv.x);
+        }
+        __syncthreads();
+        if (threadIdx.x < NC) fac[threadIdx.x] = M[threadIdx.x * 2 * NC + col];
+        __syncthreads();
+        for (int e = threadIdx.x; e < NC * 2 * NC; e += blockDim.x) {
+            const int r = e / (2 * NC), j = e - r * 2 * NC;
+            if (r == col) continue;
+            const double2 f = fac[r], u = M[col * 2 * NC + j];
+            double2 v = M[e];
+            v.x -= f.x * u.x - f.y * u.y;
+            v.y -= f.x * u.y + f.y * u.x;
+            M[e] = v;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < NC * NC; e += blockDim.x) {
+        const int r = e / NC, j = e - r * NC;
+        const double2 v = M[r * 2 * NC + NC + j];
+        inv[site * NC * NC + e] = make_float2((float)v.x, (float)v.y);
+    }
+}
+
+// parity split / merge of coarse fields [V][64][n]: half p holds the sites of parity p, site s at s / 2
+__global__ void k_parity_split(const float2 *__restrict__ full, float2 *__restrict__ he, float2 *__restrict__ ho,
+                               TcArgs a) {
+    const int64_t per = (int64_t)NC * a.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.V * per) return;
+    const int64_t site = i / per, e = i - site * per;
+    int c[4];
+    site_to_coords(site, a.L, c);
+    float2 *dst = ((c[0] + c[1] + c[2] + c[3]) & 1) ? ho : he;
+    dst[(site >> 1) * per + e] = full[i];
+}
+
+__global__ void k_parity_merge_add(const float2 *__restrict__ he, const float2 *__restrict__ ho,
+                                   float2 *__restrict__ full, TcArgs a) {
+    const int64_t per = (int64_t)NC * a.n;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.V * per) return;
+    const int64_t site = i / per, e = i - site * per;
+    int c[4];
+    site_to_coords(site, a.L, c);
+    const float2 *src = ((c[0] + c[1] + c[2] + c[3]) & 1) ? ho : he;
+    const float2 d = src[(site >> 1) * per + e];
+    float2 z = full[i];
+    z.x += d.x;
+    z.y += d.y;
+    full[i] = z;
+}
+
+}  // namespace
+
+bool coarse_eo_supported(const Level &c) {
+    if (!c.Abf.ptr) return false;
+    for (int mu = 0; mu < 4; ++mu)
+        if (c.L[mu] % 2) return false;
+    return true;
+}
+
+void coarse_eo_prepare(Level &c, cudaStream_t s) {
+    if (!coarse_eo_supported(c)) fail(MRHS_ERR_INVALID, "coarse even-odd needs 16-bit links and even coarse extents");
+    DeviceBuffer inv(sizeof(float2) * (size_t)c.V * NC * NC);
+    c.EoErr.alloc(sizeof(int));
+    MRHS_CUDA(cudaMemsetAsync(c.EoErr.ptr, 0, sizeof(int), s));
+    const size_t smem = sizeof(double2) * NC * 2 * NC;
+    MRHS_CUDA(cudaFuncSetAttribute(k_self_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_self_inverse<<<(unsigned)c.V, 256, smem, s>>>(c.A32.as<float2>(), inv.as<float2>(), c.EoErr.as<int>());
+    MRHS_LAUNCHED("k_self_inverse");
+    c.AinvScale.alloc(sizeof(float) * (size_t)c.V);
+    c.AinvBf.alloc((size_t)c.V * A_TILE);
+    k_link_scale<<<(unsigned)c.V, 256, 0, s>>>(inv.as<float2>(), c.AinvScale.as<float>(), 1);
+    MRHS_LAUNCHED("k_link_scale");
+    const int64_t count = c.V * MROWS * NC;
+    if (c.tc_fmt == MRHS_FP16)
+        k_pack_links<0><<<ceil_div(count, 256), 256, 0, s>>>(inv.as<float2>(), c.AinvBf.as<uint8_t>(), c.V,
+                                                             c.AinvScale.as<float>(), 1);
+    else
+        k_pack_links<1><<<ceil_div(count, 256), 256, 0, s>>>(inv.as<float2>(), c.AinvBf.as<uint8_t>(), c.V,
+                                                             c.AinvScale.as<float>(), 1);
+    MRHS_LAUNCHED("k_pack_links");
+    int sing = 0;
+    MRHS_CUDA(cudaMemcpyAsync(&sing, c.EoErr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MRHS_CUDA(cudaStreamSynchronize(s));
+    if (sing) fail(MRHS_ERR_INVALID, "a coarse self block is singular: no coarse even-odd inverse");
+}
+
+void coarse_eo_hop(const Level &c, int out_parity, const float2 *in_half, float2 *out_half, const float2 *y_half,
+                   int n, cudaStream_t s) {
+    coarse_tc_general(c, c.Abf.as<uint8_t>() + A_TILE, c.LinkScale.as<float>(), 9, 1, 8, out_parity, in_half,
+                      c.V / 2, out_half, y_half, n, s);
+}
+
+void coarse_eo_self(const Level &c, bool inverse, int parity, const float2 *in_half, float2 *out_half, int n,
+                    cudaStream_t s) {
+    if (inverse) {
+        if (!c.AinvBf.ptr) fail(MRHS_ERR_INVALID, "coarse even-odd inverse not prepared");
+        coarse_tc_general(c, c.AinvBf.as<uint8_t>(), c.AinvScale.as<float>(), 1, 0, 0, parity, in_half, c.V / 2,
+                          out_half, nullptr, n, s);
+    } else {
+        coarse_tc_general(c, c.Abf.as<uint8_t>(), c.LinkScale.as<float>(), 9, 0, 0, parity, in_half, c.V / 2,
+                          out_half, nullptr, n, s);
+    }
+}
+
+void coarse_schur_apply(const Level &c, const float2 *in_o, float2 *out_o, float2 *tmp_e1, float2 *tmp_e2, int n,
+                        cudaStream_t s) {
+    // t = A_ee^-1 H_eo in_o;  out_o = A_oo in_o - H_oe t
+    coarse_eo_hop(c, 0, in_o, tmp_e1, nullptr, n, s);
+    coarse_eo_self(c, true, 0, tmp_e1, tmp_e2, n, s);
+    coarse_eo_self(c, false, 1, in_o, out_o, n, s);
+    coarse_eo_hop(c, 1, tmp_e2, out_o, out_o, n, s);
+}
+
+void coarse_parity_split(const Level &c, const float2 *full, float2 *he, float2 *ho, int n, cudaStream_t s) {
+    TcArgs a{};
+    for (int mu = 0; mu < 4; ++mu) a.L[mu] = c.L[mu];
+    a.V = c.V;
+    a.n = n;
+    k_parity_split<<<ceil_div(c.V * NC * n, 256), 256, 0, s>>>(full, he, ho, a);
+    MRHS_LAUNCHED("k_parity_split");
+}
+
+void coarse_parity_merge_add(const Level &c, const float2 *he, const float2 *ho, float2 *full, int n,
+                             cudaStream_t s) {
+    TcArgs a{};
+    for (int mu = 0; mu < 4; ++mu) a.L[mu] = c.L[mu];
+    a.V = c.V;
+    a.n = n;
+    k_parity_merge_add<<<ceil_div(c.V * NC * n, 256), 256, 0, s>>>(he, ho, full, a);
+    MRHS_LAUNCHED("k_parity_merge_add");
 }
 
 int coarse_tc_error(const Level &c, cudaStream_t s) {

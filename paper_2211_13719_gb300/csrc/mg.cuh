@@ -35,6 +35,9 @@ struct Level {
     DeviceBuffer IgErr;      // int: set when a tensor-core transfer gave up waiting
     DeviceBuffer IgBound;    // float [2][64]: ones (unit-norm inputs), then the column maxima of the last input
     bool tc_intergrid = false;
+    // coarse even-odd decomposition (16-bit tensor-core levels with even extents):
+    // inverse self blocks A_0(x)^-1 as 16-bit tiles [V] with a per-site scale
+    DeviceBuffer AinvBf, AinvScale, EoErr;
     int64_t rows() const { return V * dof; }
 };
 
@@ -61,6 +64,23 @@ bool coarse_bf16_supported(const Level &c);
 // flag after the work queued on s, synchronising s)
 int coarse_tc_error(const Level &c, cudaStream_t s);
 void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s);
+// Coarse even-odd decomposition (Sec. 6, M_eooe) on 16-bit tensor-core levels with
+// even extents; half fields [V/2][64][n] hold the sites of one parity (site s at s / 2).
+bool coarse_eo_supported(const Level &c);
+// inverts every self block A_0(x) (FP64 Gauss-Jordan) and stores it as 16-bit tiles
+void coarse_eo_prepare(Level &c, cudaStream_t s);
+// out = H in (or y - H in): the 8 hop terms onto the sites of out_parity
+void coarse_eo_hop(const Level &c, int out_parity, const float2 *in_half, float2 *out_half, const float2 *y_half,
+                   int n, cudaStream_t s);
+// out = A_0 in or A_0^-1 in on the sites of `parity`
+void coarse_eo_self(const Level &c, bool inverse, int parity, const float2 *in_half, float2 *out_half, int n,
+                    cudaStream_t s);
+// out_o = D_hat in_o = A_oo in_o - H_oe A_ee^-1 H_eo in_o; tmp_e1, tmp_e2: even half fields
+void coarse_schur_apply(const Level &c, const float2 *in_o, float2 *out_o, float2 *tmp_e1, float2 *tmp_e2, int n,
+                        cudaStream_t s);
+void coarse_parity_split(const Level &c, const float2 *full, float2 *he, float2 *ho, int n, cudaStream_t s);
+void coarse_parity_merge_add(const Level &c, const float2 *he, const float2 *ho, float2 *full, int n,
+                             cudaStream_t s);
 // tensor-core restriction / prolongation (FP16, <= 32 null vectors, <= 64 RHS)
 bool intergrid_tc_supported(const Level &f);
 void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s);

@@ -97,6 +97,26 @@ struct SchurOp : Op {
     }
 };
 
+// D_hat = A_oo - H_oe A_ee^-1 H_eo on the odd half fields of a coarse level
+// (the coarse even-odd Schur complement, tensor cores); t1, t2: even half scratch
+struct CoarseSchurOp : Op {
+    const Level *lev;
+    DeviceBuffer t1, t2;
+    CoarseSchurOp(const Level *l, int nmax) : lev(l) {
+        rows = l->V / 2 * l->dof;
+        t1.alloc(sizeof(float2) * (size_t)rows * nmax);
+        t2.alloc(sizeof(float2) * (size_t)rows * nmax);
+    }
+    void apply(const float2 *in, float2 *out, int n, cudaStream_t s) override {
+        coarse_schur_apply(*lev, in, out, t1.as<float2>(), t2.as<float2>(), n, s);
+    }
+    void residual(const float2 *x, const float2 *b, float2 *r, int n, cudaStream_t s) override {
+        apply(x, r, n, s);
+        scale_real(MRHS_FP32, -1.0, r, rows * n, s);
+        axpy(MRHS_FP32, 1.0, b, r, rows * n, s);
+    }
+};
+
 struct Precond {
     virtual ~Precond() = default;
     virtual void apply(const float2 *v, float2 *z, int n, cudaStream_t s) = 0;
@@ -195,6 +215,11 @@ struct LevelWork {
     DeviceBuffer eo_r, eo_re, eo_ro, eo_te, eo_bh, eo_de, eo_do;
     KWork eo_smooth;
     DeviceBuffer sap_r;  // fine level, SAP smoother: its residual field
+    // intermediate coarse levels, even-odd smoother: residual, its halves, A_ee^-1 r_e,
+    // b_hat, the corrections and GMRES on the coarse Schur complement
+    DeviceBuffer ceo_r, ceo_re, ceo_ro, ceo_te, ceo_bh, ceo_de, ceo_do;
+    KWork ceo_smooth;
+    std::unique_ptr<CoarseSchurOp> ceo_op;
 };
 
 struct GraphKey {
@@ -330,6 +355,20 @@ void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t 
                          W.eo_smooth, s, true, nullptr);
             eo_axpy_hop(*mg.lat, 0, W.eo_re.ptr, W.eo_do.ptr, W.eo_de.ptr, true, n, s);
             eo_merge_add(*mg.lat, W.eo_de.ptr, W.eo_do.ptr, z, n, s);
+        } else if (l > 0 && mg.work[l].ceo_op) {
+            // coarse even-odd smoother: z += delta, delta from smooth_m GMRES steps on
+            // D_hat delta_o = b_hat = r_o - H_oe A_ee^-1 r_e (r = v - A z), then
+            // delta_e = A_ee^-1 (r_e - H_eo delta_o)
+            LevelWork &W = mg.work[l];
+            mg.ops[l]->residual(z, v, W.ceo_r.as<float2>(), n, s);
+            coarse_parity_split(F, W.ceo_r.as<float2>(), W.ceo_re.as<float2>(), W.ceo_ro.as<float2>(), n, s);
+            coarse_eo_self(F, true, 0, W.ceo_re.as<float2>(), W.ceo_te.as<float2>(), n, s);
+            coarse_eo_hop(F, 1, W.ceo_te.as<float2>(), W.ceo_bh.as<float2>(), W.ceo_ro.as<float2>(), n, s);
+            krylov_cycle(*W.ceo_op, nullptr, W.ceo_bh.as<float2>(), W.ceo_do.as<float2>(), n, mg.p.smooth_m,
+                         W.ceo_smooth, s, true, nullptr);
+            coarse_eo_hop(F, 0, W.ceo_do.as<float2>(), W.ceo_te.as<float2>(), W.ceo_re.as<float2>(), n, s);
+            coarse_eo_self(F, true, 0, W.ceo_te.as<float2>(), W.ceo_de.as<float2>(), n, s);
+            coarse_parity_merge_add(F, W.ceo_de.as<float2>(), W.ceo_do.as<float2>(), z, n, s);
         } else {
             krylov_cycle(*mg.ops[l], nullptr, v, z, n, mg.p.smooth_m, mg.work[l].smooth, s, false, nullptr);
         }
@@ -440,6 +479,8 @@ void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
     if (p.smoother_sap != 0 && p.smoother_sap != 1) fail(MRHS_ERR_INVALID, "smoother_sap must be 0 or 1");
     if (p.smoother_sap && (p.sap_cycles < 1 || p.sap_cycles > 16 || p.sap_mr < 1 || p.sap_mr > 64))
         fail(MRHS_ERR_INVALID, "sap_cycles must be in 1..16 and sap_mr in 1..64");
+    if (p.coarse_smoother_evenodd != 0 && p.coarse_smoother_evenodd != 1)
+        fail(MRHS_ERR_INVALID, "coarse_smoother_evenodd must be 0 or 1");
     if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
 }
 
@@ -521,6 +562,17 @@ void alloc_workspace(mrhs_mg &mg) {
     }
     if (mg.p.smoother_sap && sap_supported(*mg.lat, mg.p.sap_block, 2))
         mg.work[0].sap_r.alloc(sizeof(float2) * (size_t)mg.lev[0].rows() * nmax);
+    // coarse even-odd smoother on the intermediate levels that have the inverse self blocks
+    for (int l = 1; l + 1 < mg.nlev; ++l) {
+        Level &L = mg.lev[l];
+        if (!L.AinvBf.ptr) continue;
+        LevelWork &W = mg.work[l];
+        const size_t half = sizeof(float2) * (size_t)(L.V / 2) * L.dof * nmax;
+        W.ceo_r.alloc(2 * half);
+        for (DeviceBuffer *b : {&W.ceo_re, &W.ceo_ro, &W.ceo_te, &W.ceo_bh, &W.ceo_de, &W.ceo_do}) b->alloc(half);
+        W.ceo_smooth.init(mg.p.smooth_m, L.V / 2 * L.dof, nmax, false);
+        W.ceo_op.reset(new CoarseSchurOp(&L, nmax));
+    }
     const int64_t rows = mg.lev[0].rows();
     mg.inner.init(mg.p.inner_m, rows, nmax, true);
     mg.inner_b.alloc(sizeof(float2) * (size_t)rows * nmax);
@@ -806,6 +858,9 @@ mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_
             const bool use_tc = (params->coarse_precision == MRHS_BF16 || params->coarse_precision == MRHS_FP16) &&
                                 coarse_bf16_supported(C);
             if (use_tc) coarse_links_to_16bit(C, (mrhs_precision)params->coarse_precision, s);
+            // coarse even-odd smoother: intermediate levels (those that post-smooth) only
+            if (use_tc && params->coarse_smoother_evenodd && l + 2 < mg->nlev && coarse_eo_supported(C))
+                coarse_eo_prepare(C, s);
             // 16-bit hierarchies also move fields between levels on the tensor cores
             Level &F = mg->lev[l];
             if ((params->coarse_precision == MRHS_BF16 || params->coarse_precision == MRHS_FP16) &&
@@ -934,6 +989,27 @@ mrhs_status mrhs_coarse_apply(mrhs_mg *mg, int level, const void *in_dev, void *
     } else {
         fail(MRHS_ERR_INVALID, "links precision must be FP32 or BF16");
     }
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_coarse_apply_schur(mrhs_mg *mg, int level, const void *in_dev, void *out_dev, int nrhs,
+                                    void *stream) {
+    API_TRY
+    check_level(mg, level, 1, mg ? mg->nlev - 1 : 1);
+    if (nrhs < 1 || nrhs > 64) fail(MRHS_ERR_INVALID, "nrhs must be in 1..64");
+    if (!in_dev || !out_dev || in_dev == out_dev) fail(MRHS_ERR_INVALID, "distinct non-null fields required");
+    DevGuard dg(mg->lat->device);
+    const Level &C = mg->lev[level];
+    if (!C.AinvBf.ptr)
+        fail(MRHS_ERR_INVALID, "no coarse even-odd decomposition on this level (needs coarse_smoother_evenodd, "
+                               "16-bit links and even coarse extents on an intermediate level)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t half = sizeof(float2) * (size_t)(C.V / 2) * C.dof * nrhs;
+    DeviceBuffer t1(half), t2(half);
+    coarse_schur_apply(C, static_cast<const float2 *>(in_dev), static_cast<float2 *>(out_dev), t1.as<float2>(),
+                       t2.as<float2>(), nrhs, s);
+    check_wait_flags(C, s);
     return ok();
     API_CATCH
 }

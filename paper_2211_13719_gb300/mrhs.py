@@ -71,6 +71,7 @@ class MgParams(C.Structure):
         ("sap_block", C.c_int * 4),
         ("sap_cycles", C.c_int),
         ("sap_mr", C.c_int),
+        ("coarse_smoother_evenodd", C.c_int),
     ]
 
 
@@ -161,6 +162,7 @@ PROTOTYPES = {
     "mrhs_prolong": (_I, [_P, _I, _P, _P, _I, _P]),
     "mrhs_coarse_apply": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "mrhs_vcycle": (_I, [_P, _P, _P, _I, _P]),
+    "mrhs_coarse_apply_schur": (_I, [_P, _I, _P, _P, _I, _P]),
     "mrhs_debug_expire_waits": (_I, [_I]),
     "mrhs_solve": (_I, [_P, _P, _P, _I, _D, _P, C.POINTER(SolveStats), _P]),
     "mrhs_server_create": (_I, [C.POINTER(ServerParams), C.POINTER(_P)]),
@@ -381,6 +383,10 @@ def mrhs_prolong(mg, level, coarse_dev, fine_dev, nrhs, stream=None):
 def mrhs_coarse_apply(mg, level, in_dev, out_dev, nrhs, links_prec=MRHS_FP32, stream=None):
     _check(lib().mrhs_coarse_apply(mg, int(level), _ptr(in_dev), _ptr(out_dev), int(nrhs), int(links_prec),
                                    _stream(stream)))
+
+
+def mrhs_coarse_apply_schur(mg, level, in_dev, out_dev, nrhs, stream=None):
+    _check(lib().mrhs_coarse_apply_schur(mg, int(level), _ptr(in_dev), _ptr(out_dev), int(nrhs), _stream(stream)))
 
 
 def mrhs_vcycle(mg, v_dev, z_dev, nrhs, stream=None):
