@@ -354,12 +354,15 @@ def make_params(mrhs, n_max, coarse_precision, use_graph, **over):
 
 
 def smoother_params(args):
-    """MG parameter overrides of the --smoother choice."""
+    """MG parameter overrides of the --smoother and --coarse-smoother choices."""
+    out = {}
     if args.smoother == "sap":
-        return dict(smoother_sap=1, smoother_evenodd=0, sap_mr=args.sap_mr, sap_cycles=args.sap_cycles)
-    if args.smoother == "gmres":
-        return dict(smoother_sap=0, smoother_evenodd=0)
-    return {}
+        out = dict(smoother_sap=1, smoother_evenodd=0, sap_mr=args.sap_mr, sap_cycles=args.sap_cycles)
+    elif args.smoother == "gmres":
+        out = dict(smoother_sap=0, smoother_evenodd=0)
+    if args.coarse_smoother == "evenodd":
+        out["coarse_smoother_evenodd"] = 1
+    return out
 
 
 def gauge_field(w):
@@ -696,6 +699,7 @@ def run_ours(args, rank, world, local_rank):
                        "mass": w["mass"], "csw": w["csw"], "parallelism": f"replicas x{world}",
                        "smoother": args.smoother + (f" (SAP {args.sap_cycles} cycle(s), {args.sap_mr} MR steps, "
                                                     f"4^4 blocks)" if args.smoother == "sap" else ""),
+                       "coarse_smoother": args.coarse_smoother,
                        "l2": "inputs larger than L2 (FP64 fields of 8 GB)"},
         }
         line.update(extra)
@@ -1067,6 +1071,9 @@ def main():
     ap.add_argument("--serve-loads", default="0.5,0.8,0.95", help="offered loads of --case serving")
     ap.add_argument("--smoother", default="evenodd", choices=["evenodd", "sap", "gmres"],
                     help="fine post-smoother: GMRES on the even-odd Schur complement (default), SAP, or GMRES on D")
+    ap.add_argument("--coarse-smoother", default="gmres", choices=["gmres", "evenodd"],
+                    help="intermediate-level post-smoother: GMRES on the level operator (default) or on its "
+                         "coarse even-odd Schur complement")
     ap.add_argument("--sap-mr", type=int, default=4)
     ap.add_argument("--sap-cycles", type=int, default=1)
     ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas",
