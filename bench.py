@@ -823,8 +823,17 @@ def run_batch_case(reps):
     from paper_2211_13719_gb300 import build as _build
     from paper_2211_13719_gb300 import mrhs
     _build.build()
-    mix = [((16, 16, 16, 32), 12), ((16, 16, 16, 32), 6), ((8, 8, 8, 16), 4), ((12, 12, 12, 24), 8),
-           ((16, 16, 16, 32), 2), ((8, 8, 8, 16), 12)]
+    mixes = {"serving-size": [((16, 16, 16, 32), 12), ((16, 16, 16, 32), 6), ((8, 8, 8, 16), 4),
+                              ((12, 12, 12, 24), 8), ((16, 16, 16, 32), 2), ((8, 8, 8, 16), 12)],
+             "small": [((8, 8, 8, 8), 4), ((8, 8, 8, 16), 2), ((4, 4, 4, 8), 8), ((8, 8, 8, 8), 12),
+                       ((6, 6, 6, 6), 6), ((8, 8, 8, 8), 2), ((4, 4, 8, 8), 16), ((6, 6, 6, 6), 4)]}
+    out = {"case": "batch", "mixes": []}
+    for name, mix in mixes.items():
+        out["mixes"].append(dict(name=name, **_batch_mix(mrhs, torch, synth, mix, reps)))
+    print(json.dumps(out), flush=True)
+
+
+def _batch_mix(mrhs, torch, synth, mix, reps):
     stream = torch.cuda.current_stream()
     lats, items, alg = {}, [], 0
     for dims, n in mix:
@@ -860,12 +869,12 @@ def run_batch_case(reps):
         return e0.elapsed_time(e1) / reps
 
     ms_sep, ms_fused = ev(separate), ev(fused)
-    out = {"case": "batch", "blocks": [[list(d), n] for d, n in mix], "alg_bytes": alg,
+    out = {"blocks": [[list(d), n] for d, n in mix], "alg_bytes": alg,
            "ms_separate_launches": ms_sep, "ms_fused_launch": ms_fused, "speedup": ms_sep / ms_fused,
            "alg_GBs_separate": alg / ms_sep / 1e6, "alg_GBs_fused": alg / ms_fused / 1e6}
     for lat in lats.values():
         mrhs.mrhs_destroy_lattice(lat)
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_c0_case(reps):

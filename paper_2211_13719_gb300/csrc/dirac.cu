@@ -618,6 +618,11 @@ struct BatchArgs {
 template <bool RESID>
 __device__ __forceinline__ void batch_site(const BatchItem &w, const int c[4], int r) {
     switch (w.a.n) {
+        case 2: dslash_r1_site<RESID, 2>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 4: dslash_r1_site<RESID, 4>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 6: dslash_r1_site<RESID, 6>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 8: dslash_r1_site<RESID, 8>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
+        case 12: dslash_r1_site<RESID, 12>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
         case 16: dslash_r1_site<RESID, 16>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
         case 24: dslash_r1_site<RESID, 24>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
         case 32: dslash_r1_site<RESID, 32>(w.U, w.C, w.in, w.out, w.y, w.a, c, r); break;
