@@ -306,6 +306,12 @@ typedef struct {
                                               even-odd Schur complement (16-bit
                                               tensor-core levels with even extents;
                                               otherwise GMRES on the level operator) */
+    int coarse_solver;                     /* coarsest level: 0 GMRES(coarse_m),
+                                              1 GCRO-DR(coarse_m, coarse_recycle)
+                                              with a recycle space kept per RHS
+                                              from one V-cycle to the next
+                                              (coarse_m <= 16)                    */
+    int coarse_recycle;                    /* GCRO-DR recycle vectors k < coarse_m */
 } mrhs_mg_params;
 
 /* Fill `p` with the defaults used for the 24^3x64 three-level workload. */
@@ -370,6 +376,18 @@ mrhs_status mrhs_coarse_apply(mrhs_mg *mg, int level, const void *in_dev, void *
  * on `stream` (it reads the kernels' bounded-wait flag). */
 mrhs_status mrhs_coarse_apply_schur(mrhs_mg *mg, int level, const void *in_dev, void *out_dev, int nrhs,
                                     void *stream);
+
+/* The coarsest level's solve as the V-cycle runs it: coarse_cycles cycles
+ * of GMRES(coarse_m), or of GCRO-DR(coarse_m, coarse_recycle) with
+ * coarse_solver = 1 (Sec. 9 outlook: a recycling coarsest solver), from
+ * x = 0, on FP32 coarsest-level fields [Vc][nc][nrhs].  GCRO-DR keeps one
+ * recycle space per RHS column in the hierarchy: a solve enters with the
+ * space the previous solve (or V-cycle) left, and mrhs_coarsest_reset
+ * drops it.  The per-RHS small dense work (least squares, harmonic Ritz
+ * eigenproblem, QR) runs in FP64 on the device.  Returns after the work on
+ * `stream`; MRHS_ERR_CUDA if a harmonic Ritz eigenproblem did not converge. */
+mrhs_status mrhs_coarsest_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, void *stream);
+mrhs_status mrhs_coarsest_reset(mrhs_mg *mg);
 
 /* One MG V-cycle z = M^{-1} v on the fine level (Sec. 8 preconditioner),
  * FP32 fields [V][12][nrhs]. */

@@ -94,6 +94,20 @@ void block_orthonormalize(const Level &f, double2 *vecs, cudaStream_t s);
 // P [V][dof][N] -> Pexp [V][dof][2N] with column K = chi*N + k nonzero only on chirality chi
 void expand_chiral(const Level &f, const float2 *P, float2 *Pexp, cudaStream_t s);
 
+// GCRO-DR small dense work per RHS (gcrodr.cu).  Per-RHS matrices are
+// [n][17][17] double2 (row-major, leading dimension 17), vectors [n][17].
+void gcro_store_col(double2 *H, const double2 *hcol, const double *hn2, const double *nn, int j, int row0, int n,
+                    cudaStream_t s);
+void gcro_put_col(double2 *M, const double2 *d, int cnt, int row0, int col, int n, cudaStream_t s);
+void gcro_put_vec(double2 *v, const double2 *d, int cnt, int off, int n, cudaStream_t s);
+void gcro_put_norm(double *un2, const double *nrm2, int i, int n, cudaStream_t s);
+void gcro_seed_small(const double2 *H, const double *beta2, int m, int k, double2 *Y, double2 *QC, double2 *PU,
+                     int *err, int n, cudaStream_t s);
+void gcro_cycle_small(const double2 *H, const double2 *B, const double *UN2, const double2 *WR, const double2 *WU,
+                      int m, int k, double2 *Y, double2 *QC, double2 *PU, int *err, int n, cudaStream_t s);
+void gcro_coef_vec(double2 *coef, const double2 *v, int off, int cnt, double sign, int n, cudaStream_t s);
+void gcro_coef_col(double2 *coef, const double2 *M, int off, int cnt, int col, double sign, int n, cudaStream_t s);
+
 // Solver entry used by the C ABI and the server (solver.cu).
 bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *tols, double *rel_out,
               mrhs_solve_stats *st, cudaStream_t s, int max_outer,

@@ -205,6 +205,175 @@ int krylov_cycle(Op &A, Precond *M, const float2 *b, float2 *x, int n, int m, KW
     return steps;
 }
 
+// ------------------------------------------------ GCRO-DR (coarsest level)
+// GCRO with deflated restarting (Sec. 9 outlook names it for the coarsest
+// level), per RHS, every cycle from the true residual; the recycle space (U,
+// C = A U, k vectors per RHS) carries over from one coarsest solve (one
+// V-cycle) to the next.  Fields are FP32 and batched over the RHS; the small
+// dense work runs per RHS in FP64 on the device (gcrodr.cu).  Readings:
+// the residual entering a cycle is orthogonal to C up to rounding (GCRO-DR
+// keeps it so), hence W^H V_p = [0; I] is used for the Arnoldi columns of
+// W^H V^, while W^H U and W^H r are formed as inner products.
+struct GcroWork {
+    int m = 0, k = 0, nmax = 0;
+    int64_t rows = 0;
+    bool has_recycle = false;
+    DeviceBuffer V, U, C, U2, C2, AU, r;           // fields [rows][n]
+    DeviceBuffer H, B, WU, QC, PU;                 // per RHS [n][17][17] double2
+    DeviceBuffer WR, Y, UN2;                       // per RHS [n][17] (UN2 double)
+    DeviceBuffer dots, coef, nrm2, hn2, nn, beta2, rin2, err;
+    Scratch sc;
+    void init(int m_, int k_, int64_t rows_, int nmax_) {
+        m = m_;
+        k = k_;
+        rows = rows_;
+        nmax = nmax_;
+        const size_t f = sizeof(float2) * (size_t)rows * nmax;
+        V.alloc(f * (m + 1));
+        r.alloc(f);
+        if (k > 0) {
+            U.alloc(f * k);
+            C.alloc(f * k);
+            U2.alloc(f * k);
+            C2.alloc(f * k);
+            AU.alloc(f * k);
+        }
+        const size_t mat = sizeof(double2) * (size_t)nmax * 17 * 17, vec = sizeof(double2) * (size_t)nmax * 17;
+        H.alloc(mat);
+        B.alloc(mat);
+        WU.alloc(mat);
+        QC.alloc(mat);
+        PU.alloc(mat);
+        WR.alloc(vec);
+        Y.alloc(vec);
+        UN2.alloc(sizeof(double) * (size_t)nmax * 17);
+        dots.alloc(sizeof(double2) * (size_t)(m + 1) * nmax);
+        coef.alloc(sizeof(double2) * (size_t)(m + 1) * nmax);
+        for (DeviceBuffer *b : {&nrm2, &hn2, &nn, &beta2, &rin2}) b->alloc(sizeof(double) * nmax * 17);
+        err.alloc(sizeof(int));
+        MRHS_CUDA(cudaMemset(err.ptr, 0, sizeof(int)));
+        MRHS_CUDA(cudaMemset(H.ptr, 0, mat));
+        MRHS_CUDA(cudaMemset(B.ptr, 0, mat));
+        sc.ensure(current_sm_count() * 8, KCHUNK * nmax);
+    }
+    float2 *fld(const DeviceBuffer &b, int i, int n) const { return b.as<float2>() + (size_t)i * rows * n; }
+};
+
+// One Arnoldi step on field j+1 = A field j against fields 0..j of `V`, storing column j of the
+// per-RHS Hessenberg (rows row0..row0+j+1); with C (k > 0), first w -= C (C^H w), B column j.
+void gcro_arnoldi_step(Op &A, GcroWork &g, int j, int row0, bool project, int n, cudaStream_t s) {
+    float2 *vj = g.fld(g.V, j, n), *w = g.fld(g.V, j + 1, n);
+    const int64_t F = g.rows * n;
+    A.apply(vj, w, n, s);
+    if (project) {
+        multi_dot(MRHS_FP32, g.C.ptr, F, g.k, w, g.rows, n, g.dots.as<double2>(), g.sc, s);
+        gcro_put_col(g.B.as<double2>(), g.dots.as<double2>(), g.k, 0, j, n, s);
+        lincomb(MRHS_FP32, w, MRHS_FP32, g.C.ptr, F, g.k, g.dots.as<double2>(), -1.0, g.rows, n, s);
+    }
+    orthonormalize_step(MRHS_FP32, g.V.ptr, F, j + 1, w, g.rows, n, g.dots.as<double2>(), g.nrm2.as<double>(),
+                        g.hn2.as<double>(), g.nn.as<double>(), g.sc, s);
+    gcro_store_col(g.H.as<double2>(), g.dots.as<double2>(), g.hn2.as<double>(), g.nn.as<double>(), j, row0, n, s);
+}
+
+// out_i = sum_j coef_i[j] basis_j for the k outputs, out fields zeroed first; coefficients from column i
+// of the per-RHS matrix M (rows off..off+cnt-1)
+void gcro_combine(GcroWork &g, const DeviceBuffer &M, const void *basis, int off, int cnt, DeviceBuffer &out, int i,
+                  int n, cudaStream_t s) {
+    gcro_coef_col(g.coef.as<double2>(), M.as<double2>(), off, cnt, i, 1.0, n, s);
+    lincomb(MRHS_FP32, g.fld(out, i, n), MRHS_FP32, basis, g.rows * n, cnt, g.coef.as<double2>(), 1.0, g.rows, n,
+            s);
+}
+
+// Solve A x = b approximately by `cycles` GCRO-DR(m, k) cycles from x = 0.
+void gcro_solve(Op &A, GcroWork &g, const float2 *b, float2 *x, int n, int cycles, cudaStream_t s) {
+    const int m = g.m, k = g.k, p = m - k;
+    const int64_t F = g.rows * n;
+    float2 *r = g.r.as<float2>();
+    MRHS_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * F, s));
+    MRHS_CUDA(cudaMemcpyAsync(r, b, sizeof(float2) * F, cudaMemcpyDeviceToDevice, s));
+    if (g.has_recycle && k > 0) {
+        // C = Q, U = U R^{-1} from A U = Q R (Gram-Schmidt on the batched fields)
+        for (int i = 0; i < k; ++i) A.apply(g.fld(g.U, i, n), g.fld(g.AU, i, n), n, s);
+        for (int i = 0; i < k; ++i) {
+            float2 *ci = g.fld(g.C, i, n);
+            MRHS_CUDA(cudaMemcpyAsync(ci, g.fld(g.AU, i, n), sizeof(float2) * F, cudaMemcpyDeviceToDevice, s));
+            double *rii2 = g.rin2.as<double>() + (size_t)i * n;
+            if (i == 0) {
+                norm2(MRHS_FP32, ci, g.rows, n, rii2, g.sc, s);
+                scale_inv_sqrt(MRHS_FP32, ci, ci, rii2, g.rows, n, s);
+            } else {
+                orthonormalize_step(MRHS_FP32, g.C.ptr, F, i, ci, g.rows, n, g.dots.as<double2>(),
+                                    g.nrm2.as<double>(), rii2, g.nn.as<double>(), g.sc, s);
+                // u_i <- (u_i - sum_{j<i} R_ji u_j) / R_ii, the u_j already replaced
+                lincomb(MRHS_FP32, g.fld(g.U, i, n), MRHS_FP32, g.U.ptr, F, i, g.dots.as<double2>(), -1.0, g.rows,
+                        n, s);
+            }
+            scale_inv_sqrt(MRHS_FP32, g.fld(g.U, i, n), g.fld(g.U, i, n), rii2, g.rows, n, s);
+        }
+        // x = U C^H r, r = b - A x
+        multi_dot(MRHS_FP32, g.C.ptr, F, k, r, g.rows, n, g.dots.as<double2>(), g.sc, s);
+        lincomb(MRHS_FP32, x, MRHS_FP32, g.U.ptr, F, k, g.dots.as<double2>(), 1.0, g.rows, n, s);
+        A.residual(x, b, r, n, s);
+    }
+    for (int c = 0; c < cycles; ++c) {
+        norm2(MRHS_FP32, r, g.rows, n, g.beta2.as<double>(), g.sc, s);
+        scale_inv_sqrt(MRHS_FP32, g.fld(g.V, 0, n), r, g.beta2.as<double>(), g.rows, n, s);
+        if (!g.has_recycle || k == 0) {
+            // a GMRES(m) cycle that seeds the recycle space
+            for (int j = 0; j < m; ++j) gcro_arnoldi_step(A, g, j, 0, false, n, s);
+            gcro_seed_small(g.H.as<double2>(), g.beta2.as<double>(), m, k, g.Y.as<double2>(), g.QC.as<double2>(),
+                            g.PU.as<double2>(), g.err.as<int>(), n, s);
+            gcro_coef_vec(g.coef.as<double2>(), g.Y.as<double2>(), 0, m, 1.0, n, s);
+            lincomb(MRHS_FP32, x, MRHS_FP32, g.V.ptr, F, m, g.coef.as<double2>(), 1.0, g.rows, n, s);
+            if (k > 0) {
+                MRHS_CUDA(cudaMemsetAsync(g.C.ptr, 0, sizeof(float2) * F * k, s));
+                MRHS_CUDA(cudaMemsetAsync(g.U.ptr, 0, sizeof(float2) * F * k, s));
+                for (int i = 0; i < k; ++i) {
+                    gcro_combine(g, g.QC, g.V.ptr, 0, m + 1, g.C, i, n, s);
+                    gcro_combine(g, g.PU, g.V.ptr, 0, m, g.U, i, n, s);
+                }
+                g.has_recycle = true;
+            }
+        } else {
+            // a cycle with the recycle space: p Arnoldi steps of (I - C C^H) A
+            for (int j = 0; j < p; ++j) gcro_arnoldi_step(A, g, j, 0, true, n, s);
+            for (int i = 0; i < k; ++i) {
+                norm2(MRHS_FP32, g.fld(g.U, i, n), g.rows, n, g.nrm2.as<double>(), g.sc, s);
+                gcro_put_norm(g.UN2.as<double>(), g.nrm2.as<double>(), i, n, s);
+                // W^H u_i = [C^H u_i ; V^H u_i]
+                multi_dot(MRHS_FP32, g.C.ptr, F, k, g.fld(g.U, i, n), g.rows, n, g.dots.as<double2>(), g.sc, s);
+                gcro_put_col(g.WU.as<double2>(), g.dots.as<double2>(), k, 0, i, n, s);
+                multi_dot(MRHS_FP32, g.V.ptr, F, p + 1, g.fld(g.U, i, n), g.rows, n, g.dots.as<double2>(), g.sc, s);
+                gcro_put_col(g.WU.as<double2>(), g.dots.as<double2>(), p + 1, k, i, n, s);
+            }
+            multi_dot(MRHS_FP32, g.C.ptr, F, k, r, g.rows, n, g.dots.as<double2>(), g.sc, s);
+            gcro_put_vec(g.WR.as<double2>(), g.dots.as<double2>(), k, 0, n, s);
+            multi_dot(MRHS_FP32, g.V.ptr, F, p + 1, r, g.rows, n, g.dots.as<double2>(), g.sc, s);
+            gcro_put_vec(g.WR.as<double2>(), g.dots.as<double2>(), p + 1, k, n, s);
+            gcro_cycle_small(g.H.as<double2>(), g.B.as<double2>(), g.UN2.as<double>(), g.WR.as<double2>(),
+                             g.WU.as<double2>(), m, k, g.Y.as<double2>(), g.QC.as<double2>(), g.PU.as<double2>(),
+                             g.err.as<int>(), n, s);
+            // x += U (D y_U) + V_p y_V
+            gcro_coef_vec(g.coef.as<double2>(), g.Y.as<double2>(), 0, k, 1.0, n, s);
+            lincomb(MRHS_FP32, x, MRHS_FP32, g.U.ptr, F, k, g.coef.as<double2>(), 1.0, g.rows, n, s);
+            gcro_coef_vec(g.coef.as<double2>(), g.Y.as<double2>(), k, p, 1.0, n, s);
+            lincomb(MRHS_FP32, x, MRHS_FP32, g.V.ptr, F, p, g.coef.as<double2>(), 1.0, g.rows, n, s);
+            // C <- [C, V_{p+1}] Q, U <- [U D, V_p] P R^{-1}
+            MRHS_CUDA(cudaMemsetAsync(g.C2.ptr, 0, sizeof(float2) * F * k, s));
+            MRHS_CUDA(cudaMemsetAsync(g.U2.ptr, 0, sizeof(float2) * F * k, s));
+            for (int i = 0; i < k; ++i) {
+                gcro_combine(g, g.QC, g.C.ptr, 0, k, g.C2, i, n, s);
+                gcro_combine(g, g.QC, g.V.ptr, k, p + 1, g.C2, i, n, s);
+                gcro_combine(g, g.PU, g.U.ptr, 0, k, g.U2, i, n, s);
+                gcro_combine(g, g.PU, g.V.ptr, k, p, g.U2, i, n, s);
+            }
+            MRHS_CUDA(cudaMemcpyAsync(g.C.ptr, g.C2.ptr, sizeof(float2) * F * k, cudaMemcpyDeviceToDevice, s));
+            MRHS_CUDA(cudaMemcpyAsync(g.U.ptr, g.U2.ptr, sizeof(float2) * F * k, cudaMemcpyDeviceToDevice, s));
+        }
+        A.residual(x, b, r, n, s);
+    }
+}
+
 // ------------------------------------------------------- level workspace
 struct LevelWork {
     DeviceBuffer rhs, sol;  // coarse levels: restricted residual and coarse solution
@@ -220,6 +389,7 @@ struct LevelWork {
     DeviceBuffer ceo_r, ceo_re, ceo_ro, ceo_te, ceo_bh, ceo_de, ceo_do;
     KWork ceo_smooth;
     std::unique_ptr<CoarseSchurOp> ceo_op;
+    std::unique_ptr<GcroWork> gcro;  // coarsest level with the GCRO-DR solver
 };
 
 struct GraphKey {
@@ -324,7 +494,9 @@ void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t 
         EventTimer t(prof, s, &mg.t_coarse);
         Op &Ac = *mg.ops[l + 1];
         float2 *sol = WC.sol.as<float2>();
-        if (l + 1 == mg.nlev - 1) {
+        if (l + 1 == mg.nlev - 1 && WC.gcro) {
+            gcro_solve(Ac, *WC.gcro, WC.rhs.as<float2>(), sol, n, mg.p.coarse_cycles, s);
+        } else if (l + 1 == mg.nlev - 1) {
             for (int c = 0; c < mg.p.coarse_cycles; ++c)
                 krylov_cycle(Ac, nullptr, WC.rhs.as<float2>(), sol, n, mg.p.coarse_m, WC.solve, s, c == 0, nullptr);
         } else {
@@ -481,6 +653,9 @@ void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
         fail(MRHS_ERR_INVALID, "sap_cycles must be in 1..16 and sap_mr in 1..64");
     if (p.coarse_smoother_evenodd != 0 && p.coarse_smoother_evenodd != 1)
         fail(MRHS_ERR_INVALID, "coarse_smoother_evenodd must be 0 or 1");
+    if (p.coarse_solver != 0 && p.coarse_solver != 1) fail(MRHS_ERR_INVALID, "coarse_solver must be 0 or 1");
+    if (p.coarse_solver == 1 && (p.coarse_m > 16 || p.coarse_recycle < 0 || p.coarse_recycle >= p.coarse_m))
+        fail(MRHS_ERR_INVALID, "GCRO-DR needs coarse_m <= 16 and 0 <= coarse_recycle < coarse_m");
     if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
 }
 
@@ -548,6 +723,10 @@ void alloc_workspace(mrhs_mg &mg) {
             W.sol.alloc(sizeof(float2) * (size_t)L.rows() * nmax);
             if (l == mg.nlev - 1) W.solve.init(mg.p.coarse_m, L.rows(), nmax, false);
             else W.solve.init(mg.p.inter_m, L.rows(), nmax, true);
+            if (l == mg.nlev - 1 && mg.p.coarse_solver == 1) {
+                W.gcro.reset(new GcroWork());
+                W.gcro->init(mg.p.coarse_m, mg.p.coarse_recycle, L.rows(), nmax);
+            }
         }
         if (l < mg.nlev - 1) W.smooth.init(mg.p.smooth_m, L.rows(), nmax, false);
     }
@@ -815,6 +994,9 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     for (int mu = 0; mu < 4; ++mu) p->sap_block[mu] = 4;
     p->sap_cycles = 1;
     p->sap_mr = 4;
+    p->coarse_smoother_evenodd = 0;
+    p->coarse_solver = 0;
+    p->coarse_recycle = 4;
 }
 
 mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_mg **out) {
@@ -1010,6 +1192,45 @@ mrhs_status mrhs_coarse_apply_schur(mrhs_mg *mg, int level, const void *in_dev, 
     coarse_schur_apply(C, static_cast<const float2 *>(in_dev), static_cast<float2 *>(out_dev), t1.as<float2>(),
                        t2.as<float2>(), nrhs, s);
     check_wait_flags(C, s);
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_coarsest_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, void *stream) {
+    API_TRY
+    if (!mg) fail(MRHS_ERR_INVALID, "mg must be non-null");
+    check_n(mg, nrhs);
+    if (!b_dev || !x_dev || b_dev == x_dev) fail(MRHS_ERR_INVALID, "distinct non-null fields required");
+    DevGuard dg(mg->lat->device);
+    const int l = mg->nlev - 1;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LevelWork &W = mg->work[l];
+    Op &A = *mg->ops[l];
+    const float2 *b = static_cast<const float2 *>(b_dev);
+    float2 *x = static_cast<float2 *>(x_dev);
+    if (W.gcro) {
+        gcro_solve(A, *W.gcro, b, x, nrhs, mg->p.coarse_cycles, s);
+        int e = 0;
+        MRHS_CUDA(cudaMemcpyAsync(&e, W.gcro->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MRHS_CUDA(cudaStreamSynchronize(s));
+        if (e) {
+            MRHS_CUDA(cudaMemset(W.gcro->err.ptr, 0, sizeof(int)));
+            fail(MRHS_ERR_CUDA, "GCRO-DR: the QR algorithm of a harmonic Ritz problem did not converge");
+        }
+    } else {
+        for (int c = 0; c < mg->p.coarse_cycles; ++c)
+            krylov_cycle(A, nullptr, b, x, nrhs, mg->p.coarse_m, W.solve, s, c == 0, nullptr);
+    }
+    check_wait_flags(mg->lev[l], s);
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_coarsest_reset(mrhs_mg *mg) {
+    API_TRY
+    if (!mg) fail(MRHS_ERR_INVALID, "mg must be non-null");
+    LevelWork &W = mg->work[mg->nlev - 1];
+    if (W.gcro) W.gcro->has_recycle = false;
     return ok();
     API_CATCH
 }

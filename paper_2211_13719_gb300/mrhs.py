@@ -72,6 +72,8 @@ class MgParams(C.Structure):
         ("sap_cycles", C.c_int),
         ("sap_mr", C.c_int),
         ("coarse_smoother_evenodd", C.c_int),
+        ("coarse_solver", C.c_int),
+        ("coarse_recycle", C.c_int),
     ]
 
 
@@ -163,6 +165,8 @@ PROTOTYPES = {
     "mrhs_coarse_apply": (_I, [_P, _I, _P, _P, _I, _I, _P]),
     "mrhs_vcycle": (_I, [_P, _P, _P, _I, _P]),
     "mrhs_coarse_apply_schur": (_I, [_P, _I, _P, _P, _I, _P]),
+    "mrhs_coarsest_solve": (_I, [_P, _P, _P, _I, _P]),
+    "mrhs_coarsest_reset": (_I, [_P]),
     "mrhs_debug_expire_waits": (_I, [_I]),
     "mrhs_solve": (_I, [_P, _P, _P, _I, _D, _P, C.POINTER(SolveStats), _P]),
     "mrhs_server_create": (_I, [C.POINTER(ServerParams), C.POINTER(_P)]),
@@ -387,6 +391,14 @@ def mrhs_coarse_apply(mg, level, in_dev, out_dev, nrhs, links_prec=MRHS_FP32, st
 
 def mrhs_coarse_apply_schur(mg, level, in_dev, out_dev, nrhs, stream=None):
     _check(lib().mrhs_coarse_apply_schur(mg, int(level), _ptr(in_dev), _ptr(out_dev), int(nrhs), _stream(stream)))
+
+
+def mrhs_coarsest_solve(mg, b_dev, x_dev, nrhs, stream=None):
+    _check(lib().mrhs_coarsest_solve(mg, _ptr(b_dev), _ptr(x_dev), int(nrhs), _stream(stream)))
+
+
+def mrhs_coarsest_reset(mg):
+    _check(lib().mrhs_coarsest_reset(mg))
 
 
 def mrhs_vcycle(mg, v_dev, z_dev, nrhs, stream=None):
