@@ -218,6 +218,7 @@ struct GcroWork {
     int m = 0, k = 0, nmax = 0;
     int64_t rows = 0;
     bool has_recycle = false;
+    int last_n = 0;  // RHS count the recycle fields are laid out for
     DeviceBuffer V, U, C, U2, C2, AU, r;           // fields [rows][n]
     DeviceBuffer H, B, WU, QC, PU;                 // per RHS [n][17][17] double2
     DeviceBuffer WR, Y, UN2;                       // per RHS [n][17] (UN2 double)
@@ -289,6 +290,8 @@ void gcro_solve(Op &A, GcroWork &g, const float2 *b, float2 *x, int n, int cycle
     const int m = g.m, k = g.k, p = m - k;
     const int64_t F = g.rows * n;
     float2 *r = g.r.as<float2>();
+    if (n != g.last_n) g.has_recycle = false;  // the recycle fields hold another RHS count's layout
+    g.last_n = n;
     MRHS_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * F, s));
     MRHS_CUDA(cudaMemcpyAsync(r, b, sizeof(float2) * F, cudaMemcpyDeviceToDevice, s));
     if (g.has_recycle && k > 0) {
