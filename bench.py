@@ -362,6 +362,10 @@ def smoother_params(args):
         out = dict(smoother_sap=0, smoother_evenodd=0)
     if args.coarse_smoother == "evenodd":
         out["coarse_smoother_evenodd"] = 1
+    if args.coarse_solver == "gcrodr":
+        out.update(coarse_solver=1, coarse_recycle=args.coarse_recycle)
+        if args.coarse_m:
+            out["coarse_m"] = args.coarse_m
     return out
 
 
@@ -700,6 +704,9 @@ def run_ours(args, rank, world, local_rank):
                        "smoother": args.smoother + (f" (SAP {args.sap_cycles} cycle(s), {args.sap_mr} MR steps, "
                                                     f"4^4 blocks)" if args.smoother == "sap" else ""),
                        "coarse_smoother": args.coarse_smoother,
+                       "coarse_solver": args.coarse_solver + (f" (m {args.coarse_m or MG_PARAMS['coarse_m']}, "
+                                                              f"k {args.coarse_recycle})"
+                                                              if args.coarse_solver == "gcrodr" else ""),
                        "l2": "inputs larger than L2 (FP64 fields of 8 GB)"},
         }
         line.update(extra)
@@ -1083,6 +1090,11 @@ def main():
     ap.add_argument("--coarse-smoother", default="gmres", choices=["gmres", "evenodd"],
                     help="intermediate-level post-smoother: GMRES on the level operator (default) or on its "
                          "coarse even-odd Schur complement")
+    ap.add_argument("--coarse-solver", default="gmres", choices=["gmres", "gcrodr"],
+                    help="coarsest-level solver: GMRES(coarse_m) (default) or GCRO-DR(coarse_m, --coarse-recycle) "
+                         "with its recycle space carried across V-cycles")
+    ap.add_argument("--coarse-recycle", type=int, default=4)
+    ap.add_argument("--coarse-m", type=int, default=0, help="override the coarsest Krylov length")
     ap.add_argument("--sap-mr", type=int, default=4)
     ap.add_argument("--sap-cycles", type=int, default=1)
     ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas",
