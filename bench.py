@@ -366,6 +366,7 @@ def smoother_params(args):
         out.update(coarse_solver=1, coarse_recycle=args.coarse_recycle)
         if args.coarse_m:
             out["coarse_m"] = args.coarse_m
+    out["coarse_fused"] = args.coarse_fused
     return out
 
 
@@ -422,22 +423,24 @@ def run_serving(mrhs, mg_big, w, saturated, args, torch, np, load=None, nreq=Non
         # the small config costs about its volume ratio of a big solve
         mean_cost = 0.5 * (1.0 + vols[1] / vols[0]) * 6.5
         rate = load * saturated / mean_cost
-        pending = {}  # request id -> (nr, solution buffer), until the server reports completion
+        pending = {}  # request id -> (config, nr, solution buffer), until the server reports completion
         lat, qt, ok, solves, done = [], [], 0, 0, 0
+        equiv = 0.0  # solves weighted by volume relative to the big config (the unit of the offered load)
 
         def collect():
-            nonlocal ok, solves, done
+            nonlocal ok, solves, done, equiv
             for rid in list(pending):
                 st, rs = mrhs.mrhs_poll(srv, rid)
                 if st == mrhs.MRHS_PENDING:
                     continue
-                nr, _x = pending.pop(rid)  # the solution buffer is released here
+                c, nr, _x = pending.pop(rid)  # the solution buffer is released here
                 lat.append(rs.latency_s)
                 qt.append(rs.queue_s)
                 done += 1
                 if st == mrhs.MRHS_OK:
                     ok += 1
                     solves += nr
+                    equiv += nr * vols[c] / vols[0]
 
         t0 = time.perf_counter()
         t_next = t0
@@ -450,7 +453,7 @@ def run_serving(mrhs, mg_big, w, saturated, args, torch, np, load=None, nreq=Non
             b = pool[c][:vols[c] * 12 * nr].reshape(vols[c], 12, nr)
             x = np.empty_like(b)
             rid = mrhs.mrhs_submit(srv, cids[c], b, x, nr, w["tol"])
-            pending[rid] = (nr, x)
+            pending[rid] = (c, nr, x)
             collect()
         mrhs.mrhs_server_drain(srv)
         wall = time.perf_counter() - t0
@@ -460,7 +463,8 @@ def run_serving(mrhs, mg_big, w, saturated, args, torch, np, load=None, nreq=Non
         s_ms = lat_ms - q_ms
         return {"requests": done, "completed_ok": ok, "solves": solves, "wall_s": wall,
                 "solves_per_s": solves / wall, "offered_load": load,
-                "offered_solves_per_s": load * saturated,
+                "big_equivalent_solves_per_s": equiv / wall,
+                "offered_big_equivalent_solves_per_s": load * saturated,
                 "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                 "queue_p50_ms": float(np.percentile(q_ms, 50)), "queue_p99_ms": float(np.percentile(q_ms, 99)),
                 "in_solve_p50_ms": float(np.percentile(s_ms, 50)), "in_solve_p99_ms": float(np.percentile(s_ms, 99)),
@@ -609,6 +613,13 @@ def run_ours(args, rank, world, local_rank):
         extra["per_solve"] = {"outer_iters": s0.outer_iters, "inner_iters": s0.inner_iters, "vcycles": s0.vcycles,
                               "seconds": s0.seconds, "max_rel_residual": max_rel}
         extra["setup_s"] = setup_s
+        extra["setup_phases_ms"] = {
+            f"level{l}->{l + 1}": dict(zip(("null_vectors", "orthonormalise", "galerkin", "tc_prepare"),
+                                           [round(v, 2) for v in mrhs.mrhs_mg_setup_times(mg, l)]))
+            for l in range(w["n_levels"] - 1)}
+        fi = mrhs.mrhs_coarsest_fused_info(mg)
+        extra["coarsest_persistent_kernel"] = {"in_use": bool(fi[0]), "resident_ctas": fi[1],
+                                               "coarsest_sites": fi[2]}
         # --- rooflines.  The dominant kernel of a timed solve in the profiler's launch list is the
         # even-odd hopping kernel k_eo_x2 (the Schur operator D_hat = C_oo - 1/4 H_oe C_ee^-1 H_eo of the
         # fine smoother: one C^-1 H launch and one C - 1/4 H launch over V/2 output sites each).  Its
@@ -718,7 +729,9 @@ def run_ours(args, rank, world, local_rank):
                        "coarse_smoother": args.coarse_smoother,
                        "coarse_solver": args.coarse_solver + (f" (m {args.coarse_m or MG_PARAMS['coarse_m']}, "
                                                               f"k {args.coarse_recycle})"
-                                                              if args.coarse_solver == "gcrodr" else ""),
+                                                              if args.coarse_solver == "gcrodr" else "")
+                                        + (" (persistent kernel)" if args.coarse_fused and args.coarse_solver == "gmres"
+                                           else ""),
                        "l2": "inputs larger than L2 (FP64 fields of 8 GB)"},
         }
         line.update(extra)
@@ -1106,6 +1119,9 @@ def main():
                     help="coarsest-level solver: GMRES(coarse_m) (default) or GCRO-DR(coarse_m, --coarse-recycle) "
                          "with its recycle space carried across V-cycles")
     ap.add_argument("--coarse-recycle", type=int, default=4)
+    ap.add_argument("--coarse-fused", type=int, default=1, choices=[0, 1],
+                    help="1 (default): the coarsest GMRES cycle as one persistent kernel; 0: one launch per "
+                         "operation")
     ap.add_argument("--coarse-m", type=int, default=0, help="override the coarsest Krylov length")
     ap.add_argument("--sap-mr", type=int, default=4)
     ap.add_argument("--sap-cycles", type=int, default=1)

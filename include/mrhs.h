@@ -312,6 +312,12 @@ typedef struct {
                                               from one V-cycle to the next
                                               (coarse_m <= 16)                    */
     int coarse_recycle;                    /* GCRO-DR recycle vectors k < coarse_m */
+    int coarse_fused;                      /* 1: the coarsest GMRES cycle runs as one
+                                              persistent cooperative kernel (16-bit
+                                              tensor-core coarsest level with 64 dof,
+                                              coarse_m <= 16, every coarsest site's
+                                              CTA resident); else, and with 0, one
+                                              launch per operation                */
 } mrhs_mg_params;
 
 /* Fill `p` with the defaults used for the 24^3x64 three-level workload. */
@@ -388,6 +394,21 @@ mrhs_status mrhs_coarse_apply_schur(mrhs_mg *mg, int level, const void *in_dev, 
  * `stream`; MRHS_ERR_CUDA if a harmonic Ritz eigenproblem did not converge. */
 mrhs_status mrhs_coarsest_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, void *stream);
 mrhs_status mrhs_coarsest_reset(mrhs_mg *mg);
+/* Setup time of the transfer level -> level + 1 (milliseconds, CUDA events
+ * on the setup stream, recorded by mrhs_setup_mg): [0] null-vector
+ * relaxation (Sec. 5, the N vectors as N right-hand sides), [1] chiral split
+ * and FP64 block orthonormalisation, [2] Galerkin coarse operator (Sec. 6),
+ * [3] 16-bit links, tensor-core transfer tiles and coarse even-odd inverses.
+ * MRHS_ERR_INVALID unless 0 <= level < n_levels - 1. */
+mrhs_status mrhs_mg_setup_times(mrhs_mg *mg, int level, double out_ms[4]);
+
+/* Whether the coarsest solve runs as the persistent kernel (coarse_fused):
+ * *in_use 1 if it does; *resident_ctas the kernel's CTAs that fit on the
+ * device at once (one per SM: it holds tensor memory; 0 without a 16-bit
+ * tensor-core coarsest level); *sites the coarsest level's sites, which the
+ * CTAs share, up to 4 each (one tensor-memory accumulator per site; 8 at
+ * max_rhs <= 16). */
+mrhs_status mrhs_coarsest_fused_info(mrhs_mg *mg, int *in_use, int *resident_ctas, int *sites);
 
 /* One MG V-cycle z = M^{-1} v on the fine level (Sec. 8 preconditioner),
  * FP32 fields [V][12][nrhs]. */
@@ -422,7 +443,8 @@ mrhs_status mrhs_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, do
  * cleared, so the next call on the same hierarchy starts clean. */
 
 /* Testing hook, not part of the paper's method: the next `launches` launches
- * of the 16-bit tensor-core coarse stencil that are not being recorded into
+ * of the 16-bit tensor-core coarse stencil (or of the persistent coarsest
+ * GMRES kernel, which contains it) that are not being recorded into
  * a CUDA graph give up their first operand wait at once (zero try_wait
  * rounds) instead of after the normal bound.  The kernel still waits for
  * every copy it has issued before it frees its tensor memory and returns,

@@ -82,16 +82,6 @@ __device__ __forceinline__ int64_t cb_site(int64_t cb, int p, const int L[4]) {
     return ((c[0] + c[1] + c[2] + c[3]) & 1) == p ? 2 * cb : 2 * cb + 1;
 }
 
-__device__ __forceinline__ int64_t nb_site(int64_t site, const int L[4], int d) {
-    if (d == 0) return site;
-    int c[4];
-    site_to_coords(site, L, c);
-    const int mu = d <= 4 ? d - 1 : d - 5;
-    const int step = d <= 4 ? 1 : -1;
-    c[mu] = (c[mu] + step + L[mu]) % L[mu];
-    return coords_to_site(c, L);
-}
-
 template <int STAGES>
 __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ Abf, const uint8_t *__restrict__ Phi,
                                                    float2 *__restrict__ out, const float2 *__restrict__ y, TcArgs a,
@@ -140,7 +130,7 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const uint8_t *__restrict__ A
                 if (q >= STAGES) ok = mbar_wait(empty0 + 8 * s, ((q / STAGES) - 1) & 1);
                 if (!ok) break;
                 const int d = a.d_first + q;
-                const int64_t nb = nb_site(site, a.L, d);
+                const int64_t nb = stencil_nb_site(site, a.L, d);
                 const int64_t pin = a.parity < 0 ? nb : nb >> 1;
                 const uint32_t sa = sbase + s * stage_bytes;
                 mbar_expect_tx(full0 + 8 * s, A_TILE + b_tile);
@@ -310,6 +300,17 @@ size_t tc_smem_bytes(int npad, int stages) {
 
 bool coarse_bf16_supported(const Level &c) { return c.dof == NC; }
 
+uint32_t tc_first_wait_limit(cudaStream_t s) {
+    // a launch recorded into a graph would keep the expired limit for every replay: only eager launches
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MRHS_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return SPIN_LIMIT;
+    int left = g_expire_waits.load();
+    while (left > 0 && !g_expire_waits.compare_exchange_weak(left, left - 1)) {
+    }
+    return left > 0 ? 0u : SPIN_LIMIT;
+}
+
 void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s) {
     if (!coarse_bf16_supported(c)) fail(MRHS_ERR_INVALID, "16-bit tensor-core stencil needs 64 coarse dof");
     if (fmt != MRHS_FP16 && fmt != MRHS_BF16) fail(MRHS_ERR_INVALID, "16-bit format must be FP16 or BF16");
@@ -365,21 +366,11 @@ void coarse_tc_general(const Level &c, const uint8_t *links, const float *link_s
     a.npad = npad;
     a.idesc = idesc_16bit(MROWS, npad, c.tc_fmt == MRHS_FP16 ? 0u : 1u);
     a.tmem_cols = npad <= 32 ? 32 : (npad <= 64 ? 64 : 128);
-    a.first_limit = SPIN_LIMIT;
+    a.first_limit = tc_first_wait_limit(s);
     a.d_first = d_first;
     a.d_last = d_last;
     a.links_per_site = links_per_site;
     a.parity = parity;
-    {
-        // a launch recorded into a graph would keep the expired limit for every replay: only eager launches
-        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-        MRHS_CUDA(cudaStreamIsCapturing(s, &cap));
-        int left = g_expire_waits.load();
-        while (cap == cudaStreamCaptureStatusNone && left > 0 &&
-               !g_expire_waits.compare_exchange_weak(left, left - 1)) {
-        }
-        if (cap == cudaStreamCaptureStatusNone && left > 0) a.first_limit = 0;
-    }
     static bool attr = false;
     if (!attr) {
         MRHS_CUDA(cudaFuncSetAttribute(k_coarse_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,

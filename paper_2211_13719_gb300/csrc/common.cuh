@@ -141,4 +141,16 @@ __host__ __device__ __forceinline__ int64_t coords_to_site(const int c[4], const
     return c[0] + (int64_t)L[0] * (c[1] + (int64_t)L[1] * (c[2] + (int64_t)L[2] * c[3]));
 }
 
+// neighbour of `site` in direction d of the 9-point coarse stencil (Sec. 6): d = 0 the site
+// itself, d = 1..4 the forward neighbours in x, y, z, t, d = 5..8 the backward ones (periodic)
+__host__ __device__ __forceinline__ int64_t stencil_nb_site(int64_t site, const int L[4], int d) {
+    if (d == 0) return site;
+    int c[4];
+    site_to_coords(site, L, c);
+    const int mu = d <= 4 ? d - 1 : d - 5;
+    const int step = d <= 4 ? 1 : -1;
+    c[mu] = (c[mu] + step + L[mu]) % L[mu];
+    return coords_to_site(c, L);
+}
+
 }  // namespace mrhs

@@ -64,6 +64,9 @@ bool coarse_bf16_supported(const Level &c);
 // flag after the work queued on s, synchronising s)
 int coarse_tc_error(const Level &c, cudaStream_t s);
 void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s);
+// try_wait rounds of the first operand wait of the next tensor-core coarse launch on s:
+// the normal bound, or 0 while mrhs_debug_expire_waits has eager launches left to expire
+uint32_t tc_first_wait_limit(cudaStream_t s);
 // Coarse even-odd decomposition (Sec. 6, M_eooe) on 16-bit tensor-core levels with
 // even extents; half fields [V/2][64][n] hold the sites of one parity (site s at s / 2).
 bool coarse_eo_supported(const Level &c);
@@ -107,6 +110,25 @@ void gcro_cycle_small(const double2 *H, const double2 *B, const double *UN2, con
                       int m, int k, double2 *Y, double2 *QC, double2 *PU, int *err, int n, cudaStream_t s);
 void gcro_coef_vec(double2 *coef, const double2 *v, int off, int cnt, double sign, int n, cudaStream_t s);
 void gcro_coef_col(double2 *coef, const double2 *M, int off, int cnt, int col, double sign, int n, cudaStream_t s);
+
+// The coarsest level's GMRES(m) cycle from x = 0 as one persistent cooperative kernel
+// (coarsest_fused.cu): 16-bit tensor-core levels with 64 dof, <= 64 RHS, m <= 16, every
+// CTA resident at once, each owning up to max_sites_per_cta sites.
+struct CoarsestFused {
+    int m = 0, nmax = 0, G = 0, S = 0;  // restart length, RHS bound, CTAs, sites per CTA
+    DeviceBuffer part, npart, hcol, sig, R, cs, sn, g, y, sync;
+    static size_t smem_bytes(int n);
+    // CTAs of the kernel sized for nmax RHS that can be resident at once on `device` (0: no
+    // tensor-core level or no cooperative launch); the kernel needs one per coarsest site
+    static int resident_ctas(const Level &c, int nmax, int device);
+    // sites one CTA can own: one tensor-memory accumulator each
+    static int max_sites_per_cta(int nmax);
+    static bool supported(const Level &c, int nmax, int m, int device);
+    void init(const Level &c, int m, int nmax, int device);
+    // x = GMRES_m(A_c) b on level c (x overwritten); Vbasis: m + 1 fields of workspace.
+    // Uses the level's packed-input buffer and records expired waits in its TcErr.
+    void solve(const Level &c, float2 *Vbasis, const float2 *b, float2 *x, int n, cudaStream_t s);
+};
 
 // Solver entry used by the C ABI and the server (solver.cu).
 bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *tols, double *rel_out,

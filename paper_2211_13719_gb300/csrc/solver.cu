@@ -393,6 +393,10 @@ struct LevelWork {
     KWork ceo_smooth;
     std::unique_ptr<CoarseSchurOp> ceo_op;
     std::unique_ptr<GcroWork> gcro;  // coarsest level with the GCRO-DR solver
+    // coarsest level, GMRES as one persistent kernel; fused_r, fused_e: residual and
+    // correction fields of the cycles after the first
+    std::unique_ptr<CoarsestFused> fused;
+    DeviceBuffer fused_r, fused_e;
 };
 
 struct GraphKey {
@@ -434,6 +438,9 @@ struct mrhs_mg {
     // component timing (profiled, non-graph solves only)
     bool profile = false;
     double t_fine = 0, t_restrict = 0, t_prolong = 0, t_coarse = 0;
+    // setup phases per transfer l -> l+1 (milliseconds, CUDA events on the setup stream): null
+    // vectors, chiral split + orthonormalisation, Galerkin operator, 16-bit / tensor-core preparation
+    double setup_ms[MRHS_MAX_LEVELS - 1][4] = {};
     int vcycles = 0;
     // the solver's own stream: graphs cannot be captured on the legacy default stream
     cudaStream_t own = nullptr;
@@ -472,6 +479,29 @@ struct EventTimer {
     }
 };
 
+// The coarsest level's solve x = A^-1 b as the V-cycle runs it: coarse_cycles
+// cycles of GCRO-DR, of GMRES as one persistent kernel, or of GMRES one launch
+// per operation, from x = 0.
+void coarsest_solve(mrhs_mg &mg, const float2 *b, float2 *x, int n, cudaStream_t s) {
+    const int l = mg.nlev - 1;
+    LevelWork &W = mg.work[l];
+    Op &A = *mg.ops[l];
+    if (W.gcro) {
+        gcro_solve(A, *W.gcro, b, x, n, mg.p.coarse_cycles, s);
+    } else if (W.fused) {
+        const Level &C = mg.lev[l];
+        W.fused->solve(C, W.solve.Vj(0, n), b, x, n, s);
+        for (int c = 1; c < mg.p.coarse_cycles; ++c) {
+            A.residual(x, b, W.fused_r.as<float2>(), n, s);
+            W.fused->solve(C, W.solve.Vj(0, n), W.fused_r.as<float2>(), W.fused_e.as<float2>(), n, s);
+            axpy(MRHS_FP32, 1.0, W.fused_e.ptr, x, C.rows() * n, s);
+        }
+    } else {
+        for (int c = 0; c < mg.p.coarse_cycles; ++c)
+            krylov_cycle(A, nullptr, b, x, n, mg.p.coarse_m, W.solve, s, c == 0, nullptr);
+    }
+}
+
 // unit_norm: every RHS column of v has norm <= 1 (true for the Arnoldi vectors
 // the preconditioned Krylov cycles pass in)
 void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t s, bool unit_norm = true);
@@ -497,11 +527,8 @@ void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t 
         EventTimer t(prof, s, &mg.t_coarse);
         Op &Ac = *mg.ops[l + 1];
         float2 *sol = WC.sol.as<float2>();
-        if (l + 1 == mg.nlev - 1 && WC.gcro) {
-            gcro_solve(Ac, *WC.gcro, WC.rhs.as<float2>(), sol, n, mg.p.coarse_cycles, s);
-        } else if (l + 1 == mg.nlev - 1) {
-            for (int c = 0; c < mg.p.coarse_cycles; ++c)
-                krylov_cycle(Ac, nullptr, WC.rhs.as<float2>(), sol, n, mg.p.coarse_m, WC.solve, s, c == 0, nullptr);
+        if (l + 1 == mg.nlev - 1) {
+            coarsest_solve(mg, WC.rhs.as<float2>(), sol, n, s);
         } else {
             VcyclePrecond M(&mg, l + 1);
             krylov_cycle(Ac, &M, WC.rhs.as<float2>(), sol, n, mg.p.inter_m, WC.solve, s, true, nullptr);
@@ -657,12 +684,35 @@ void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
     if (p.coarse_smoother_evenodd != 0 && p.coarse_smoother_evenodd != 1)
         fail(MRHS_ERR_INVALID, "coarse_smoother_evenodd must be 0 or 1");
     if (p.coarse_solver != 0 && p.coarse_solver != 1) fail(MRHS_ERR_INVALID, "coarse_solver must be 0 or 1");
+    if (p.coarse_fused != 0 && p.coarse_fused != 1) fail(MRHS_ERR_INVALID, "coarse_fused must be 0 or 1");
     if (p.coarse_solver == 1 && (p.coarse_m > 16 || p.coarse_recycle < 0 || p.coarse_recycle >= p.coarse_m))
         fail(MRHS_ERR_INVALID, "GCRO-DR needs coarse_m <= 16 and 0 <= coarse_recycle < coarse_m");
     if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
 }
 
-void setup_level(mrhs_mg &mg, int l, cudaStream_t s) {
+// CUDA events marking the setup phases of one level on the setup stream
+struct PhaseEvents {
+    std::vector<cudaEvent_t> ev;
+    void mark(cudaStream_t s) {
+        cudaEvent_t e = nullptr;
+        MRHS_CUDA(cudaEventCreate(&e));
+        ev.push_back(e);
+        MRHS_CUDA(cudaEventRecord(e, s));
+    }
+    // milliseconds between consecutive marks (after the stream has finished them)
+    void read(double *out, int count) {
+        for (int i = 0; i < count && i + 1 < (int)ev.size(); ++i) {
+            float ms = 0.f;
+            MRHS_CUDA(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+            out[i] = ms;
+        }
+    }
+    ~PhaseEvents() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    }
+};
+
+void setup_level(mrhs_mg &mg, int l, cudaStream_t s, PhaseEvents &ph) {
     Level &F = mg.lev[l];
     Level &Cl = mg.lev[l + 1];
     const int N = F.N;
@@ -677,6 +727,7 @@ void setup_level(mrhs_mg &mg, int l, cudaStream_t s) {
         fill_gaussian(MRHS_FP32, v32.ptr, count, mg.p.seed * 0x9E3779B9ull + (uint64_t)l, s);
     }
     // relaxation of A v = 0, the N vectors as N right-hand sides
+    ph.mark(s);
     if (mg.p.setup_sweeps > 0) {
         KWork rw;
         rw.init(mg.p.setup_m, F.rows(), N, false);
@@ -690,12 +741,14 @@ void setup_level(mrhs_mg &mg, int l, cudaStream_t s) {
         cast(MRHS_FP64, v64.ptr, MRHS_FP32, v32.ptr, count, s);
     }
     // chiral split + FP64 block orthonormalisation
+    ph.mark(s);
     block_orthonormalize(F, v64.as<double2>(), s);
     F.P64 = std::move(v64);
     F.P32.alloc(sizeof(float2) * count);
     cast(MRHS_FP32, F.P32.ptr, MRHS_FP64, F.P64.ptr, count, s);
     v32.release();
     // Galerkin coarse operator R A P, stencil block by stencil block
+    ph.mark(s);
     const int nc = 2 * N;
     Cl.A32.alloc(sizeof(float2) * (size_t)Cl.V * 9 * nc * nc);
     DeviceBuffer Pe(sizeof(float2) * (size_t)F.V * F.dof * nc);
@@ -712,6 +765,7 @@ void setup_level(mrhs_mg &mg, int l, cudaStream_t s) {
         }
         restrict_fields(F, Cl, H.as<float2>(), Cl.A32.as<float2>() + (size_t)d * nc * nc, nc, ostride, s);
     }
+    ph.mark(s);
     MRHS_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -729,6 +783,14 @@ void alloc_workspace(mrhs_mg &mg) {
             if (l == mg.nlev - 1 && mg.p.coarse_solver == 1) {
                 W.gcro.reset(new GcroWork());
                 W.gcro->init(mg.p.coarse_m, mg.p.coarse_recycle, L.rows(), nmax);
+            } else if (l == mg.nlev - 1 && mg.p.coarse_fused &&
+                       CoarsestFused::supported(L, nmax, mg.p.coarse_m, mg.lat->device)) {
+                W.fused.reset(new CoarsestFused());
+                W.fused->init(L, mg.p.coarse_m, nmax, mg.lat->device);
+                if (mg.p.coarse_cycles > 1) {
+                    W.fused_r.alloc(sizeof(float2) * (size_t)L.rows() * nmax);
+                    W.fused_e.alloc(sizeof(float2) * (size_t)L.rows() * nmax);
+                }
             }
         }
         if (l < mg.nlev - 1) W.smooth.init(mg.p.smooth_m, L.rows(), nmax, false);
@@ -1000,6 +1062,7 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->coarse_smoother_evenodd = 0;
     p->coarse_solver = 0;
     p->coarse_recycle = 4;
+    p->coarse_fused = 1;
 }
 
 mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_mg **out) {
@@ -1038,7 +1101,8 @@ mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_
     MRHS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     try {
         for (int l = 0; l < mg->nlev - 1; ++l) {
-            setup_level(*mg, l, s);
+            PhaseEvents ph;
+            setup_level(*mg, l, s, ph);
             Level &C = mg->lev[l + 1];
             const bool use_tc = (params->coarse_precision == MRHS_BF16 || params->coarse_precision == MRHS_FP16) &&
                                 coarse_bf16_supported(C);
@@ -1053,6 +1117,9 @@ mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_
                 intergrid_tc_prepare(F, C, s);
                 F.tc_intergrid = true;
             }
+            ph.mark(s);
+            MRHS_CUDA(cudaStreamSynchronize(s));
+            ph.read(mg->setup_ms[l], 4);
             mg->ops.emplace_back(new CoarseOp(&C, use_tc));
         }
         MRHS_CUDA(cudaStreamSynchronize(s));
@@ -1208,11 +1275,10 @@ mrhs_status mrhs_coarsest_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int
     const int l = mg->nlev - 1;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     LevelWork &W = mg->work[l];
-    Op &A = *mg->ops[l];
     const float2 *b = static_cast<const float2 *>(b_dev);
     float2 *x = static_cast<float2 *>(x_dev);
+    coarsest_solve(*mg, b, x, nrhs, s);
     if (W.gcro) {
-        gcro_solve(A, *W.gcro, b, x, nrhs, mg->p.coarse_cycles, s);
         int e = 0;
         MRHS_CUDA(cudaMemcpyAsync(&e, W.gcro->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
         MRHS_CUDA(cudaStreamSynchronize(s));
@@ -1220,11 +1286,29 @@ mrhs_status mrhs_coarsest_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int
             MRHS_CUDA(cudaMemset(W.gcro->err.ptr, 0, sizeof(int)));
             fail(MRHS_ERR_CUDA, "GCRO-DR: the QR algorithm of a harmonic Ritz problem did not converge");
         }
-    } else {
-        for (int c = 0; c < mg->p.coarse_cycles; ++c)
-            krylov_cycle(A, nullptr, b, x, nrhs, mg->p.coarse_m, W.solve, s, c == 0, nullptr);
     }
     check_wait_flags(mg->lev[l], s);
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_mg_setup_times(mrhs_mg *mg, int level, double out_ms[4]) {
+    API_TRY
+    if (!mg || !out_ms) fail(MRHS_ERR_INVALID, "non-null mg and output required");
+    if (level < 0 || level >= mg->nlev - 1) fail(MRHS_ERR_INVALID, "level must name a transfer l -> l+1");
+    for (int i = 0; i < 4; ++i) out_ms[i] = mg->setup_ms[level][i];
+    return ok();
+    API_CATCH
+}
+
+mrhs_status mrhs_coarsest_fused_info(mrhs_mg *mg, int *in_use, int *resident_ctas, int *sites) {
+    API_TRY
+    if (!mg || !in_use || !resident_ctas || !sites) fail(MRHS_ERR_INVALID, "non-null mg and outputs required");
+    DevGuard dg(mg->lat->device);
+    const int l = mg->nlev - 1;
+    *in_use = mg->work[l].fused ? 1 : 0;
+    *resident_ctas = l >= 1 ? CoarsestFused::resident_ctas(mg->lev[l], mg->nmax, mg->lat->device) : 0;
+    *sites = (int)mg->lev[l].V;
     return ok();
     API_CATCH
 }

@@ -74,6 +74,7 @@ class MgParams(C.Structure):
         ("coarse_smoother_evenodd", C.c_int),
         ("coarse_solver", C.c_int),
         ("coarse_recycle", C.c_int),
+        ("coarse_fused", C.c_int),
     ]
 
 
@@ -167,6 +168,8 @@ PROTOTYPES = {
     "mrhs_coarse_apply_schur": (_I, [_P, _I, _P, _P, _I, _P]),
     "mrhs_coarsest_solve": (_I, [_P, _P, _P, _I, _P]),
     "mrhs_coarsest_reset": (_I, [_P]),
+    "mrhs_coarsest_fused_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "mrhs_mg_setup_times": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "mrhs_debug_expire_waits": (_I, [_I]),
     "mrhs_solve": (_I, [_P, _P, _P, _I, _D, _P, C.POINTER(SolveStats), _P]),
     "mrhs_server_create": (_I, [C.POINTER(ServerParams), C.POINTER(_P)]),
@@ -395,6 +398,20 @@ def mrhs_coarse_apply_schur(mg, level, in_dev, out_dev, nrhs, stream=None):
 
 def mrhs_coarsest_solve(mg, b_dev, x_dev, nrhs, stream=None):
     _check(lib().mrhs_coarsest_solve(mg, _ptr(b_dev), _ptr(x_dev), int(nrhs), _stream(stream)))
+
+
+def mrhs_mg_setup_times(mg, level):
+    """setup milliseconds of transfer level -> level + 1: null vectors, orthonormalisation, Galerkin, 16-bit prep"""
+    out = (C.c_double * 4)()
+    _check(lib().mrhs_mg_setup_times(mg, int(level), out))
+    return list(out)
+
+
+def mrhs_coarsest_fused_info(mg):
+    """(in use, resident CTAs, coarsest sites) of the persistent coarsest kernel"""
+    a, b, c = C.c_int(), C.c_int(), C.c_int()
+    _check(lib().mrhs_coarsest_fused_info(mg, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
 
 
 def mrhs_coarsest_reset(mg):
