@@ -406,8 +406,7 @@ mrhs_status mrhs_mg_setup_times(mrhs_mg *mg, int level, double out_ms[4]);
  * *in_use 1 if it does; *resident_ctas the kernel's CTAs that fit on the
  * device at once (one per SM: it holds tensor memory; 0 without a 16-bit
  * tensor-core coarsest level); *sites the coarsest level's sites, which the
- * CTAs share, up to 4 each (one tensor-memory accumulator per site; 8 at
- * max_rhs <= 16). */
+ * CTAs share, up to 2 each (each staged in shared memory). */
 mrhs_status mrhs_coarsest_fused_info(mrhs_mg *mg, int *in_use, int *resident_ctas, int *sites);
 
 /* One MG V-cycle z = M^{-1} v on the fine level (Sec. 8 preconditioner),

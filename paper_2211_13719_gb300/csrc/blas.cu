@@ -696,8 +696,25 @@ void multi_dot(mrhs_precision p, const void *basis, int64_t stride, int k, const
     }
 }
 
+// hn2 = beta^2 = max(||w||^2 - sum_j |h_j|^2, 1e-6 ||w||^2) and nn = 1 per RHS: the Hessenberg
+// entry of a last Arnoldi step whose normalised vector is never used
+__global__ void k_pythag_norm(const double2 *__restrict__ h, int k, const double *__restrict__ nrm2,
+                              double *__restrict__ hn2, double *__restrict__ nn, int n) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    double hh = 0.0;
+    for (int j = 0; j < k; ++j) {
+        const double2 c = h[(int64_t)j * n + r];
+        hh += c.x * c.x + c.y * c.y;
+    }
+    const double w2 = nrm2[r];
+    hn2[r] = fmax(w2 - hh, 1e-6 * w2);
+    nn[r] = 1.0;
+}
+
 void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, int k, void *w, int64_t rows, int n,
-                         double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s) {
+                         double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s,
+                         bool need_vector) {
     check_n(n);
     const int pw = pair_width(p, n, {basis, w}, stride);
     RedGeom g0 = red_geom(rows, n, pw);
@@ -740,6 +757,11 @@ void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, in
         }
         MRHS_LAUNCHED("k_dots_norm");
         break;
+    }
+    if (!need_vector) {
+        k_pythag_norm<<<ceil_div(n, 64), 64, 0, s>>>(h, k, nrm2, hn2, nn, n);
+        MRHS_LAUNCHED("k_pythag_norm");
+        return;
     }
     // subtract, normalise
     for (int j0 = 0; j0 < k || j0 == 0; j0 += KCHUNK) {

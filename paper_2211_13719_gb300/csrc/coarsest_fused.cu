@@ -10,14 +10,19 @@
 // update -- each bound by its launch and its grid-wide reduction, not by the
 // bytes it moves.  Here one cooperative launch runs the whole cycle:
 //
-//  * One CTA per coarse site, all resident at once.  A CTA owns its site's
-//    64 rows of every field, so the Krylov basis never crosses CTAs.  What
-//    does: the packed 16-bit image of the newest basis vector (the stencil's
-//    neighbour input), per-CTA partial sums, and per-RHS scalars.
+//  * One 512-thread CTA per SM, all resident at once (a kernel that holds
+//    tensor memory is resident one CTA per SM for the occupancy calculator
+//    and the cooperative launch), each owning one or two coarse sites.  A
+//    CTA owns its sites' 64 rows of every field, so the Krylov basis never
+//    crosses CTAs.  What does: the packed 16-bit image of the newest basis
+//    vector (the stencil's neighbour input), per-CTA partial sums, and
+//    per-RHS scalars.
 //  * The stencil of a step is the tcgen05 MMA of the coarse stencil kernel:
 //    link and neighbour tiles through a bulk-copy ring, FP32 accumulation in
-//    tensor memory allocated once for the launch.  Its result stays in
-//    shared memory for the dots and the update of the same step.
+//    tensor memory (one accumulator per own site) allocated once for the
+//    launch.  Its result, scaled to w = A v_j, stays in shared memory for
+//    the dots and the update of the same step.  While thread 0 streams the
+//    stencil, another warp does the Givens update of the previous column.
 //  * Grid-wide barriers (a monotonic arrival counter; every wait bounded)
 //    separate the three phases of a step: (1) stencil + partial dots,
 //    (2) the sum of the partials of each RHS column by the column's owner
@@ -55,7 +60,7 @@ constexpr int A_TILE = MROWS * NC * 2;  // bytes of one 16-bit link tile
 constexpr int RING = 5;                 // bulk-copy ring depth
 constexpr int MMAX = 16;                // largest restart length
 constexpr int THREADS = 512;            // 16 warps: the row phases are bound by L2 latency
-constexpr int MAX_SITES = 8;            // most coarse sites of one CTA
+constexpr int MAX_SITES = 2;            // most coarse sites of one CTA (each staged in shared memory)
 constexpr uint32_t BAR_LIMIT = 1u << 22;  // polls of a grid barrier before it gives up
 constexpr float IMG_BOUND = 256.f;        // largest image component
 
@@ -121,7 +126,7 @@ __device__ bool grid_barrier(const FusedArgs &a, unsigned &k, int *flag_sh) {
                 ok = false;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(20);
         }
         if (!ok) record_error(a);
         __threadfence();
@@ -149,6 +154,7 @@ __device__ void reduce_norms(const FusedArgs &a, double *red_d, double *eta) {
     const RowMap t(a.n);
     if (t.active) {
         double s = 0.0;
+        #pragma unroll 8
         for (int c = t.sub; c < a.G; c += t.RS) s += a.npart[(int64_t)c * a.n + t.r];
         red_d[t.sub * a.n + t.r] = s;
     }
@@ -273,26 +279,33 @@ __device__ bool stencil_issue(const FusedArgs &a, int cta, int ns, uint32_t sbas
 
 // shared-memory overlay of the ring once a step's MMAs are complete
 struct Overlay {
-    float *D;        // [128][ld] accumulator image
-    int ld;
-    uint8_t *tile;   // b_tile bytes: the site's packed image
+    float2 *W;       // [MAX_SITES][64][ldw]: the scaled stencil output w of each own site
+    int ldw;         // n + 1 (padding against bank conflicts)
+    float *Dhi;      // [64][ld]: accumulator rows 64..127 of one site while w is formed
+    int ld;          // npad + 1
+    uint8_t *tile;   // [MAX_SITES] x b_tile bytes: the own sites' packed images
     float2 *red;     // [RS][MMAX + 1][n] partial sums of the row slices
     float2 *coef;    // [MMAX][n] h (or y) coefficients
 };
 
 __host__ __device__ inline size_t overlay_bytes(int n, int npad, Overlay *o, uint8_t *base) {
-    const int ld = npad + 1;
+    const int ldw = n + 1, ld = npad + 1;
+    auto up = [](size_t v) { return (v + 127) & ~size_t(127); };
     size_t off = 0;
-    const size_t d_bytes = (size_t)MROWS * ld * sizeof(float);
-    off += (d_bytes + 127) & ~size_t(127);
+    const size_t w_off = off;
+    off += up(sizeof(float2) * (size_t)MAX_SITES * NC * ldw);
+    const size_t d_off = off;
+    off += up(sizeof(float) * (size_t)NC * ld);
     const size_t tile_off = off;
-    off += (size_t)npad * 128;
+    off += (size_t)MAX_SITES * npad * 128;
     const size_t red_off = off;
     off += sizeof(float2) * (size_t)THREADS * (MMAX + 1);  // >= (THREADS / n) slices x n columns, any n
     const size_t coef_off = off;
     off += sizeof(float2) * (size_t)MMAX * n;
     if (o) {
-        o->D = reinterpret_cast<float *>(base);
+        o->W = reinterpret_cast<float2 *>(base + w_off);
+        o->ldw = ldw;
+        o->Dhi = reinterpret_cast<float *>(base + d_off);
         o->ld = ld;
         o->tile = base + tile_off;
         o->red = reinterpret_cast<float2 *>(base + red_off);
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
     // a site's accumulator (times its link scale) into A v_j
     __shared__ float sig_sh[64], inv_sh[64], cinv_sh[64];
 
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int cta = blockIdx.x;
     const int n = a.n, m = a.m;
     const int ns = (a.V - cta + a.G - 1) / a.G;  // this CTA's sites: cta + ls * G, ls < ns
@@ -334,6 +347,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
     uint32_t q0 = 0;
     auto site_of = [&](int ls) { return (int64_t)cta + (int64_t)ls * a.G; };
     auto row0_of = [&](int ls) { return site_of(ls) * NC * n; };
+    auto tile_of = [&](int ls) { return ov.tile + (size_t)ls * a.b_tile; };
+    auto Wrow = [&](int ls, int k) { return ov.W + ((size_t)ls * NC + k) * ov.ldw; };
 
     if (tid == 0) {
         for (int s = 0; s < RING; ++s) {
@@ -350,17 +365,38 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
     fence_after_sync();
     const uint32_t tmem = tmem_base_sh;
 
-    // accumulator of local site ls (tensor memory) -> shared D; ends with a CTA barrier
-    // (warp w reads tensor-memory lanes 32 (w % 4) .. + 31; the warps of one lane quarter split the columns)
-    auto stage = [&](int ls) {
+    // w of local site ls from its accumulator: Re w = sc (D[K][r] - D[64+K][n+r]), Im w = sc (D[64+K][r] +
+    // D[K][n+r]) with sc = link scale * cinv[r].  Warp w reads tensor-memory lanes 32 (w % 4) .. + 31 and
+    // every fourth 16-column chunk from chunk w / 4: the upper lanes first into Dhi, then the lower ones
+    // combine.  Ends with a CTA barrier.
+    auto stage_w = [&](int ls) {
         fence_after_sync();
-        const int lane0 = 32 * (warp & 3), grp = warp >> 2;
-        const int row = lane0 + (tid & 31);
-        for (int c0 = 16 * grp; c0 < a.npad; c0 += 16 * (THREADS / 128)) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)lane0 << 16) + (uint32_t)(ls * a.cols_site + c0), v);
+        const int q = warp & 3, grp = warp >> 2;
+        const float ls_scale = a.lscale[site_of(ls)];
+        if (q >= 2) {
+            const int K = 32 * (q - 2) + lane;
+            for (int c0 = 16 * grp; c0 < a.npad; c0 += 16 * (THREADS / 128)) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ls * a.cols_site + c0), v);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) ov.D[row * ov.ld + c0 + i] = v[i];
+                for (int i = 0; i < 16; ++i) ov.Dhi[K * ov.ld + c0 + i] = v[i];
+            }
+        }
+        __syncthreads();
+        if (q < 2) {
+            const int K = 32 * q + lane;
+            float2 *Wk = Wrow(ls, K);
+            float *Wf = reinterpret_cast<float *>(Wk);
+            for (int c0 = 16 * grp; c0 < a.npad; c0 += 16 * (THREADS / 128)) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ls * a.cols_site + c0), v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + i;
+                    if (c < n) Wf[2 * c] = ls_scale * cinv_sh[c] * (v[i] - ov.Dhi[K * ov.ld + n + c]);
+                    else if (c < 2 * n) Wf[2 * (c - n) + 1] = ls_scale * cinv_sh[c - n] * (ov.Dhi[K * ov.ld + c - n] + v[i]);
+                }
+            }
         }
         fence_before_sync();
         __syncthreads();
@@ -368,10 +404,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
     // the packed tile of local site ls -> its image in global memory (after the tile is complete)
     auto tile_out = [&](int ls) {
         uint4 *dst = reinterpret_cast<uint4 *>(a.img + (size_t)site_of(ls) * a.b_tile);
-        for (int i = tid; i < a.npad * 8; i += THREADS) dst[i] = reinterpret_cast<const uint4 *>(ov.tile)[i];
+        const uint4 *src = reinterpret_cast<const uint4 *>(tile_of(ls));
+        for (int i = tid; i < a.npad * 8; i += THREADS) dst[i] = src[i];
     };
-    auto tile_zero = [&]() {
-        for (int i = tid; i < a.npad * 8; i += THREADS) reinterpret_cast<uint4 *>(ov.tile)[i] = make_uint4(0, 0, 0, 0);
+    auto tiles_zero = [&]() {
+        uint4 *t4 = reinterpret_cast<uint4 *>(ov.tile);
+        for (int i = tid; i < ns * a.npad * 8; i += THREADS) t4[i] = make_uint4(0, 0, 0, 0);
+    };
+    auto pack = [&](int ls, int k, int r, float re, float im) {
+        *reinterpret_cast<uint16_t *>(tile_of(ls) + sw128_offset(r, k)) = to16<FMT>(re);
+        *reinterpret_cast<uint16_t *>(tile_of(ls) + sw128_offset(n + r, k)) = to16<FMT>(im);
     };
     // per-CTA norm partial: the row slices' sums in slice order
     auto norm_partial_out = [&](float un) {
@@ -390,6 +432,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
         float acc = 0.f;
         if (t.active)
             for (int ls = 0; ls < ns; ++ls)
+#pragma unroll 4
                 for (int k = t.sub; k < NC; k += t.RS) {
                     const int64_t e = row0_of(ls) + (int64_t)k * n + t.r;
                     const float2 v = a.b[e];
@@ -402,20 +445,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
     if (ok) {
         reduce_norms(a, red_d, eta_sh);
         if (tid < n) sig_sh[tid] = eta_sh[tid] > 0.0 ? (float)(IMG_BOUND / eta_sh[tid]) : 1.f;
-        for (int ls = 0; ls < ns; ++ls) {
-            tile_zero();
-            __syncthreads();
-            if (t.active)
+        tiles_zero();
+        __syncthreads();
+        if (t.active)
+            for (int ls = 0; ls < ns; ++ls)
+#pragma unroll 4
                 for (int k = t.sub; k < NC; k += t.RS) {
                     const float2 v = a.Vb[row0_of(ls) + (int64_t)k * n + t.r];
                     const float sc = sig_sh[t.r];
-                    *reinterpret_cast<uint16_t *>(ov.tile + sw128_offset(t.r, k)) = to16<FMT>(v.x * sc);
-                    *reinterpret_cast<uint16_t *>(ov.tile + sw128_offset(n + t.r, k)) = to16<FMT>(v.y * sc);
+                    pack(ls, k, t.r, v.x * sc, v.y * sc);
                 }
-            __syncthreads();
-            tile_out(ls);
-            __syncthreads();
-        }
+        __syncthreads();
+        for (int ls = 0; ls < ns; ++ls) tile_out(ls);
         if (cta == 0 && tid < n) a.sig[tid] = sig_sh[tid];
         fence_proxy_async_global();
         ok = grid_barrier(a, nbar, &flag_sh);
@@ -423,7 +464,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
 
     // ---- Arnoldi steps
     for (int j = 0; ok && j < m; ++j) {
-        // (S) eta_j = ||u_j||, v_j = u_j / eta_j on own rows; owners fold column j - 1 (h_{j,j-1} = eta_j)
+        // (S) eta_j = ||u_j||; the per-RHS scalars of this step
         reduce_norms(a, red_d, eta_sh);
         if (tid < n) {
             const double eta = eta_sh[tid];
@@ -433,17 +474,16 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
             cinv_sh[tid] = eta > 0.0 ? (float)(1.0 / ((double)sg * eta)) : 0.f;
         }
         __syncthreads();
-        {
-            float2 *Vj = a.Vb + (int64_t)j * F;
-            if (t.active)
-                for (int ls = 0; ls < ns; ++ls)
-                    for (int k = t.sub; k < NC; k += t.RS) {
-                        const int64_t e = row0_of(ls) + (int64_t)k * n + t.r;
-                        const float2 v = Vj[e];
-                        Vj[e] = make_float2(v.x * inv_sh[t.r], v.y * inv_sh[t.r]);
-                    }
-        }
-        if (tid == 0)
+        // (1) thread 0 streams the stencil of the own sites through the tensor cores; meanwhile thread 32
+        // folds column j - 1 into the owned columns' Givens state (h_{j,j-1} = eta_j) and every thread
+        // normalises its rows of v_j = u_j / eta_j
+        if (tid == 0) {
+            fence_proxy_async_global();  // the neighbours' images were written through the generic proxy
+            if (!stencil_issue(a, cta, ns, sbase, full0, empty0, done, tmem, q0)) {
+                record_error(a);
+                abort_sh = 1;
+            }
+        } else if (tid == 32) {
             for (int r = cta; r < n; r += a.G) {
                 if (j == 0) {
                     double2 *g = a.g + (int64_t)r * (m + 1);
@@ -453,14 +493,17 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
                     givens_column(a, r, j - 1, eta_sh[r]);
                 }
             }
-
-        // (1) w = A v_j on the tensor cores for every own site; partial dots <v_i, w> (i <= j), ||w||^2
-        if (tid == 0) {
-            fence_proxy_async_global();  // the neighbours' images were written through the generic proxy
-            if (!stencil_issue(a, cta, ns, sbase, full0, empty0, done, tmem, q0)) {
-                record_error(a);
-                abort_sh = 1;
-            }
+        }
+        {
+            float2 *Vj = a.Vb + (int64_t)j * F;
+            if (t.active)
+                for (int ls = 0; ls < ns; ++ls)
+#pragma unroll 4
+                    for (int k = t.sub; k < NC; k += t.RS) {
+                        const int64_t e = row0_of(ls) + (int64_t)k * n + t.r;
+                        const float2 v = Vj[e];
+                        Vj[e] = make_float2(v.x * inv_sh[t.r], v.y * inv_sh[t.r]);
+                    }
         }
         __syncthreads();
         const bool mma_ok = mbar_wait(done, j & 1);
@@ -473,31 +516,28 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
             ok = false;
             break;
         }
+        for (int ls = 0; ls < ns; ++ls) stage_w(ls);
+        // partial dots <v_i, w> (i <= j) and ||w||^2 over the own rows
         {
             float2 acc[MMAX];
 #pragma unroll
             for (int i = 0; i < MMAX; ++i) acc[i] = make_float2(0.f, 0.f);
             float wn = 0.f;
-            for (int ls = 0; ls < ns; ++ls) {
-                stage(ls);
-                if (t.active) {
-                    const float sc = a.lscale[site_of(ls)] * cinv_sh[t.r];
+            if (t.active)
+                for (int ls = 0; ls < ns; ++ls)
+#pragma unroll 4
                     for (int k = t.sub; k < NC; k += t.RS) {
-                        const float *Dk = ov.D + k * ov.ld, *Dk2 = ov.D + (NC + k) * ov.ld;
-                        const float wr = sc * (Dk[t.r] - Dk2[n + t.r]), wi = sc * (Dk2[t.r] + Dk[n + t.r]);
-                        wn = fmaf(wr, wr, fmaf(wi, wi, wn));
+                        const float2 w = Wrow(ls, k)[t.r];
+                        wn = fmaf(w.x, w.x, fmaf(w.y, w.y, wn));
                         const int64_t e = row0_of(ls) + (int64_t)k * n + t.r;
 #pragma unroll
                         for (int i = 0; i < MMAX; ++i)
                             if (i <= j) {
                                 const float2 v = a.Vb[(int64_t)i * F + e];
-                                acc[i].x = fmaf(v.x, wr, fmaf(v.y, wi, acc[i].x));
-                                acc[i].y = fmaf(v.x, wi, fmaf(-v.y, wr, acc[i].y));
+                                acc[i].x = fmaf(v.x, w.x, fmaf(v.y, w.y, acc[i].x));
+                                acc[i].y = fmaf(v.x, w.y, fmaf(-v.y, w.x, acc[i].y));
                             }
                     }
-                }
-                __syncthreads();  // D is restaged for the next site
-            }
             if (t.active) {
 #pragma unroll
                 for (int i = 0; i < MMAX; ++i)
@@ -521,9 +561,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
         // (2) owners: h_{i,j} = sum over CTAs (i <= j), and the next image scale 256 / ||w||
         for (int r = cta; r < n; r += a.G) {
             for (int i0 = 0; i0 < j + 2; i0 += THREADS / 32) {
-                const int i = i0 + warp, sub = tid & 31;  // one warp per Hessenberg entry
+                const int i = i0 + warp, sub = lane;  // one warp per Hessenberg entry
                 double sx = 0.0, sy = 0.0;
                 if (i < j + 2)
+#pragma unroll 8
                     for (int c = sub; c < a.G; c += 32) {
                         const double2 p = a.part[((int64_t)c * (m + 1) + i) * n + r];
                         sx += p.x;
@@ -546,18 +587,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
             const double2 h = a.hcol[e];
             ov.coef[e] = make_float2((float)h.x, (float)h.y);
         }
-        if (tid < n) sig_sh[tid] = a.sig[tid];  // sigma_{j+1}; cinv_sh still holds step j's factor
+        if (tid < n) sig_sh[tid] = a.sig[tid];  // sigma_{j+1}
+        tiles_zero();
+        __syncthreads();
         {
             float un = 0.f;
             float2 *U = a.Vb + (int64_t)(j + 1) * F;
-            for (int ls = 0; ls < ns; ++ls) {
-                tile_zero();
-                stage(ls);
-                if (t.active) {
-                    const float sc = a.lscale[site_of(ls)] * cinv_sh[t.r], si = sig_sh[t.r];
+            if (t.active) {
+                const float si = sig_sh[t.r];
+                for (int ls = 0; ls < ns; ++ls)
+#pragma unroll 4
                     for (int k = t.sub; k < NC; k += t.RS) {
-                        const float *Dk = ov.D + k * ov.ld, *Dk2 = ov.D + (NC + k) * ov.ld;
-                        float ur = sc * (Dk[t.r] - Dk2[n + t.r]), ui = sc * (Dk2[t.r] + Dk[n + t.r]);
+                        const float2 w = Wrow(ls, k)[t.r];
+                        float ur = w.x, ui = w.y;
                         const int64_t e = row0_of(ls) + (int64_t)k * n + t.r;
 #pragma unroll
                         for (int i = 0; i < MMAX; ++i)
@@ -569,14 +611,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
                             }
                         U[e] = make_float2(ur, ui);
                         un = fmaf(ur, ur, fmaf(ui, ui, un));
-                        *reinterpret_cast<uint16_t *>(ov.tile + sw128_offset(t.r, k)) = to16<FMT>(ur * si);
-                        *reinterpret_cast<uint16_t *>(ov.tile + sw128_offset(n + t.r, k)) = to16<FMT>(ui * si);
+                        pack(ls, k, t.r, ur * si, ui * si);
                     }
-                }
-                __syncthreads();
-                tile_out(ls);
-                __syncthreads();
             }
+            __syncthreads();
+            for (int ls = 0; ls < ns; ++ls) tile_out(ls);
             norm_partial_out(un);
             fence_proxy_async_global();
         }
@@ -601,6 +640,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
         __syncthreads();
         if (t.active)
             for (int ls = 0; ls < ns; ++ls)
+#pragma unroll 4
                 for (int k = t.sub; k < NC; k += t.RS) {
                     const int64_t e = row0_of(ls) + (int64_t)k * n + t.r;
                     float xr = 0.f, xi = 0.f;

@@ -164,8 +164,11 @@ void krylov_givens(KrylovState &ks, int j, int n, cudaStream_t s, bool single_pa
 // h = V^H w and ||w||^2 together, then w <- (w - V h) / beta with
 // beta^2 = ||w||^2 - |h|^2 (hn2 <- beta^2), nn <- ||w_new||^2, and a fix-up that
 // rescales columns whose new norm is off by more than 1% (cancellation).
+// need_vector false: only h, ||w||^2, hn2 (Pythagoras) and nn = 1 -- for a last step
+// whose new basis vector is never read; w is left as it was.
 void orthonormalize_step(mrhs_precision p, const void *basis, int64_t stride, int k, void *w, int64_t rows, int n,
-                         double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s);
+                         double2 *h, double *nrm2, double *hn2, double *nn, Scratch &sc, cudaStream_t s,
+                         bool need_vector = true);
 // y = R^{-1} g for the first `j` columns
 void krylov_solve(KrylovState &ks, int j, int n, cudaStream_t s);
 

@@ -192,8 +192,11 @@ int krylov_cycle(Op &A, Precond *M, const float2 *b, float2 *x, int n, int m, KW
         }
         float2 *wj = w.Vj(j + 1, n);
         A.apply(zj, wj, n, s);
+        // a fixed-length cycle (no convergence check) never reads v_m: its last step needs only
+        // h_{m,m-1}, from Pythagoras, and skips the subtract-and-normalise pass
+        const bool need_vector = chk || j + 1 < m;
         orthonormalize_step(MRHS_FP32, V0, F, j + 1, wj, rows, n, ks.hcol.as<double2>(), ks.nrm2w.as<double>(),
-                            ks.hn2.as<double>(), ks.nn.as<double>(), w.sc, s);
+                            ks.hn2.as<double>(), ks.nn.as<double>(), w.sc, s, need_vector);
         krylov_givens(ks, j, n, s, true);
         if (chk && chk->test(ks, n, s)) {
             steps = j + 1;
