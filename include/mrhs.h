@@ -318,6 +318,16 @@ typedef struct {
                                               coarse_m <= 16, every coarsest site's
                                               CTA resident); else, and with 0, one
                                               launch per operation                */
+    int galerkin_tc;                       /* the restriction R = P^dagger of the
+                                              Galerkin build R D P: on the tensor
+                                              cores with every operand split into two
+                                              FP16 numbers, three MMA terms, FP32
+                                              accumulation (<= 32 null vectors; the
+                                              links to about 1e-5 relative) -- 1: on
+                                              16-bit hierarchies, whose links are
+                                              rounded to 16 bits afterwards; 2: on
+                                              every hierarchy; 0: never (CUDA cores,
+                                              FP32)                                */
 } mrhs_mg_params;
 
 /* Fill `p` with the defaults used for the 24^3x64 three-level workload. */

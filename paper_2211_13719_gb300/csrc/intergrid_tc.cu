@@ -41,6 +41,9 @@ constexpr int IG_ROWS = 128;              // MMA M
 constexpr int IG_K = 64;                  // one swizzle atom of 16-bit values
 constexpr int IG_TILE = IG_ROWS * IG_K * 2;  // 16 KB
 constexpr int IG_BTILE = 64 * IG_K * 2;      // 8 KB (restriction: 64 columns of P)
+// scale of the lo parts of split-precision operands: the rounding error of an FP16 number is at
+// most 2^-11 of it, so lo * 2^11 keeps the magnitude of hi and stays a normal FP16 number
+constexpr float SPLIT_LO = 2048.f;
 
 struct IgArgs {
     int L[4], Lc[4], B[4];
@@ -92,6 +95,9 @@ __global__ void k_pack_prolong_tiles(const float2 *__restrict__ P, uint8_t *__re
 }
 
 // restriction B tiles: [Vc][2][chunks] x (64 rows kp, 64 columns rho)
+// LO: the FP16 rounding error of each value instead, times 2^11 (SPLIT_LO), so that it stays a
+// normal FP16 number: the second term of a split-precision product
+template <bool LO>
 __global__ void k_pack_restrict_tiles(const float2 *__restrict__ P, uint8_t *__restrict__ img, IgArgs a, int64_t Vc) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per_tile = 64LL * IG_K;
@@ -103,7 +109,8 @@ __global__ void k_pack_restrict_tiles(const float2 *__restrict__ P, uint8_t *__r
     const int chi = (int)((tile / a.chunks) % 2);
     const int64_t xc = tile / (2 * a.chunks);
     const float v = pblock(P, a, xc, chi, c * IG_K + rl, kp);
-    *reinterpret_cast<uint16_t *>(img + tile * IG_BTILE + sw128_offset(kp, rl)) = to16<0>(v);
+    const float x = LO ? (v - __half2float(__float2half_rn(v))) * SPLIT_LO : v;
+    *reinterpret_cast<uint16_t *>(img + tile * IG_BTILE + sw128_offset(kp, rl)) = to16<0>(x);
 }
 
 __device__ __forceinline__ void atomic_max_pos(unsigned *addr, float v) { atomicMax(addr, __float_as_uint(v)); }
@@ -112,6 +119,15 @@ __device__ __forceinline__ void atomic_max_pos(unsigned *addr, float v) { atomic
 __device__ __forceinline__ uint32_t pack_half2(float lo, float hi) {
     const __half2 h = __floats2half2_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// hi = fp16 of two floats, lo = fp16 of their rounding errors times SPLIT_LO (halves: a low, b high)
+__device__ __forceinline__ void split_half2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn((a - hf.x) * SPLIT_LO, (b - hf.y) * SPLIT_LO);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
 // rowoff[rho] = fine row index (site * dof + component) of row rho of (aggregate xc, chirality chi)
@@ -291,14 +307,24 @@ __global__ void __launch_bounds__(IG_PTHREADS) k_prolong_tc(const float2 *__rest
 
 // ----------------------------------------------------------- restriction
 
-// smem: [A tiles 2 x 128 x 64 (field) | B tiles 2 x 64 x 64 (P) | row table R ints];
-// the epilogue's D staging (128 x 65 floats) reuses the A and B tiles.
-// Each thread loads all of its share of the next 64-row chunk into registers
-// before it converts the current one.
-template <int VEC>
+// smem: [A tiles 2 x NS x 128 x 64 (field) | B tiles 2 x NS x 64 x 64 (P) | row table R ints]
+// (NS = 2 with SPLIT: hi and lo parts); the epilogue's D staging (128 x 65
+// floats) reuses the A and B tiles.  Each thread loads all of its share of
+// the next 64-row chunk into registers before it converts the current one.
+//
+// SPLIT (the Galerkin construction, where the result must keep FP32
+// accuracy): every operand is the sum of two FP16 numbers, hi = fp16(x) and
+// lo = fp16((x - hi) 2^11) 2^-11, 22 significant bits.  The product takes
+// hi.hi into one FP32 accumulator and hi.lo + lo.hi into a second (the lo
+// parts scaled by 2^11 stay normal FP16 numbers even where x is small); the
+// epilogue adds acc0 + 2^-11 acc1.  The dropped lo.lo term is 2^-22 of the
+// product.
+template <int VEC, bool SPLIT>
 __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict__ fine, const uint8_t *__restrict__ RB,
+                                                     const uint8_t *__restrict__ RBlo,
                                                      float2 *__restrict__ coarse, const float *__restrict__ bound,
                                                      IgArgs a, int *__restrict__ err) {
+    constexpr int NS = SPLIT ? 2 : 1;
     using LT = typename std::conditional<VEC == 2, float4, float2>::type;
     extern __shared__ uint8_t smem_raw[];
     __shared__ uint64_t bars[4];  // [0, 1]: MMAs of buffer b complete; [2, 3]: B tile b landed
@@ -310,12 +336,12 @@ __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict
     const int chi = blockIdx.y;
     const int n = a.n, N = a.N;
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint8_t *At = base;
-    uint8_t *Bt = base + 2 * IG_TILE;
+    uint8_t *At = base;                  // buffer b, part h at At + (b * NS + h) * IG_TILE
+    uint8_t *Bt = base + 2 * NS * IG_TILE;  // buffer b, part h at Bt + (b * NS + h) * IG_BTILE
     float *Ds = reinterpret_cast<float *>(base);
     constexpr int ld = 65;
-    int *rowoff = reinterpret_cast<int *>(Bt + 2 * IG_BTILE);
-    constexpr uint32_t cols = 64;
+    int *rowoff = reinterpret_cast<int *>(Bt + 2 * NS * IG_BTILE);
+    constexpr uint32_t cols = SPLIT ? 128 : 64;  // SPLIT: acc0 at column 0, acc1 at column 64
 
     fill_rows(rowoff, a, xc, chi);
     if (tid < n) {
@@ -329,8 +355,9 @@ __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tmem_alloc(smem_u32(&tmem_sh), cols);
-    // rows j >= 2n of both A buffers stay zero
-    for (int i = tid; i < 2 * IG_TILE / 16; i += blockDim.x) reinterpret_cast<uint4 *>(At)[i] = make_uint4(0, 0, 0, 0);
+    // rows j >= 2n of the A buffers stay zero
+    for (int i = tid; i < 2 * NS * IG_TILE / 16; i += blockDim.x)
+        reinterpret_cast<uint4 *>(At)[i] = make_uint4(0, 0, 0, 0);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -370,7 +397,7 @@ __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict
             for (int q = 0; q < VEC; ++q) {
                 const int r = VEC * p + q;
                 const float sc = inv_s[r];
-                uint32_t re[4], im[4];
+                uint32_t re[4], im[4], rel[4], iml[4];
 #pragma unroll
                 for (int j = 0; j < 8; j += 2) {
                     float2 x0, x1;
@@ -382,17 +409,29 @@ __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict
                         x0 = buf[v][j];
                         x1 = buf[v][j + 1];
                     }
-                    re[j / 2] = pack_half2(x0.x * sc, x1.x * sc);
-                    im[j / 2] = pack_half2(x0.y * sc, x1.y * sc);
+                    if constexpr (SPLIT) {
+                        split_half2(x0.x * sc, x1.x * sc, re[j / 2], rel[j / 2]);
+                        split_half2(x0.y * sc, x1.y * sc, im[j / 2], iml[j / 2]);
+                    } else {
+                        re[j / 2] = pack_half2(x0.x * sc, x1.x * sc);
+                        im[j / 2] = pack_half2(x0.y * sc, x1.y * sc);
+                    }
                 }
                 *reinterpret_cast<uint4 *>(Ab + sw128_offset(r, 8 * kc)) = make_uint4(re[0], re[1], re[2], re[3]);
                 *reinterpret_cast<uint4 *>(Ab + sw128_offset(n + r, 8 * kc)) = make_uint4(im[0], im[1], im[2], im[3]);
+                if constexpr (SPLIT) {
+                    uint8_t *Al = Ab + IG_TILE;
+                    *reinterpret_cast<uint4 *>(Al + sw128_offset(r, 8 * kc)) = make_uint4(rel[0], rel[1], rel[2], rel[3]);
+                    *reinterpret_cast<uint4 *>(Al + sw128_offset(n + r, 8 * kc)) =
+                        make_uint4(iml[0], iml[1], iml[2], iml[3]);
+                }
             }
         }
     };
 
     const uint32_t idesc = idesc_16bit(IG_ROWS, 64, 0);
     const uint8_t *rb = RB + ((xc * 2 + chi) * (int64_t)a.chunks) * IG_BTILE;
+    const uint8_t *rbl = SPLIT ? RBlo + ((xc * 2 + chi) * (int64_t)a.chunks) * IG_BTILE : nullptr;
     // thread 0's record of what it has in flight, for a clean exit after an expired wait
     int copies = 0, copies_waited = 0, mmas = 0;
     load_chunk(0);
@@ -406,11 +445,14 @@ __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict
             if (abort_sh) break;
         }
         if (tid == 0) {
-            mbar_expect_tx(smem_u32(&bars[2 + b]), IG_BTILE);
-            bulk_g2s(smem_u32(Bt + b * IG_BTILE), rb + (int64_t)c * IG_BTILE, IG_BTILE, smem_u32(&bars[2 + b]));
+            mbar_expect_tx(smem_u32(&bars[2 + b]), NS * IG_BTILE);
+            bulk_g2s(smem_u32(Bt + b * NS * IG_BTILE), rb + (int64_t)c * IG_BTILE, IG_BTILE, smem_u32(&bars[2 + b]));
+            if constexpr (SPLIT)
+                bulk_g2s(smem_u32(Bt + (b * NS + 1) * IG_BTILE), rbl + (int64_t)c * IG_BTILE, IG_BTILE,
+                         smem_u32(&bars[2 + b]));
             ++copies;
         }
-        convert_chunk(At + b * IG_TILE);
+        convert_chunk(At + b * NS * IG_TILE);
         if (c + 1 < a.chunks) load_chunk(c + 1);
         fence_async_smem();
         __syncthreads();
@@ -420,10 +462,17 @@ __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict
             } else {
                 ++copies_waited;
                 fence_after_sync();
+                const uint32_t a0 = smem_u32(At + b * NS * IG_TILE), b0 = smem_u32(Bt + b * NS * IG_BTILE);
 #pragma unroll
-                for (int kk = 0; kk < IG_K / 16; ++kk)
-                    mma_16bit(tmem, sdesc(smem_u32(At + b * IG_TILE) + kk * 32),
-                              sdesc(smem_u32(Bt + b * IG_BTILE) + kk * 32), idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < IG_K / 16; ++kk) {
+                    mma_16bit(tmem, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                    if constexpr (SPLIT) {
+                        // the hi.lo and lo.hi terms, into the second accumulator
+                        mma_16bit(tmem + 64, sdesc(a0 + kk * 32), sdesc(b0 + IG_BTILE + kk * 32), idesc,
+                                  (c > 0 || kk > 0) ? 1u : 0u);
+                        mma_16bit(tmem + 64, sdesc(a0 + IG_TILE + kk * 32), sdesc(b0 + kk * 32), idesc, 1u);
+                    }
+                }
                 mma_commit(smem_u32(&bars[b]));
                 ++mmas;
             }
@@ -441,6 +490,15 @@ __global__ void __launch_bounds__(128, 4) k_restrict_tc(const float2 *__restrict
         float v[4][16];
 #pragma unroll
         for (int c0 = 0; c0 < 4; ++c0) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(16 * c0), v[c0]);
+        if constexpr (SPLIT) {
+#pragma unroll
+            for (int c0 = 0; c0 < 4; ++c0) {
+                float u[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(64 + 16 * c0), u);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[c0][i] = fmaf(u[i], 1.f / SPLIT_LO, v[c0][i]);
+            }
+        }
         // the tile buffers are free: every MMA reading them has completed
 #pragma unroll
         for (int c0 = 0; c0 < 4; ++c0)
@@ -508,7 +566,10 @@ size_t prolong_smem(int npad, int R) {
     const size_t bt = ((size_t)npad * 128 + 1023) & ~size_t(1023);
     return 1024 + bt + (size_t)IG_STAGES * IG_TILE + sizeof(int) * (size_t)R;
 }
-size_t restrict_smem(int R) { return 1024 + 2 * IG_TILE + 2 * IG_BTILE + sizeof(int) * (size_t)R; }
+size_t restrict_smem(int R, bool split = false) {
+    const size_t ns = split ? 2 : 1;
+    return 1024 + 2 * ns * IG_TILE + 2 * ns * IG_BTILE + sizeof(int) * (size_t)R;
+}
 
 // 16-byte loads and stores of RHS pairs need an even n and a 16-byte aligned field
 bool paired(const void *field, int n) { return n % 2 == 0 && (reinterpret_cast<uintptr_t>(field) & 15u) == 0; }
@@ -521,9 +582,17 @@ template <typename K> void allow_smem(K kernel, size_t bytes) {
 
 bool intergrid_tc_supported(const Level &f) { return f.N >= 1 && f.N <= 32 && f.asize * (f.dof / 2) <= IG_MAX_ROWS; }
 
-void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s) {
+void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s, bool split) {
     if (!intergrid_tc_supported(f)) fail(MRHS_ERR_INVALID, "tensor-core intergrid needs at most 32 null vectors");
     const IgArgs a = ig_args(f, c, 1);
+    if (split && !f.RBlo.ptr) {
+        f.RBlo.alloc((size_t)c.V * 2 * a.chunks * IG_BTILE);
+        const int64_t nr = c.V * 2 * a.chunks * 64LL * IG_K;
+        k_pack_restrict_tiles<true><<<ceil_div(nr, 256), 256, 0, s>>>(f.P32.as<float2>(), f.RBlo.as<uint8_t>(), a,
+                                                                       c.V);
+        MRHS_LAUNCHED("k_pack_restrict_tiles");
+    }
+    if (f.PA.ptr) return;  // the tiles of this prolongator are packed already
     f.PA.alloc((size_t)c.V * 2 * a.tiles * IG_TILE);
     f.RB.alloc((size_t)c.V * 2 * a.chunks * IG_BTILE);
     f.IgErr.alloc(sizeof(int));
@@ -538,14 +607,14 @@ void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s) {
     k_pack_prolong_tiles<<<ceil_div(np, 256), 256, 0, s>>>(f.P32.as<float2>(), f.PA.as<uint8_t>(), a, c.V);
     MRHS_LAUNCHED("k_pack_prolong_tiles");
     const int64_t nr = c.V * 2 * a.chunks * 64LL * IG_K;
-    k_pack_restrict_tiles<<<ceil_div(nr, 256), 256, 0, s>>>(f.P32.as<float2>(), f.RB.as<uint8_t>(), a, c.V);
+    k_pack_restrict_tiles<false><<<ceil_div(nr, 256), 256, 0, s>>>(f.P32.as<float2>(), f.RB.as<uint8_t>(), a, c.V);
     MRHS_LAUNCHED("k_pack_restrict_tiles");
     MRHS_CUDA(cudaStreamSynchronize(s));  // the host array of ones is copied before it can go out of scope
 }
 
 void restrict_fields_tc(const Level &f, const Level &c, const float2 *fine, float2 *coarse, int n, int64_t ostride,
-                        bool unit_norm, cudaStream_t s) {
-    if (!f.RB.ptr) fail(MRHS_ERR_INVALID, "tensor-core restriction not prepared");
+                        bool unit_norm, cudaStream_t s, bool split) {
+    if (!f.RB.ptr || (split && !f.RBlo.ptr)) fail(MRHS_ERR_INVALID, "tensor-core restriction not prepared");
     if (n < 1 || n > 64) fail(MRHS_ERR_INVALID, "tensor-core restriction supports 1..64 RHS");
     IgArgs a = ig_args(f, c, n);
     a.ostride = ostride;
@@ -563,18 +632,23 @@ void restrict_fields_tc(const Level &f, const Level &c, const float2 *fine, floa
     }
     static bool attr = false;
     if (!attr) {
-        allow_smem(k_restrict_tc<1>, restrict_smem(IG_MAX_ROWS));
-        allow_smem(k_restrict_tc<2>, restrict_smem(IG_MAX_ROWS));
+        allow_smem(k_restrict_tc<1, false>, restrict_smem(IG_MAX_ROWS));
+        allow_smem(k_restrict_tc<2, false>, restrict_smem(IG_MAX_ROWS));
+        allow_smem(k_restrict_tc<1, true>, restrict_smem(IG_MAX_ROWS, true));
+        allow_smem(k_restrict_tc<2, true>, restrict_smem(IG_MAX_ROWS, true));
         attr = true;
     }
     const dim3 grid((unsigned)c.V, 2);
+    const uint8_t *rb = f.RB.as<uint8_t>(), *rbl = f.RBlo.as<uint8_t>();
+    const size_t smem = restrict_smem(a.R, split);
     MRHS_TIMED("k_restrict_tc", s);
-    if (paired(fine, n))
-        k_restrict_tc<2><<<grid, 128, restrict_smem(a.R), s>>>(fine, f.RB.as<uint8_t>(), coarse, bound, a,
-                                                               f.IgErr.as<int>());
-    else
-        k_restrict_tc<1><<<grid, 128, restrict_smem(a.R), s>>>(fine, f.RB.as<uint8_t>(), coarse, bound, a,
-                                                               f.IgErr.as<int>());
+    if (paired(fine, n)) {
+        if (split) k_restrict_tc<2, true><<<grid, 128, smem, s>>>(fine, rb, rbl, coarse, bound, a, f.IgErr.as<int>());
+        else k_restrict_tc<2, false><<<grid, 128, smem, s>>>(fine, rb, rbl, coarse, bound, a, f.IgErr.as<int>());
+    } else {
+        if (split) k_restrict_tc<1, true><<<grid, 128, smem, s>>>(fine, rb, rbl, coarse, bound, a, f.IgErr.as<int>());
+        else k_restrict_tc<1, false><<<grid, 128, smem, s>>>(fine, rb, rbl, coarse, bound, a, f.IgErr.as<int>());
+    }
     MRHS_LAUNCHED("k_restrict_tc");
 }
 

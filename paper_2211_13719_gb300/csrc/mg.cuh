@@ -32,6 +32,7 @@ struct Level {
     // tensor-core transfer to the next level (16-bit hierarchies): packed P tiles
     DeviceBuffer PA;         // prolongation A tiles [Vc][2][tiles] 128 x 64 FP16
     DeviceBuffer RB;         // restriction B tiles [Vc][2][chunks] 64 x 64 FP16
+    DeviceBuffer RBlo;       // their FP16 rounding errors (split-precision restriction of the Galerkin build)
     DeviceBuffer IgErr;      // int: set when a tensor-core transfer gave up waiting
     DeviceBuffer IgBound;    // float [2][64]: ones (unit-norm inputs), then the column maxima of the last input
     bool tc_intergrid = false;
@@ -86,10 +87,14 @@ void coarse_parity_merge_add(const Level &c, const float2 *he, const float2 *ho,
                              cudaStream_t s);
 // tensor-core restriction / prolongation (FP16, <= 32 null vectors, <= 64 RHS)
 bool intergrid_tc_supported(const Level &f);
-void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s);
-// unit_norm: every RHS column of `fine` has norm <= 1 (its components are then bounded by 1)
+// packs the prolongation and restriction tiles once (a second call adds only what is missing);
+// split: also the FP16 rounding errors of the restriction tiles
+void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s, bool split = false);
+// unit_norm: every RHS column of `fine` has norm <= 1 (its components are then bounded by 1).
+// split: every operand as the sum of two FP16 numbers, three MMA terms (FP32-level accuracy,
+// for the Galerkin construction); needs intergrid_tc_prepare(..., split = true)
 void restrict_fields_tc(const Level &f, const Level &c, const float2 *fine, float2 *coarse, int n, int64_t ostride,
-                        bool unit_norm, cudaStream_t s);
+                        bool unit_norm, cudaStream_t s, bool split = false);
 void prolong_fields_tc(const Level &f, const Level &c, const float2 *coarse, float2 *fine, int n, cudaStream_t s);
 int intergrid_tc_error(const Level &f, cudaStream_t s);
 // FP64 modified Gram-Schmidt (twice) of the chiral halves of `vecs` per aggregate, in place

@@ -688,6 +688,7 @@ void validate_params(const mrhs_lattice *lat, const mrhs_mg_params &p) {
         fail(MRHS_ERR_INVALID, "coarse_smoother_evenodd must be 0 or 1");
     if (p.coarse_solver != 0 && p.coarse_solver != 1) fail(MRHS_ERR_INVALID, "coarse_solver must be 0 or 1");
     if (p.coarse_fused != 0 && p.coarse_fused != 1) fail(MRHS_ERR_INVALID, "coarse_fused must be 0 or 1");
+    if (p.galerkin_tc < 0 || p.galerkin_tc > 2) fail(MRHS_ERR_INVALID, "galerkin_tc must be 0, 1 or 2");
     if (p.coarse_solver == 1 && (p.coarse_m > 16 || p.coarse_recycle < 0 || p.coarse_recycle >= p.coarse_m))
         fail(MRHS_ERR_INVALID, "GCRO-DR needs coarse_m <= 16 and 0 <= coarse_recycle < coarse_m");
     if (!(p.inner_tol > 0 && p.inner_tol < 1)) fail(MRHS_ERR_INVALID, "inner_tol must be in (0, 1)");
@@ -750,9 +751,14 @@ void setup_level(mrhs_mg &mg, int l, cudaStream_t s, PhaseEvents &ph) {
     F.P32.alloc(sizeof(float2) * count);
     cast(MRHS_FP32, F.P32.ptr, MRHS_FP64, F.P64.ptr, count, s);
     v32.release();
-    // Galerkin coarse operator R A P, stencil block by stencil block
+    // Galerkin coarse operator R A P, stencil block by stencil block; the restriction R = P^dagger
+    // on the tensor cores in split FP16 (FP32-level accuracy) where the transfer tiles apply
     ph.mark(s);
     const int nc = 2 * N;
+    const bool bit16 = mg.p.coarse_precision == MRHS_FP16 || mg.p.coarse_precision == MRHS_BF16;
+    const bool tc_galerkin = (mg.p.galerkin_tc == 2 || (mg.p.galerkin_tc == 1 && bit16)) &&
+                             intergrid_tc_supported(F) && nc <= 64;
+    if (tc_galerkin) intergrid_tc_prepare(F, Cl, s, true);
     Cl.A32.alloc(sizeof(float2) * (size_t)Cl.V * 9 * nc * nc);
     DeviceBuffer Pe(sizeof(float2) * (size_t)F.V * F.dof * nc);
     DeviceBuffer H(sizeof(float2) * (size_t)F.V * F.dof * nc);
@@ -766,9 +772,15 @@ void setup_level(mrhs_mg &mg, int l, cudaStream_t s, PhaseEvents &ph) {
             StencilMask m{d == 0 ? 1 : 0, d == 0 ? -1 : d, d == 0 ? 2 : 1, {F.B[0], F.B[1], F.B[2], F.B[3]}};
             coarse_apply_fp32(F, Pe.as<float2>(), H.as<float2>(), nullptr, nc, s, &m);
         }
-        restrict_fields(F, Cl, H.as<float2>(), Cl.A32.as<float2>() + (size_t)d * nc * nc, nc, ostride, s);
+        if (tc_galerkin)
+            restrict_fields_tc(F, Cl, H.as<float2>(), Cl.A32.as<float2>() + (size_t)d * nc * nc, nc, ostride, false, s,
+                               true);
+        else
+            restrict_fields(F, Cl, H.as<float2>(), Cl.A32.as<float2>() + (size_t)d * nc * nc, nc, ostride, s);
     }
     ph.mark(s);
+    if (tc_galerkin && intergrid_tc_error(F, s))
+        fail(MRHS_ERR_TIMEOUT, "setup: a tensor-core restriction of the Galerkin build gave up waiting");
     MRHS_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1066,6 +1078,7 @@ void mrhs_mg_default_params(mrhs_mg_params *p) {
     p->coarse_solver = 0;
     p->coarse_recycle = 4;
     p->coarse_fused = 1;
+    p->galerkin_tc = 1;
 }
 
 mrhs_status mrhs_setup_mg(mrhs_lattice *lat, const mrhs_mg_params *params, mrhs_mg **out) {

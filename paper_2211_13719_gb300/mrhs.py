@@ -75,6 +75,7 @@ class MgParams(C.Structure):
         ("coarse_solver", C.c_int),
         ("coarse_recycle", C.c_int),
         ("coarse_fused", C.c_int),
+        ("galerkin_tc", C.c_int),
     ]
 
 

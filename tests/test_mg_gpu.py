@@ -3,7 +3,11 @@
 Start vectors come from the seeded generator and are given to both sides, with
 no setup relaxation, so both build the prolongator from the same vectors:
 * prolongator (FP64 block Gram-Schmidt) to 1e-12,
-* Galerkin links (FP32 on the GPU) to 2e-6 relative per stencil block,
+* Galerkin links (FP32 on the GPU) to 2e-6 relative per stencil block with
+  the restriction of the build on the CUDA cores in FP32, and to 2e-5 with it
+  on the tensor cores in split FP16 (hi + lo operands, 22 significant bits,
+  three MMA terms; the remaining error, about 1e-5, is the tensor cores' FP32
+  accumulation over the aggregate's rows; the kernel timer shows which ran),
 * restriction / prolongation (FP32) to 2e-6 relative per site,
 * coarse stencil (FP32 links, FP32 fields) to 1e-6 relative per site
   against the oracle's FP64 stencil on the same (GPU-built FP32) links, so
@@ -38,15 +42,19 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("galerkin_tc", [2, 0])
 @pytest.mark.parametrize("dims,blocks,nvec", CASES)
-def test_two_level_rows(dims, blocks, nvec):
+def test_two_level_rows(dims, blocks, nvec, galerkin_tc):
     mass, csw, n = -0.2, 1.0, 5
     U = synth.gauge_exp(dims, 0.4, 1001)
     V = wilson.volume(dims)
     v0 = synth.gaussian_field(V, 12, nvec[0], 3001)
     lat = make_lattice(U, dims, mass, csw)
+    mrhs.mrhs_kernel_timer_start("k_restrict_tc")
     mg = make_mg(lat, dict(n_levels=2, blocks=blocks, nvec=nvec, setup_sweeps=0, max_rhs=8,
-                           coarse_precision=mrhs.MRHS_FP32), [v0])
+                           coarse_precision=mrhs.MRHS_FP32, galerkin_tc=galerkin_tc), [v0])
+    _, tc_launches, _ = mrhs.mrhs_kernel_timer_stop()
+    assert tc_launches == (9 if galerkin_tc else 0)
     try:
         # prolongator
         Pg = np.zeros((V, 12, nvec[0]), np.complex128)
@@ -62,7 +70,9 @@ def test_two_level_rows(dims, blocks, nvec):
         Ao = coarse.galerkin_fine(U, C, Po, dims, blocks[0], mass)
         Ag = np.zeros((Vc, 9, nc, nc), np.complex128)
         mrhs.mrhs_mg_get_coarse_links(mg, 1, Ag)
-        assert _block_rel_err(Ag.reshape(-1, nc, nc), Ao.reshape(-1, nc, nc)) < 2e-6
+        gal_err = _block_rel_err(Ag.reshape(-1, nc, nc), Ao.reshape(-1, nc, nc))
+        print(f"galerkin_tc={galerkin_tc} dims={dims} nvec={nvec}: Galerkin block error {gal_err:.2e}")
+        assert gal_err < (2e-5 if galerkin_tc else 2e-6)
         # restriction and prolongation
         psi = synth.gaussian_field(V, 12, n, 4001, np.complex64)
         d_psi = to_dev(psi)
