@@ -41,7 +41,9 @@ WORKLOAD = dict(dims=(24, 24, 24, 64), eps=0.25, gauge_seed=1301, source_seed=23
 MG_PARAMS = dict(setup_sweeps=6, setup_m=8, smooth_m=3, coarse_m=14, coarse_cycles=1, inter_m=4, inner_m=8,
                  inner_max_iters=200, inner_tol=1e-5, outer_m=4, max_outer_iters=30, smoother_evenodd=1)
 # the kernel with the largest share of a timed solve in the profiler's launch list (the even-odd
-# hopping kernel of the fine smoother's Schur operator), and the full-lattice fine stencil
+# hopping kernel of the fine smoother's Schur operator), and the full-lattice fine stencil; the
+# names are the kernel timer's, which cover the paired (k_eo_x2, k_dslash_x2) and the
+# one-RHS-per-thread (k_eo_r1, k_dslash_r1) forms
 DOMINANT_KERNEL = "k_eo_x2"
 FINE_STENCIL_KERNEL = "k_dslash_x2"
 WORKLOAD_NAME = ("wilson-clover MG solve 24^3x64 antiperiodic, U=exp(i0.25H), c_sw=1, 3 levels "
@@ -650,7 +652,8 @@ def run_ours(args, rank, world, local_rank):
         extra["roofline_fine_stencil"] = {
             "bound": "hbm", "achieved": alg / t_k / 1e9, "peak": peak, "unit": "GB/s",
             "frac": alg / t_k / 1e9 / peak, "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-            "kernel": f"{FINE_STENCIL_KERNEL} (fp32 full-lattice fine stencil D), "
+            "kernel": f"{FINE_STENCIL_KERNEL} (fp32 full-lattice fine stencil D; default variant: the "
+                      f"one-RHS-per-thread form k_dslash_r1), "
                       f"{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}, nRHS={n}",
             "algorithmic_bytes_per_launch": alg, "bytes_per_site": f"576 + 192 n = {576 + 192 * n}",
             "ms_per_launch": t_k * 1e3,
@@ -676,7 +679,8 @@ def run_ours(args, rank, world, local_rank):
             "bound": "hbm", "achieved": alg_eo / t_eo / 1e9, "peak": peak, "unit": "GB/s",
             "frac": alg_eo / t_eo / 1e9 / peak, "traffic": (tre["dram_bytes_per_launch"] if tre else None),
             "kernel": f"{DOMINANT_KERNEL} (fp32 even-odd hopping kernel, both launches of the Schur operator "
-                      f"D_hat), {dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}, nRHS={n}",
+                      f"D_hat; default variant: the one-RHS-per-thread form k_eo_r1), "
+                      f"{dims[0]}x{dims[1]}x{dims[2]}x{dims[3]}, nRHS={n}",
             "algorithmic_bytes_per_launch": alg_eo,
             "bytes_per_output_site": f"per D_hat (2 launches) 1728 + 480 n = {1728 + 480 * n}",
             "ms_per_launch": t_eo * 1e3, "ms_per_dhat": t_dhat * 1e3,

@@ -548,12 +548,16 @@ __device__ __forceinline__ void hop_pair_r1(cplx<float> (&acc)[12], const float2
 }
 
 // out(x) = (D in)(x) (RESID: y(x) - (D in)(x)) for RHS r of the site at coordinates c:
-// the hop, the clover term and the axpy of one thread (one RHS)
-template <bool RESID, int N>
+// the hop, the clover term and the axpy of one thread (one RHS).  SPLIT (even-odd
+// smoother): the result goes to half fields instead, out (even sites) or ro (odd sites)
+// at index site / 2, and at the even sites also te = Cinv out.
+template <bool RESID, int N, bool SPLIT = false>
 __device__ __forceinline__ void dslash_r1_site(const float2 *__restrict__ U, const float2 *__restrict__ C,
                                                const float2 *__restrict__ in, float2 *__restrict__ out,
                                                const float2 *__restrict__ y, const KArgs32 &a, const int c[4],
-                                               int r) {
+                                               int r, float2 *__restrict__ ro = nullptr,
+                                               float2 *__restrict__ te = nullptr,
+                                               const float2 *__restrict__ Cinv = nullptr) {
     const int n = N ? N : a.n;
     const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
     cplx<float> acc[12];
@@ -564,9 +568,11 @@ __device__ __forceinline__ void dslash_r1_site(const float2 *__restrict__ U, con
     hop_pair_r1<2, N>(acc, U, in, a, site, c, r);
     hop_pair_r1<3, N>(acc, U, in, a, site, c, r);
     const int64_t base = (int64_t)site * 12 * n + r;
+    const int64_t hbase = (int64_t)(site >> 1) * 12 * n + r;  // SPLIT: the half-field index
+    const bool odd = ((c[0] + c[1] + c[2] + c[3]) & 1) != 0;
 #pragma unroll
     for (int chi = 0; chi < 2; ++chi) {
-        cplx<float> v[6], o[6];
+        cplx<float> v[6], o[6], res6[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) v[i] = ld_c1(in, base + (6 * chi + i) * n);
         site_mat_r1(C, site, chi, v, o);
@@ -579,7 +585,21 @@ __device__ __forceinline__ void dslash_r1_site(const float2 *__restrict__ U, con
                 const cplx<float> yy = ld_c1(y, off);
                 res = {__fadd_rn(yy.re, -res.re), __fadd_rn(yy.im, -res.im)};
             }
-            __stcs(out + off, make_float2(res.re, res.im));
+            if constexpr (SPLIT) {
+                res6[i] = res;
+                __stcs((odd ? ro : out) + hbase + (6 * chi + i) * n, make_float2(res.re, res.im));
+            } else {
+                __stcs(out + off, make_float2(res.re, res.im));
+            }
+        }
+        if constexpr (SPLIT) {
+            if (!odd) {
+                cplx<float> t[6];
+                site_mat_r1(Cinv, site, chi, res6, t);
+#pragma unroll
+                for (int i = 0; i < 6; ++i)
+                    __stcs(te + hbase + (6 * chi + i) * n, make_float2(t[i].re, t[i].im));
+            }
         }
     }
 }
@@ -592,6 +612,20 @@ __global__ void __launch_bounds__(128, 6) k_dslash_r1(const float2 *__restrict__
     int c[4], r;
     if (!visit_coords(a, item, a.V, false, c, r, 1)) return;
     dslash_r1_site<RESID, N>(U, C, in, out, y, a, c, r);
+}
+
+// the even-odd smoother's residual r = y - D x written as r_e, r_o and te = C_ee^-1 r_e
+template <int N>
+__global__ void __launch_bounds__(128, 6) k_dslash_r1_split(const float2 *__restrict__ U, const float2 *__restrict__ C,
+                                                             const float2 *__restrict__ Cinv,
+                                                             const float2 *__restrict__ in,
+                                                             const float2 *__restrict__ y, float2 *__restrict__ re,
+                                                             float2 *__restrict__ ro, float2 *__restrict__ te,
+                                                             KArgs32 a) {
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    int c[4], r;
+    if (!visit_coords(a, item, a.V, false, c, r, 1)) return;
+    dslash_r1_site<true, N, true>(U, C, in, re, y, a, c, r, ro, te, Cinv);
 }
 
 // ------------------------------------- fused batch of uneven problems
@@ -840,7 +874,10 @@ void dslash_batch(const BatchItemHost *items, int count, cudaStream_t s) {
 // sites followed by EO_SCHUR onto the odd ones, and the even-odd solution of
 // D x = b takes b_hat = b_o + 1/2 H_oe C_ee^-1 b_e (EO_AXPY_HOP onto the odd
 // sites) and x_e = C_ee^-1 (b_e + 1/2 H_eo x_o) (EO_CINV_AXPY_HOP).
-enum { EO_HOP = 0, EO_CINV_HOP = 1, EO_SCHUR = 2, EO_AXPY_HOP = 3, EO_CINV_AXPY_HOP = 4 };
+//   EO_CINV_AXPY_HOP_MERGE: the even-odd smoother's last step in one pass,
+//        z_e += C^-1 (self + 1/2 H in) at the output sites and z_o += in at
+//        their x-pair partners, with z the full-lattice field `out`
+enum { EO_HOP = 0, EO_CINV_HOP = 1, EO_SCHUR = 2, EO_AXPY_HOP = 3, EO_CINV_AXPY_HOP = 4, EO_CINV_AXPY_HOP_MERGE = 5 };
 
 struct KArgsEO {
     KArgs32 k;   // full-lattice geometry (k.V is the full volume), n, RHS pairs
@@ -893,8 +930,9 @@ __global__ void __launch_bounds__(128, 3) k_eo_x2(const float2 *__restrict__ U, 
     if constexpr (MODE == EO_HOP) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) st_p2(out, base + i * n, acc[i]);
-    } else if constexpr (MODE == EO_AXPY_HOP || MODE == EO_CINV_AXPY_HOP) {
+    } else if constexpr (MODE == EO_AXPY_HOP || MODE == EO_CINV_AXPY_HOP || MODE == EO_CINV_AXPY_HOP_MERGE) {
         const float2 half = make_float2(0.5f, 0.5f);
+        const int64_t zbase = (int64_t)site * 12 * n + r0;  // MERGE: z at the output site
 #pragma unroll
         for (int chi = 0; chi < 2; ++chi) {
             P2 v[6], o[6];
@@ -904,10 +942,20 @@ __global__ void __launch_bounds__(128, 3) k_eo_x2(const float2 *__restrict__ U, 
                 const P2 ai = acc[6 * chi + i];
                 v[i] = {__ffma2_rn(half, ai.re, y.re), __ffma2_rn(half, ai.im, y.im)};
             }
-            if constexpr (MODE == EO_CINV_AXPY_HOP) site_mat_x2<AOS>(M, a.V, site, chi, v, o);
+            if constexpr (MODE != EO_AXPY_HOP) site_mat_x2<AOS>(M, a.V, site, chi, v, o);
 #pragma unroll
-            for (int i = 0; i < 6; ++i)
-                st_p2(out, base + (6 * chi + i) * n, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
+            for (int i = 0; i < 6; ++i) {
+                if constexpr (MODE == EO_CINV_AXPY_HOP_MERGE)
+                    st_p2(out, zbase + (6 * chi + i) * n, p2add(ld_p2(out, zbase + (6 * chi + i) * n), o[i]));
+                else
+                    st_p2(out, base + (6 * chi + i) * n, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
+            }
+        }
+        if constexpr (MODE == EO_CINV_AXPY_HOP_MERGE) {
+            // the x-pair partner (the other parity, same half-field index): z_o += in
+            const int64_t pbase = (int64_t)(site ^ 1) * 12 * n + r0;
+#pragma unroll
+            for (int i = 0; i < 12; ++i) st_p2(out, pbase + i * n, p2add(ld_p2(out, pbase + i * n), ld_p2(in, base + i * n)));
         }
     } else {
         const float2 quarter = make_float2(-0.25f, -0.25f);
@@ -974,7 +1022,8 @@ __global__ void __launch_bounds__(128, 6) k_eo_r1(const float2 *__restrict__ U, 
     if constexpr (MODE == EO_HOP) {
 #pragma unroll
         for (int i = 0; i < 12; ++i) st1(i, acc[i]);
-    } else if constexpr (MODE == EO_AXPY_HOP || MODE == EO_CINV_AXPY_HOP) {
+    } else if constexpr (MODE == EO_AXPY_HOP || MODE == EO_CINV_AXPY_HOP || MODE == EO_CINV_AXPY_HOP_MERGE) {
+        const int64_t zbase = (int64_t)site * 12 * N + r;  // MERGE: z at the output site
 #pragma unroll
         for (int chi = 0; chi < 2; ++chi) {
             cplx<float> v[6], o[6];
@@ -984,9 +1033,26 @@ __global__ void __launch_bounds__(128, 6) k_eo_r1(const float2 *__restrict__ U, 
                 const cplx<float> ai = acc[6 * chi + i];
                 v[i] = {__fmaf_rn(0.5f, ai.re, yv.re), __fmaf_rn(0.5f, ai.im, yv.im)};
             }
-            if constexpr (MODE == EO_CINV_AXPY_HOP) site_mat_r1(M, site, chi, v, o);
+            if constexpr (MODE != EO_AXPY_HOP) site_mat_r1(M, site, chi, v, o);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) st1(6 * chi + i, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
+            for (int i = 0; i < 6; ++i) {
+                if constexpr (MODE == EO_CINV_AXPY_HOP_MERGE) {
+                    const int64_t zi = zbase + (6 * chi + i) * N;
+                    const float2 zv = out[zi];
+                    out[zi] = make_float2(__fadd_rn(zv.x, o[i].re), __fadd_rn(zv.y, o[i].im));
+                } else {
+                    st1(6 * chi + i, MODE == EO_CINV_AXPY_HOP ? o[i] : v[i]);
+                }
+            }
+        }
+        if constexpr (MODE == EO_CINV_AXPY_HOP_MERGE) {
+            // the x-pair partner (the other parity, same half-field index): z_o += in
+            const int64_t pbase = (int64_t)(site ^ 1) * 12 * N + r;
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const float2 zv = out[pbase + i * N], d = __ldg(in + base + i * N);
+                out[pbase + i * N] = make_float2(__fadd_rn(zv.x, d.x), __fadd_rn(zv.y, d.y));
+            }
         }
     } else {
 #pragma unroll
@@ -1051,9 +1117,11 @@ static void check_eo(const mrhs_lattice &lat, int n) {
 
 enum { EO_NOMAT = 0, EO_MAT_C = 1, EO_MAT_CINV = 2 };
 
+// tune_scratch (EO_CINV_AXPY_HOP_MERGE only): a half field the tuner may write; the merge
+// accumulates into z, so it takes the variant tuned for EO_CINV_AXPY_HOP, timed into the scratch
 template <int MODE>
 static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const float2 *self, float2 *out, int n,
-                      int parity, cudaStream_t s) {
+                      int parity, cudaStream_t s, float2 *tune_scratch = nullptr) {
     // tile variants for the autotuner (variant 0: one x pair x 4 x 8 x 8)
     const int prefs[][4] = {{2, 4, 8, 8}, {2, 4, 4, 8}, {2, 2, 8, 8}, {2, 8, 8, 8}, {2, 4, 8, 4}};
     std::vector<KArgsEO> args;
@@ -1091,7 +1159,8 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
     const unsigned blocks_r1 = (unsigned)(((int64_t)args[0].V2 * n + 127) / 128);
     // as the full-lattice stencil: compile-time RHS count and site-major links /
     // site matrices for 16, 24, 32, 48, 64 RHS
-    auto launch = [&](int v) {
+    auto launch_m = [&](auto modec, int v, float2 *dst) {
+        constexpr int MD = decltype(modec)::value;
         const KArgsEO &e = args[(size_t)v];
         const bool one = v < nx2;
         auto go = [&](auto nc, auto aos) {
@@ -1103,11 +1172,11 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
                                                    : nullptr;
             if constexpr (NC > 0 && AO) {
                 if (one) {
-                    k_eo_r1<MODE, NC><<<blocks_r1, 128, 0, s>>>(U, M, in, self, out, e);
+                    k_eo_r1<MD, NC><<<blocks_r1, 128, 0, s>>>(U, M, in, self, dst, e);
                     return;
                 }
             }
-            k_eo_x2<MODE, NC, AO><<<blocks, 128, 0, s>>>(U, M, in, self, out, e);
+            k_eo_x2<MD, NC, AO><<<blocks, 128, 0, s>>>(U, M, in, self, dst, e);
         };
         switch (n) {
             case 16: go(std::integral_constant<int, 16>{}, std::true_type{}); break;
@@ -1119,11 +1188,20 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
         }
         MRHS_CUDA(cudaGetLastError());
     };
+    auto launch = [&](int v) { launch_m(std::integral_constant<int, MODE>{}, v, out); };
     static const char *names[] = {"k_eo_x2_hop", "k_eo_x2_cinv_hop", "k_eo_x2_schur", "k_eo_x2_axpy_hop",
                                   "k_eo_x2_cinv_axpy_hop"};
-    // an output that aliases an input would not survive repeated launches: no tuning then
-    const bool alias = out == in || (self && out == self);
-    const int v = alias ? 0 : tune_pick(names[MODE], lat.g.L, n, (int)args.size(), launch, s);
+    int v = 0;
+    if constexpr (MODE == EO_CINV_AXPY_HOP_MERGE) {
+        auto tune_launch = [&](int vv) {
+            launch_m(std::integral_constant<int, EO_CINV_AXPY_HOP>{}, vv, tune_scratch);
+        };
+        if (tune_scratch) v = tune_pick(names[EO_CINV_AXPY_HOP], lat.g.L, n, (int)args.size(), tune_launch, s);
+    } else {
+        // an output that aliases an input would not survive repeated launches: no tuning then
+        const bool alias = out == in || (self && out == self);
+        v = alias ? 0 : tune_pick(names[MODE], lat.g.L, n, (int)args.size(), launch, s);
+    }
     MRHS_TIMED("k_eo_x2", s);
     launch(v);
     MRHS_LAUNCHED("k_eo_x2");
@@ -1189,31 +1267,48 @@ __global__ void __launch_bounds__(128) k_eo_split(const float2 *__restrict__ r, 
     }
 }
 
-// z += (d_e on the even sites, d_o on the odd sites)
-__global__ void __launch_bounds__(128) k_eo_merge_add(const float2 *__restrict__ de, const float2 *__restrict__ dod,
-                                                       float2 *__restrict__ z, KArgsEO e) {
-    const KArgs32 &a = e.k;
-    const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    const int cb = item / a.G;
-    if (cb >= e.V2) return;
-    const int r0 = (item - cb * a.G) * 2;
-    int se, so;
-    eo_pair_sites(a, cb, se, so);
-    const int64_t hb = (int64_t)cb * 12 * a.n + r0;
-    const int64_t fe = (int64_t)se * 12 * a.n + r0, fo = (int64_t)so * 12 * a.n + r0;
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        const P2 ze = ld_p2(z, fe + (int64_t)i * a.n), zo = ld_p2(z, fo + (int64_t)i * a.n);
-        const P2 ae = ld_p2(de, hb + (int64_t)i * a.n), ao = ld_p2(dod, hb + (int64_t)i * a.n);
-        st_p2(z, fe + (int64_t)i * a.n, p2add(ze, ae));
-        st_p2(z, fo + (int64_t)i * a.n, p2add(zo, ao));
-    }
-}
-
 bool eo_supported(const mrhs_lattice &lat, int n) {
     for (int mu = 0; mu < 4; ++mu)
         if (lat.g.L[mu] % 2) return false;
     return n >= 2 && n % 2 == 0 && !lat.cinv_singular && lat.g.V * 6LL * n < (1LL << 31);
+}
+
+bool residual_eo_split(const mrhs_lattice &lat, const void *x, const void *y, void *re, void *ro, void *te, int n,
+                       cudaStream_t s) {
+    if (!(n == 16 || n == 24 || n == 32 || n == 48 || n == 64) || !eo_supported(lat, n)) return false;
+    if (lat.g.V * 12LL * n >= (1LL << 31)) return false;
+    // the one-RHS-per-thread stencil's tile shapes (its first two variants); every variant
+    // computes the same values, the autotuner picks between them per (lattice, n)
+    const int prefs[][4] = {{1, 4, 8, 8}, {1, 4, 4, 8}};
+    std::vector<KArgs32> args;
+    for (const auto &pref : prefs) {
+        KArgs32 a = x2_args(lat, n, pref);
+        a.G = n;
+        a.GS = n;
+        bool dup = false;
+        for (const KArgs32 &b : args) dup = dup || (b.T[1] == a.T[1] && b.T[2] == a.T[2] && b.T[3] == a.T[3]);
+        if (!dup) args.push_back(a);
+    }
+    const unsigned blocks = (unsigned)(((int64_t)lat.g.V * n + 127) / 128);
+    const float2 *U = lat.U32a.as<float2>(), *C = lat.C32a.as<float2>(), *Ci = lat.Cinv32a.as<float2>();
+    const float2 *xi = static_cast<const float2 *>(x), *yi = static_cast<const float2 *>(y);
+    float2 *e = static_cast<float2 *>(re), *o = static_cast<float2 *>(ro), *t = static_cast<float2 *>(te);
+    auto launch = [&](int v) {
+        const KArgs32 &a = args[(size_t)v];
+        switch (n) {
+            case 16: k_dslash_r1_split<16><<<blocks, 128, 0, s>>>(U, C, Ci, xi, yi, e, o, t, a); break;
+            case 24: k_dslash_r1_split<24><<<blocks, 128, 0, s>>>(U, C, Ci, xi, yi, e, o, t, a); break;
+            case 32: k_dslash_r1_split<32><<<blocks, 128, 0, s>>>(U, C, Ci, xi, yi, e, o, t, a); break;
+            case 48: k_dslash_r1_split<48><<<blocks, 128, 0, s>>>(U, C, Ci, xi, yi, e, o, t, a); break;
+            default: k_dslash_r1_split<64><<<blocks, 128, 0, s>>>(U, C, Ci, xi, yi, e, o, t, a); break;
+        }
+        MRHS_CUDA(cudaGetLastError());
+    };
+    const int v = tune_pick("k_dslash_r1_split", lat.g.L, n, (int)args.size(), launch, s);
+    MRHS_TIMED("k_dslash_r1_split", s);
+    launch(v);
+    MRHS_LAUNCHED("k_dslash_r1_split");
+    return true;
 }
 
 void eo_split(const mrhs_lattice &lat, const void *r, void *re, void *ro, void *te, int n, cudaStream_t s) {
@@ -1237,13 +1332,12 @@ void eo_axpy_hop(const mrhs_lattice &lat, int out_parity, const void *self, cons
                                static_cast<float2 *>(out), n, out_parity, s);
 }
 
-void eo_merge_add(const mrhs_lattice &lat, const void *de, const void *d_o, void *z, int n, cudaStream_t s) {
+void eo_cinv_axpy_hop_merge(const mrhs_lattice &lat, const void *r_e, const void *d_o, void *z, void *scratch_half,
+                            int n, cudaStream_t s) {
     check_eo(lat, n);
-    const KArgsEO e = eo_args(lat, n, 0);
-    const int64_t items = (int64_t)e.V2 * e.k.G;
-    k_eo_merge_add<<<(unsigned)((items + 127) / 128), 128, 0, s>>>(
-        static_cast<const float2 *>(de), static_cast<const float2 *>(d_o), static_cast<float2 *>(z), e);
-    MRHS_LAUNCHED("k_eo_merge_add");
+    launch_eo<EO_CINV_AXPY_HOP_MERGE>(lat, EO_MAT_CINV, static_cast<const float2 *>(d_o),
+                                      static_cast<const float2 *>(r_e), static_cast<float2 *>(z), n, 0, s,
+                                      static_cast<float2 *>(scratch_half));
 }
 
 int clover_inverse_error(const mrhs_lattice &lat) {

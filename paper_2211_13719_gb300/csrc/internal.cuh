@@ -61,13 +61,19 @@ void schur_apply(const mrhs_lattice &lat, const void *in_odd, void *out_odd, int
 int clover_inverse_error(const mrhs_lattice &lat);
 // even-odd solution pieces (FP32, even n): eo_supported tells whether the lattice
 // and n allow them; eo_split: r (full) -> r_e, r_o, t_e = C_ee^-1 r_e (halves);
-// eo_axpy_hop: out = self + 1/2 H in onto out_parity (cinv: C^-1 of that);
-// eo_merge_add: z (full) += (d_e, d_o)
+// eo_axpy_hop: out = self + 1/2 H in onto out_parity (cinv: C^-1 of that)
 bool eo_supported(const mrhs_lattice &lat, int n);
 void eo_split(const mrhs_lattice &lat, const void *r, void *re, void *ro, void *te, int n, cudaStream_t s);
+// r = y - D x (FP32) straight into the halves r_e, r_o and te = C_ee^-1 r_e: the residual and
+// eo_split in one pass, for 16, 24, 32, 48 or 64 RHS (false: not applicable, nothing launched)
+bool residual_eo_split(const mrhs_lattice &lat, const void *x, const void *y, void *re, void *ro, void *te, int n,
+                       cudaStream_t s);
 void eo_axpy_hop(const mrhs_lattice &lat, int out_parity, const void *self, const void *in, void *out, bool cinv,
                  int n, cudaStream_t s);
-void eo_merge_add(const mrhs_lattice &lat, const void *de, const void *d_o, void *z, int n, cudaStream_t s);
+// the smoother's last step in one pass: z_e += C_ee^-1 (r_e + 1/2 H_eo d_o), z_o += d_o;
+// scratch_half: an even half field the autotuner may overwrite
+void eo_cinv_axpy_hop_merge(const mrhs_lattice &lat, const void *r_e, const void *d_o, void *z, void *scratch_half,
+                            int n, cudaStream_t s);
 // SAP smoother (FP32, even n): `cycles` cycles of the block-coloured Schwarz
 // alternating procedure for D z = v, each block system by `mr_steps` MR steps
 // in shared memory; r_tmp: a full FP32 field of n RHS, overwritten.

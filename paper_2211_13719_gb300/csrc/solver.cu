@@ -551,15 +551,16 @@ void vcycle(mrhs_mg &mg, int l, const float2 *v, float2 *z, int n, cudaStream_t 
         } else if (l == 0 && mg.schur && eo_supported(*mg.lat, n)) {
             // even-odd smoother: z += delta, D delta ~= r = v - D z through smooth_m GMRES
             // steps on D_hat delta_o = b_hat = r_o + 1/2 H_oe C_ee^-1 r_e from 0, then
-            // delta_e = C_ee^-1 (r_e + 1/2 H_eo delta_o)
+            // delta_e = C_ee^-1 (r_e + 1/2 H_eo delta_o), both added to z in one pass
             LevelWork &W = mg.work[0];
-            mg.ops[0]->residual(z, v, W.eo_r.as<float2>(), n, s);
-            eo_split(*mg.lat, W.eo_r.ptr, W.eo_re.ptr, W.eo_ro.ptr, W.eo_te.ptr, n, s);
+            if (!residual_eo_split(*mg.lat, z, v, W.eo_re.ptr, W.eo_ro.ptr, W.eo_te.ptr, n, s)) {
+                mg.ops[0]->residual(z, v, W.eo_r.as<float2>(), n, s);
+                eo_split(*mg.lat, W.eo_r.ptr, W.eo_re.ptr, W.eo_ro.ptr, W.eo_te.ptr, n, s);
+            }
             eo_axpy_hop(*mg.lat, 1, W.eo_ro.ptr, W.eo_te.ptr, W.eo_bh.ptr, false, n, s);
             krylov_cycle(*mg.schur, nullptr, W.eo_bh.as<float2>(), W.eo_do.as<float2>(), n, mg.p.smooth_m,
                          W.eo_smooth, s, true, nullptr);
-            eo_axpy_hop(*mg.lat, 0, W.eo_re.ptr, W.eo_do.ptr, W.eo_de.ptr, true, n, s);
-            eo_merge_add(*mg.lat, W.eo_de.ptr, W.eo_do.ptr, z, n, s);
+            eo_cinv_axpy_hop_merge(*mg.lat, W.eo_re.ptr, W.eo_do.ptr, z, W.eo_de.ptr, n, s);
         } else if (l > 0 && mg.work[l].ceo_op) {
             // coarse even-odd smoother: z += delta, delta from smooth_m GMRES steps on
             // D_hat delta_o = b_hat = r_o - H_oe A_ee^-1 r_e (r = v - A z), then
