@@ -753,6 +753,8 @@ def run_case(name, reps, args=None):
     schur:     even-odd hop and Schur operator (FP32), 24^4 lattice, 48 RHS
     intergrid: tensor-core restriction + prolongation, 16^4 lattice, 4^4 aggregates, 32 vectors, 48 RHS
     blas:      the FP32 batched multi-dot and linear combination, 16^4 x 12 rows (--blas-rows), 48 RHS, 4 vectors
+    coarsest:  the coarsest GMRES(14) solve at 3^3x8 sites, nc = 64, 48 RHS (small 2-level hierarchy), the
+               persistent kernel and the launch-per-operation path
     Prints one JSON line with the CUDA-event time per launch."""
     import numpy as np
     import torch
@@ -793,6 +795,8 @@ def run_case(name, reps, args=None):
         return print(json.dumps(out), flush=True)
     if name == "coarse":
         return print(json.dumps(run_coarse_case(mrhs, torch, reps)), flush=True)
+    if name == "coarsest":
+        return print(json.dumps(run_coarsest_case(mrhs, torch, reps, ev)), flush=True)
     dims = (24, 24, 24, 24) if name in ("stencil", "schur", "stencil-sweep") else (16, 16, 16, 16)
     V = volume(dims)
     U = synth.gauge_exp(dims, WORKLOAD["eps"], WORKLOAD["gauge_seed"])
@@ -1007,6 +1011,42 @@ def run_serving_case(args):
     print(json.dumps(out), flush=True)
 
 
+def run_coarsest_case(mrhs, torch, reps, ev):
+    """The coarsest solve at the benchmark's coarsest size (3^3x8 sites, nc = 64, 48 RHS, GMRES(14)) on a
+    small 2-level hierarchy (fine 12^3x32, 4^4 aggregates, 32 null vectors): the persistent kernel against
+    the launch-per-operation path, CUDA events per solve."""
+    import synth
+    dims = (12, 12, 12, 32)
+    w = WORKLOAD
+    U = synth.gauge_exp(dims, w["eps"], w["gauge_seed"])
+    lat = mrhs.mrhs_create_lattice(dims, -1, torch.cuda.current_device())
+    mrhs.mrhs_load_gauge(lat, U)
+    mrhs.mrhs_build_clover(lat, w["mass"], w["csw"])
+    out = {"case": "coarsest", "fine_dims": list(dims), "nrhs": 48, "coarse_m": MG_PARAMS["coarse_m"]}
+    for fused in (1, 0):
+        p = mrhs.mrhs_mg_default_params()
+        p.n_levels = 2
+        for mu in range(4):
+            p.block[0][mu] = 4
+        p.n_vec[0] = 32
+        p.max_rhs = 48
+        p.coarse_precision = mrhs.MRHS_FP16
+        p.setup_sweeps = 2
+        p.coarse_m = MG_PARAMS["coarse_m"]
+        p.coarse_fused = fused
+        mg = mrhs.mrhs_setup_mg(lat, p)
+        d, dof = mrhs.mrhs_mg_level_info(mg, 1)
+        cv = torch.randn((volume(d), dof, 48), dtype=torch.complex64, device="cuda")
+        co = torch.zeros_like(cv)
+        out["coarsest_dims"] = list(d)
+        out["persistent_kernel" if fused else "launch_per_operation"] = {
+            "ms_per_solve": ev(lambda: mrhs.mrhs_coarsest_solve(mg, cv, co, 48)),
+            "info": list(mrhs.mrhs_coarsest_fused_info(mg))}
+        mrhs.mrhs_destroy_mg(mg)
+    mrhs.mrhs_destroy_lattice(lat)
+    return out
+
+
 def run_coarse_case(mrhs, torch, reps):
     """Coarse level and intergrid operators on 24^4 (Haar gauge) with 4^4 aggregates and 32 null
     vectors: the 6^4 coarse lattice with nc = 64.  Per nRHS in {12, 24, 48}: the coarse stencil with FP32
@@ -1130,7 +1170,8 @@ def main():
     ap.add_argument("--sap-mr", type=int, default=4)
     ap.add_argument("--sap-cycles", type=int, default=1)
     ap.add_argument("--case", default=None, choices=["stencil", "stencil-sweep", "schur", "intergrid", "blas",
-                                                     "coarse", "oracle-table", "serving", "c0", "batch"],
+                                                     "coarse", "coarsest", "oracle-table", "serving", "c0",
+                                                     "batch"],
                     help="run a small profiling case of one kernel family instead of the benchmark")
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--blas-rows", type=int, default=16 ** 4 * 12,

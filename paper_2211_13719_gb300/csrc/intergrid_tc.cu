@@ -153,11 +153,11 @@ constexpr int IG_STAGES = 3;  // P tiles in flight per CTA
 // The output columns of D interleave Re and Im (2r: Re psi[r], 2r + 1: Im
 // psi[r]), so tensor-memory lane rho holds fine row rho in memory order and
 // each thread stores its own row.  Two accumulators: the MMAs of tile t + 1
-// run while tile t is drained.
-constexpr int IG_PTHREADS = 128;
-
-template <int VEC>
-__global__ void __launch_bounds__(IG_PTHREADS) k_prolong_tc(const float2 *__restrict__ coarse,
+// run while tile t is drained.  THR = 256 (an autotuner variant): the two
+// warps of each tensor-memory lane quarter share a row's columns, twice the
+// warps draining the store-bound epilogue.
+template <int VEC, int THR>
+__global__ void __launch_bounds__(THR) k_prolong_tc(const float2 *__restrict__ coarse,
                                                             const uint8_t *__restrict__ PA, float2 *__restrict__ fine,
                                                             IgArgs a, int *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
@@ -267,10 +267,11 @@ __global__ void __launch_bounds__(IG_PTHREADS) k_prolong_tc(const float2 *__rest
             ++copies;
         }
         fence_after_sync();
-        const int rho = t * IG_ROWS + 32 * warp + lane;
+        const int q = warp & 3, grp = warp >> 2;  // lane quarter, column group
+        const int rho = t * IG_ROWS + 32 * q + lane;
         float2 *dst = rho < a.R ? fine + (int64_t)rowoff[rho] * n : nullptr;
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t & 1) * acc_cols;
-        for (int c0 = 0; c0 < 2 * n; c0 += 16) {
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t & 1) * acc_cols;
+        for (int c0 = 16 * grp; c0 < 2 * n; c0 += 16 * (THR / 128)) {
             float v[16];
             tmem_ld16(trow + (uint32_t)c0, v);
             if (!dst) continue;
@@ -562,6 +563,8 @@ IgArgs ig_args(const Level &f, const Level &c, int n) {
     return a;
 }
 
+constexpr int kProlongThreads[] = {128, 256};  // autotuner variants of the prolongation
+
 size_t prolong_smem(int npad, int R) {
     const size_t bt = ((size_t)npad * 128 + 1023) & ~size_t(1023);
     return 1024 + bt + (size_t)IG_STAGES * IG_TILE + sizeof(int) * (size_t)R;
@@ -658,18 +661,31 @@ void prolong_fields_tc(const Level &f, const Level &c, const float2 *coarse, flo
     const IgArgs a = ig_args(f, c, n);
     static bool attr = false;
     if (!attr) {
-        allow_smem(k_prolong_tc<1>, prolong_smem(128, IG_MAX_ROWS));
-        allow_smem(k_prolong_tc<2>, prolong_smem(128, IG_MAX_ROWS));
+        allow_smem(k_prolong_tc<1, 128>, prolong_smem(128, IG_MAX_ROWS));
+        allow_smem(k_prolong_tc<2, 128>, prolong_smem(128, IG_MAX_ROWS));
+        allow_smem(k_prolong_tc<1, 256>, prolong_smem(128, IG_MAX_ROWS));
+        allow_smem(k_prolong_tc<2, 256>, prolong_smem(128, IG_MAX_ROWS));
         attr = true;
     }
     const dim3 grid((unsigned)c.V, 2);
+    const size_t smem = prolong_smem(a.npad, a.R);
+    const bool pr = paired(fine, n);
+    auto launch = [&](int v) {
+        const uint8_t *pa = f.PA.as<uint8_t>();
+        int *err = f.IgErr.as<int>();
+        if (kProlongThreads[v] == 256) {
+            if (pr) k_prolong_tc<2, 256><<<grid, 256, smem, s>>>(coarse, pa, fine, a, err);
+            else k_prolong_tc<1, 256><<<grid, 256, smem, s>>>(coarse, pa, fine, a, err);
+        } else {
+            if (pr) k_prolong_tc<2, 128><<<grid, 128, smem, s>>>(coarse, pa, fine, a, err);
+            else k_prolong_tc<1, 128><<<grid, 128, smem, s>>>(coarse, pa, fine, a, err);
+        }
+        MRHS_CUDA(cudaGetLastError());
+    };
+    // the output overwrites `fine` from `coarse` alone: repeated launches are harmless
+    const int v = tune_pick("k_prolong_tc", c.L, n, 2, launch, s);
     MRHS_TIMED("k_prolong_tc", s);
-    if (paired(fine, n))
-        k_prolong_tc<2><<<grid, IG_PTHREADS, prolong_smem(a.npad, a.R), s>>>(coarse, f.PA.as<uint8_t>(), fine, a,
-                                                                     f.IgErr.as<int>());
-    else
-        k_prolong_tc<1><<<grid, IG_PTHREADS, prolong_smem(a.npad, a.R), s>>>(coarse, f.PA.as<uint8_t>(), fine, a,
-                                                                     f.IgErr.as<int>());
+    launch(v);
     MRHS_LAUNCHED("k_prolong_tc");
 }
 

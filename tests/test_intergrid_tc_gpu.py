@@ -78,3 +78,37 @@ def test_tensor_core_transfer_second_level():
     finally:
         mrhs.mrhs_destroy_mg(mg)
         mrhs.mrhs_destroy_lattice(lat)
+
+
+@pytest.mark.parametrize("n", [5, 48])
+def test_prolongation_variants_are_bitwise_equal(tmp_path, n):
+    """The autotuner's prolongation variants (128 and 256 threads: the same MMAs, the epilogue's
+    columns split over more warps) write the same field, bit for bit, and pass the oracle's bar."""
+    dims, block, N = (8, 8, 8, 16), (4, 4, 4, 4), 32
+    U = synth.gauge_exp(dims, 0.4, 1201)
+    V = wilson.volume(dims)
+    v0 = synth.gaussian_field(V, 12, N, 3301)
+    lat = make_lattice(U, dims, -0.2, 1.0)
+    mg = make_mg(lat, dict(n_levels=2, blocks=[block], nvec=[N], setup_sweeps=0, max_rhs=64,
+                           coarse_precision=mrhs.MRHS_FP16), [v0])
+    try:
+        cd = coarse.coarse_dims(dims, block)
+        Vc = wilson.volume(cd)
+        cin = synth.gaussian_field(Vc, 2 * N, n, 6300 + n, np.complex64)
+        outs = []
+        for variant in (0, 1):
+            path = tmp_path / f"tune{variant}.txt"
+            path.write_text(f"k_prolong_tc {cd[0]} {cd[1]} {cd[2]} {cd[3]} {n} {variant} 2 1.0 1.0\n")
+            mrhs.mrhs_tune_clear()
+            mrhs.mrhs_tune_load(str(path))
+            d_f = to_dev(np.full((V, 12, n), np.nan, np.complex64))
+            mrhs.mrhs_prolong(mg, 0, to_dev(cin), d_f, n)
+            outs.append(to_host(d_f))
+        assert np.array_equal(outs[0], outs[1])
+        P = coarse.build_prolongator(v0, dims, block, FINE_CHIRALITY)
+        ref = coarse.prolong(P, cin.astype(np.complex128), dims, block)
+        assert site_rel_err(outs[1].astype(np.complex128), ref) < TOL
+    finally:
+        mrhs.mrhs_tune_clear()
+        mrhs.mrhs_destroy_mg(mg)
+        mrhs.mrhs_destroy_lattice(lat)
