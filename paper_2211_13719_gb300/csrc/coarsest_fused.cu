@@ -20,9 +20,10 @@
 //  * The stencil of a step is the tcgen05 MMA of the coarse stencil kernel:
 //    link and neighbour tiles through a bulk-copy ring, FP32 accumulation in
 //    tensor memory (one accumulator per own site) allocated once for the
-//    launch.  Its result, scaled to w = A v_j, stays in shared memory for
-//    the dots and the update of the same step.  While thread 0 streams the
-//    stencil, another warp does the Givens update of the previous column.
+//    launch.  Each own site has its own copy ring and issuing thread.  The
+//    result, scaled to w = A v_j, stays in shared memory for the dots and the
+//    update of the same step.  While the stencils stream, another warp does
+//    the Givens update of the previous column.
 //  * Grid-wide barriers (a monotonic arrival counter; every wait bounded)
 //    separate the three phases of a step: (1) stencil + partial dots,
 //    (2) the sum of the partials of each RHS column by the column's owner
@@ -57,7 +58,7 @@ using namespace tc;
 constexpr int NC = 64;                  // coarse dof
 constexpr int MROWS = 128;              // 2 * NC real rows of a link tile
 constexpr int A_TILE = MROWS * NC * 2;  // bytes of one 16-bit link tile
-constexpr int RING = 5;                 // bulk-copy ring depth
+constexpr int RING = 3;                 // bulk-copy ring depth of each own site (one ring and thread per site)
 constexpr int MMAX = 16;                // largest restart length
 constexpr int THREADS = 512;            // 16 warps: the row phases are bound by L2 latency
 constexpr int MAX_SITES = 2;            // most coarse sites of one CTA (each staged in shared memory)
@@ -226,43 +227,40 @@ __device__ void back_substitute(const FusedArgs &a, int r) {
     for (int i = 0; i < m; ++i) a.y[(int64_t)i * a.n + r] = yy[i];
 }
 
-// Thread 0: for each of the CTA's `ns` sites the 9 direction tiles of its
-// stencil through the ring and the MMAs into that site's tensor-memory
-// accumulator, then one commit on `done`.  q0: ring position of the first
-// load, continued across steps.  On an expired wait the loads in flight are
-// drained (every one is in its own stage, so its parity is exact).
-__device__ bool stencil_issue(const FusedArgs &a, int cta, int ns, uint32_t sbase, uint32_t full0, uint32_t empty0,
-                              uint32_t done, uint32_t tmem, uint32_t &q0) {
+// One issuing thread per own site: the 9 direction tiles of that site's
+// stencil through the site's own ring (its stages at `sbase`, its barriers at
+// full0 / empty0) and the MMAs into its tensor-memory accumulator `acc`, then
+// a commit on `done` (which expects one commit per own site).  q0: the ring
+// position of the site's first load, continued across steps.  On an expired
+// wait the loads in flight are drained (every one is in its own stage, so its
+// parity is exact).
+__device__ bool stencil_issue(const FusedArgs &a, int64_t site, uint32_t sbase, uint32_t full0, uint32_t empty0,
+                              uint32_t done, uint32_t acc, uint32_t &q0) {
     bool ok = true;
     int issued = 0, consumed = 0;
-    const int total = 9 * ns;
-    for (int step = 0; step < total + RING - 1 && ok; ++step) {
-        if (step < total) {
+    for (int step = 0; step < 9 + RING - 1 && ok; ++step) {
+        if (step < 9) {
             const uint32_t q = q0 + step, s = q % RING;
             if (q >= (uint32_t)RING) ok = mbar_wait(empty0 + 8 * s, ((q / RING) - 1) & 1);
             if (!ok) break;
-            const int ls = step / 9, d = step - 9 * ls;
-            const int64_t site = cta + (int64_t)ls * a.G;
-            const int64_t nb = stencil_nb_site(site, a.L, d);
+            const int64_t nb = stencil_nb_site(site, a.L, step);
             const uint32_t sa = sbase + s * a.stage_bytes;
             mbar_expect_tx(full0 + 8 * s, A_TILE + a.b_tile);
-            bulk_g2s(sa, a.Abf + ((size_t)site * 9 + d) * A_TILE, A_TILE, full0 + 8 * s);
+            bulk_g2s(sa, a.Abf + ((size_t)site * 9 + step) * A_TILE, A_TILE, full0 + 8 * s);
             bulk_g2s(sa + A_TILE, a.img + (size_t)nb * a.b_tile, a.b_tile, full0 + 8 * s);
             ++issued;
         }
         const int e = step - (RING - 1);
-        if (e >= 0 && e < total) {
+        if (e >= 0 && e < 9) {
             const uint32_t q = q0 + e, s = q % RING;
             ok = mbar_wait_n(full0 + 8 * s, (q / RING) & 1, q == 0 ? a.first_limit : SPIN_LIMIT);
             if (!ok) break;
             ++consumed;
             fence_after_sync();
-            const int ls = e / 9, d = e - 9 * ls;
-            const uint32_t acc = tmem + (uint32_t)(ls * a.cols_site);
             const uint32_t sa = sbase + s * a.stage_bytes, sb = sa + A_TILE;
 #pragma unroll
             for (int kk = 0; kk < NC / 16; ++kk)
-                mma_16bit(acc, sdesc(sa + kk * 32), sdesc(sb + kk * 32), a.idesc, (d > 0 || kk > 0) ? 1u : 0u);
+                mma_16bit(acc, sdesc(sa + kk * 32), sdesc(sb + kk * 32), a.idesc, (e > 0 || kk > 0) ? 1u : 0u);
             mma_commit(empty0 + 8 * s);
         }
     }
@@ -273,7 +271,7 @@ __device__ bool stencil_issue(const FusedArgs &a, int cta, int ns, uint32_t sbas
         }
     }
     mma_commit(done);
-    q0 += total;
+    q0 += 9;
     return ok;
 }
 
@@ -315,7 +313,7 @@ __host__ __device__ inline size_t overlay_bytes(int n, int npad, Overlay *o, uin
 }
 
 __host__ __device__ inline size_t fused_smem_bytes(int n, int npad, uint32_t stage_bytes) {
-    const size_t ring = (size_t)RING * stage_bytes;
+    const size_t ring = (size_t)MAX_SITES * RING * stage_bytes;
     const size_t ov = overlay_bytes(n, npad, nullptr, nullptr);
     return (ring > ov ? ring : ov) + 1024;
 }
@@ -323,7 +321,7 @@ __host__ __device__ inline size_t fused_smem_bytes(int n, int npad, uint32_t sta
 template <int FMT>
 __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ uint64_t bars[2 * RING + 1];
+    __shared__ uint64_t bars[2 * MAX_SITES * RING + 1];  // per own site: RING full, RING empty; then done
     __shared__ uint32_t tmem_base_sh;
     __shared__ int flag_sh, abort_sh;
     __shared__ double red_d[THREADS];
@@ -339,7 +337,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
     const int64_t F = (int64_t)a.V * NC * n;     // complex values per field
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t sbase = smem_u32(base);
-    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[RING]), done = smem_u32(&bars[2 * RING]);
+    const uint32_t done = smem_u32(&bars[2 * MAX_SITES * RING]);
+    // ring of own site ls: stages at ring_of(ls), barriers full_of(ls) / empty_of(ls)
+    auto full_of = [&](int ls) { return smem_u32(&bars[2 * RING * ls]); };
+    auto empty_of = [&](int ls) { return smem_u32(&bars[2 * RING * ls + RING]); };
+    auto ring_of = [&](int ls) { return sbase + (uint32_t)(ls * RING) * a.stage_bytes; };
     Overlay ov;
     overlay_bytes(n, a.npad, &ov, base);
     const RowMap t(n);
@@ -351,11 +353,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
     auto Wrow = [&](int ls, int k) { return ov.W + ((size_t)ls * NC + k) * ov.ldw; };
 
     if (tid == 0) {
-        for (int s = 0; s < RING; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
-        }
-        mbar_init(done, 1);
+        for (int ls = 0; ls < MAX_SITES; ++ls)
+            for (int s = 0; s < RING; ++s) {
+                mbar_init(full_of(ls) + 8 * s, 1);
+                mbar_init(empty_of(ls) + 8 * s, 1);
+            }
+        mbar_init(done, ns);  // one MMA commit per own site and step
         abort_sh = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -474,12 +477,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_coarsest_gmres(const FusedArgs a
             cinv_sh[tid] = eta > 0.0 ? (float)(1.0 / ((double)sg * eta)) : 0.f;
         }
         __syncthreads();
-        // (1) thread 0 streams the stencil of the own sites through the tensor cores; meanwhile thread 32
-        // folds column j - 1 into the owned columns' Givens state (h_{j,j-1} = eta_j) and every thread
-        // normalises its rows of v_j = u_j / eta_j
-        if (tid == 0) {
+        // (1) threads 0 and 64 stream the stencils of the first and the second own site through their
+        // rings and the tensor cores; meanwhile thread 32 folds column j - 1 into the owned columns'
+        // Givens state (h_{j,j-1} = eta_j) and every thread normalises its rows of v_j = u_j / eta_j
+        if (tid == 0 || (tid == 64 && ns > 1)) {
+            const int ls = tid == 0 ? 0 : 1;
             fence_proxy_async_global();  // the neighbours' images were written through the generic proxy
-            if (!stencil_issue(a, cta, ns, sbase, full0, empty0, done, tmem, q0)) {
+            if (!stencil_issue(a, site_of(ls), ring_of(ls), full_of(ls), empty_of(ls), done,
+                               tmem + (uint32_t)(ls * a.cols_site), q0)) {
                 record_error(a);
                 abort_sh = 1;
             }
