@@ -24,6 +24,7 @@
 #include "internal.cuh"
 #include "pair.cuh"
 #include "spin.cuh"
+#include "tc_common.cuh"
 
 namespace mrhs {
 
@@ -460,24 +461,34 @@ __device__ __forceinline__ cplx<float> cadd_rn(cplx<float> a, cplx<float> b) {
     return {__fadd_rn(a.re, b.re), __fadd_rn(a.im, b.im)};
 }
 
-template <int MU, bool FWD, int N>
-__device__ __forceinline__ void hop_r1(cplx<float> (&acc)[12], const float2 *__restrict__ U,
-                                      const float2 *__restrict__ in, int nb, int link_site, bool flip, int r,
-                                      int n_rt = 0) {
+// one complex value of a neighbour spinor: from global memory (read-only path)
+// or from a shared-memory copy
+template <bool SMEM> __device__ __forceinline__ cplx<float> ld_src(const float2 *__restrict__ p, int off) {
+    if constexpr (SMEM) {
+        const float2 v = p[off];
+        return {v.x, v.y};
+    } else {
+        return ld_c1(p, off);
+    }
+}
+
+// one hop for one RHS: pin points at the neighbour's first spin-colour
+// component of this RHS, components n apart
+template <int MU, bool FWD, bool SMEM>
+__device__ __forceinline__ void hop_r1_at(cplx<float> (&acc)[12], const float2 *__restrict__ U,
+                                         const float2 *__restrict__ pin, int n, int link_site, bool flip) {
     using P = Proj<MU>;
     constexpr int F0 = FWD ? P::F0 : neg_f<P::F0>::v;
     constexpr int F1 = FWD ? P::F1 : neg_f<P::F1>::v;
     constexpr int G2 = FWD ? P::G2 : neg_f<P::G2>::v;
     constexpr int G3 = FWD ? P::G3 : neg_f<P::G3>::v;
-    const int n = N ? N : n_rt;  // RHS count: compiled in, or at run time (N = 0)
-    const float2 *pin = in + ((int64_t)nb * 12 * n + r);
     cplx<float> h0[3], h1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const cplx<float> p0 = ld_c1(pin, (0 * 3 + c) * n);
-        const cplx<float> p1 = ld_c1(pin, (1 * 3 + c) * n);
-        const cplx<float> pa = ld_c1(pin, (P::P0 * 3 + c) * n);
-        const cplx<float> pb = ld_c1(pin, (P::P1 * 3 + c) * n);
+        const cplx<float> p0 = ld_src<SMEM>(pin, (0 * 3 + c) * n);
+        const cplx<float> p1 = ld_src<SMEM>(pin, (1 * 3 + c) * n);
+        const cplx<float> pa = ld_src<SMEM>(pin, (P::P0 * 3 + c) * n);
+        const cplx<float> pb = ld_src<SMEM>(pin, (P::P1 * 3 + c) * n);
         h0[c] = cadd_rn(p0, fmul<F0>(pa));
         h1[c] = cadd_rn(p1, fmul<F1>(pb));
     }
@@ -509,6 +520,14 @@ __device__ __forceinline__ void hop_r1(cplx<float> (&acc)[12], const float2 *__r
         acc[2 * 3 + row] = cadd_rn(acc[2 * 3 + row], fmul<G2>(P::Q2 == 0 ? s0 : s1));
         acc[3 * 3 + row] = cadd_rn(acc[3 * 3 + row], fmul<G3>(P::Q3 == 0 ? s0 : s1));
     }
+}
+
+template <int MU, bool FWD, int N>
+__device__ __forceinline__ void hop_r1(cplx<float> (&acc)[12], const float2 *__restrict__ U,
+                                      const float2 *__restrict__ in, int nb, int link_site, bool flip, int r,
+                                      int n_rt = 0) {
+    const int n = N ? N : n_rt;  // RHS count: compiled in, or at run time (N = 0)
+    hop_r1_at<MU, FWD, false>(acc, U, in + ((int64_t)nb * 12 * n + r), n, link_site, flip);
 }
 
 // o = M v for chirality block chi of a site-major compact Hermitian site matrix (one RHS)
@@ -892,6 +911,7 @@ struct KArgsEO {
     KArgs32 k;   // full-lattice geometry (k.V is the full volume), n, RHS pairs
     int parity;  // parity of the output sites
     int V2;      // V / 2
+    int ts;      // host side: > 0 selects the half-line ring kernel with ts time slices per CTA
 };
 
 template <int MODE, int N, bool AOS>
@@ -988,44 +1008,13 @@ __global__ void __launch_bounds__(128, 3) k_eo_x2(const float2 *__restrict__ U, 
     }
 }
 
-// k_eo_x2 with one RHS per thread (scalar FMA in the paired code's order: bitwise equal results)
-template <int MODE, int N, int MINB = 6>
-__global__ void __launch_bounds__(128, MINB) k_eo_r1(const float2 *__restrict__ U, const float2 *__restrict__ M,
-                                                   const float2 *__restrict__ in, const float2 *__restrict__ self,
-                                                   float2 *__restrict__ out, KArgsEO e) {
-    const KArgs32 &a = e.k;
-    const int item = blockIdx.x * blockDim.x + threadIdx.x;
-    int c[4], r;
-    if (!visit_coords(a, item, e.V2, true, c, r, 1)) return;
-    c[0] *= 2;
-    if (((c[0] + c[1] + c[2] + c[3]) & 1) != e.parity) ++c[0];
-    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
-    const int cb = site >> 1;
-    cplx<float> acc[12];
-#pragma unroll
-    for (int i = 0; i < 12; ++i) acc[i] = {0.f, 0.f};
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-        const int L = a.L[mu], st = a.stride[mu];
-        const bool wrapF = (c[mu] == L - 1), wrapB = (c[mu] == 0);
-        const int sf = wrapF ? site - st * (L - 1) : site + st;
-        const int sb = wrapB ? site + st * (L - 1) : site - st;
-        const bool flipF = mu == 3 && wrapF && a.tb < 0;
-        const bool flipB = mu == 3 && wrapB && a.tb < 0;
-        if (mu == 0) {
-            hop_r1<0, true, N>(acc, U, in, sf >> 1, site, flipF, r);
-            hop_r1<0, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
-        } else if (mu == 1) {
-            hop_r1<1, true, N>(acc, U, in, sf >> 1, site, flipF, r);
-            hop_r1<1, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
-        } else if (mu == 2) {
-            hop_r1<2, true, N>(acc, U, in, sf >> 1, site, flipF, r);
-            hop_r1<2, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
-        } else {
-            hop_r1<3, true, N>(acc, U, in, sf >> 1, site, flipF, r);
-            hop_r1<3, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
-        }
-    }
+// k_eo_x2 with one RHS per thread (scalar FMA in the paired code's order: bitwise equal results).
+// eo_r1_finish: the mode's epilogue at the output site (site, half-field index cb) for RHS r,
+// shared with the ring kernel below.
+template <int MODE, int N>
+__device__ __forceinline__ void eo_r1_finish(const cplx<float> (&acc)[12], const float2 *__restrict__ M,
+                                             const float2 *__restrict__ in, const float2 *__restrict__ self,
+                                             float2 *__restrict__ out, int site, int cb, int r) {
     const int64_t base = (int64_t)cb * 12 * N + r;
     auto st1 = [&](int i, cplx<float> v) { __stcs(out + base + i * N, make_float2(v.re, v.im)); };
     if constexpr (MODE == EO_HOP) {
@@ -1083,6 +1072,208 @@ __global__ void __launch_bounds__(128, MINB) k_eo_r1(const float2 *__restrict__ 
     }
 }
 
+// the hops of direction mu at output site `site` (coordinates c) from the other
+// parity's half field in global memory
+template <int MU, int N>
+__device__ __forceinline__ void eo_r1_hops_global(cplx<float> (&acc)[12], const float2 *__restrict__ U,
+                                                  const float2 *__restrict__ in, const KArgs32 &a, int site,
+                                                  const int c[4], int r) {
+    const int L = a.L[MU], st = a.stride[MU];
+    const bool wrapF = (c[MU] == L - 1), wrapB = (c[MU] == 0);
+    const int sf = wrapF ? site - st * (L - 1) : site + st;
+    const int sb = wrapB ? site + st * (L - 1) : site - st;
+    const bool flipF = MU == 3 && wrapF && a.tb < 0;
+    const bool flipB = MU == 3 && wrapB && a.tb < 0;
+    // neighbours live in the other parity's half field, at index site / 2
+    hop_r1<MU, true, N>(acc, U, in, sf >> 1, site, flipF, r);
+    hop_r1<MU, false, N>(acc, U, in, sb >> 1, sb, flipB, r);
+}
+
+template <int MODE, int N>
+__device__ __forceinline__ void eo_r1_site(const float2 *__restrict__ U, const float2 *__restrict__ M,
+                                           const float2 *__restrict__ in, const float2 *__restrict__ self,
+                                           float2 *__restrict__ out, const KArgs32 &a, const int c[4], int r) {
+    const int site = c[0] + a.L[0] * (c[1] + a.L[1] * (c[2] + a.L[2] * c[3]));
+    cplx<float> acc[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = {0.f, 0.f};
+    eo_r1_hops_global<0, N>(acc, U, in, a, site, c, r);
+    eo_r1_hops_global<1, N>(acc, U, in, a, site, c, r);
+    eo_r1_hops_global<2, N>(acc, U, in, a, site, c, r);
+    eo_r1_hops_global<3, N>(acc, U, in, a, site, c, r);
+    eo_r1_finish<MODE, N>(acc, M, in, self, out, site, site >> 1, r);
+}
+
+template <int MODE, int N, int MINB = 6>
+__global__ void __launch_bounds__(128, MINB) k_eo_r1(const float2 *__restrict__ U, const float2 *__restrict__ M,
+                                                   const float2 *__restrict__ in, const float2 *__restrict__ self,
+                                                   float2 *__restrict__ out, KArgsEO e) {
+    const KArgs32 &a = e.k;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    int c[4], r;
+    if (!visit_coords(a, item, e.V2, true, c, r, 1)) return;
+    c[0] *= 2;
+    if (((c[0] + c[1] + c[2] + c[3]) & 1) != e.parity) ++c[0];
+    eo_r1_site<MODE, N>(U, M, in, self, out, a, c, r);
+}
+
+// ----------------------------------- even-odd hop with a ring of half lines
+// One CTA per (y, z) column and segment of `ts` time slices.  The other
+// parity's half line at (y, z, t) -- Lx / 2 sites x 12 x N, contiguous in the
+// half field -- is bulk-copied into a ring of RING_SLOTS shared-memory slots,
+// one copy per site, by a producer warp; the compute threads (one per output
+// site of the line and RHS) read the x neighbours (same half line) and the t
+// neighbours (the lines of t - 1 and t + 1) from the ring and only the y and
+// z neighbours from global memory.  Each half line crosses L2 -> SM once per
+// column instead of once per consumer, and the staged half of the neighbour
+// reads no longer waits on L2.  Line j of the segment is t = t0 - 1 + j; step
+// i computes t0 + i from lines i, i + 1, i + 2 while line i + 3 lands; a
+// compute warp releases line i's slot (empty barrier) after step i and the
+// producer then copies line i + 4 into it.  Every hop is the one-RHS hop of
+// k_eo_r1 in the same order, so outputs are bitwise those of k_eo_r1.
+// Every wait is bounded: a compute warp whose wait gives up (or that finds the
+// abort flag set) computes from global memory from then on (the same values),
+// and the producer stops copying and waits, bounded, for the copies it issued.
+constexpr int RING_SLOTS = 4;
+constexpr int RING_MAX_COMPUTE = 576;  // compute threads per CTA (Lx / 2 x N)
+
+struct RingArgs {
+    int H;                 // sites per half line (L[0] / 2)
+    int ts;                // time slices per CTA
+    uint32_t first_limit;  // try_wait rounds of a compute warp's first wait (SPIN_LIMIT; 0 expires it)
+};
+
+__device__ __forceinline__ void mbar_arrive_cta(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <int MODE, int N>
+__global__ void __launch_bounds__(RING_MAX_COMPUTE + 32, 1)
+    k_eo_ring(const float2 *__restrict__ U, const float2 *__restrict__ M, const float2 *__restrict__ in,
+              const float2 *__restrict__ self, float2 *__restrict__ out, KArgsEO e, RingArgs g) {
+    extern __shared__ __align__(16) float2 ring_raw[];
+    __shared__ __align__(8) uint64_t bars[2 * RING_SLOTS];
+    // [RING_SLOTS][H][12][N], 16-byte aligned for the bulk copies
+    float2 *const ring = ring_raw + ((16u - (tc::smem_u32(ring_raw) & 15u)) & 15u) / 8u;
+    __shared__ int abort_sh;
+    const KArgs32 &a = e.k;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int H = g.H, NCT = H * N, ncw = NCT / 32;
+    int u = blockIdx.x;
+    const int y = u % a.L[1];
+    u /= a.L[1];
+    const int z = u % a.L[2];
+    const int t0 = (u / a.L[2]) * g.ts;
+    const int nlines = g.ts + 2;
+    const int slot_elems = H * 12 * N;
+    const uint32_t site_bytes = 12u * N * 8u, slot_bytes = (uint32_t)H * site_bytes;
+    const uint32_t full0 = tc::smem_u32(&bars[0]), empty0 = tc::smem_u32(&bars[RING_SLOTS]);
+    if (tid == 0) {
+        for (int s = 0; s < RING_SLOTS; ++s) {
+            tc::mbar_init(full0 + 8 * s, 1);
+            tc::mbar_init(empty0 + 8 * s, ncw);
+        }
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // first half-field index of the half line of line j (t periodic)
+    auto line_base = [&](int j) -> int64_t {
+        int t = t0 - 1 + j;
+        t = t < 0 ? t + a.L[3] : (t >= a.L[3] ? t - a.L[3] : t);
+        return (int64_t)(y + a.L[1] * (z + a.L[2] * t)) * H;
+    };
+    if (warp == ncw) {
+        // producer: lane 0 copies line j into slot j % RING_SLOTS once the compute
+        // warps have released line j - RING_SLOTS
+        if (lane != 0) return;
+        const uint32_t ring0 = tc::smem_u32(ring);
+        int issued = 0;
+        for (int j = 0; j < nlines; ++j) {
+            const int s = j % RING_SLOTS;
+            if (j >= RING_SLOTS) {
+                if (!tc::mbar_wait(empty0 + 8 * s, ((j / RING_SLOTS) - 1) & 1)) {
+                    abort_sh = 1;
+                    break;
+                }
+                if (*(volatile int *)&abort_sh) break;
+                tc::fence_async_smem();
+            }
+            tc::mbar_expect_tx(full0 + 8 * s, slot_bytes);
+            const float2 *src = in + line_base(j) * 12 * N;
+            for (int q = 0; q < H; ++q)
+                tc::bulk_g2s(ring0 + s * slot_bytes + q * site_bytes, src + (int64_t)q * 12 * N, site_bytes,
+                             full0 + 8 * s);
+            issued = j + 1;
+        }
+        // the last copies issued into each slot land before the CTA exits
+        for (int s = 0; s < RING_SLOTS && s < issued; ++s) {
+            const int jl = s + ((issued - 1 - s) / RING_SLOTS) * RING_SLOTS;
+            tc::mbar_wait(full0 + 8 * s, (jl / RING_SLOTS) & 1);
+        }
+        return;
+    }
+    const int k = tid / N, r = tid - k * N;
+    bool fb = false;  // this warp computes from global memory (a wait gave up)
+    int waited = 0;   // lines this warp has waited for
+    for (int i = 0; i < g.ts; ++i) {
+        const int t = t0 + i;
+        for (; waited <= i + 2; ++waited) {
+            if (fb) continue;
+            const uint32_t bar = full0 + 8 * (waited % RING_SLOTS), par = (waited / RING_SLOTS) & 1;
+            const uint32_t lim = waited == 0 ? g.first_limit : tc::SPIN_LIMIT;
+            bool ok = false;
+            for (uint32_t it = 0; it < lim; ++it) {
+                if (tc::mbar_try_wait(bar, par)) {
+                    ok = true;
+                    break;
+                }
+                if (*(volatile int *)&abort_sh) break;
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                fb = true;
+                if (lane == 0) *(volatile int *)&abort_sh = 1;
+            }
+        }
+        const int off = (e.parity ^ (y + z + t)) & 1;
+        const int x = 2 * k + off;
+        const int c[4] = {x, y, z, t};
+        if (fb) {
+            eo_r1_site<MODE, N>(U, M, in, self, out, a, c, r);
+        } else {
+            const int site = x + a.L[0] * (y + a.L[1] * (z + a.L[2] * t));
+            const float2 *lm = ring + ((i + 0) % RING_SLOTS) * slot_elems;  // t - 1
+            const float2 *l0 = ring + ((i + 1) % RING_SLOTS) * slot_elems;  // t
+            const float2 *lp = ring + ((i + 2) % RING_SLOTS) * slot_elems;  // t + 1
+            cplx<float> acc[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) acc[q] = {0.f, 0.f};
+            {
+                // x: the neighbours x +- 1 are entries (x +- 1) / 2 of the current half line
+                const int L = a.L[0];
+                const int xf = x == L - 1 ? 0 : x + 1, xb = x == 0 ? L - 1 : x - 1;
+                const int sb = x == 0 ? site + (L - 1) : site - 1;
+                hop_r1_at<0, true, true>(acc, U, l0 + (xf >> 1) * 12 * N + r, N, site, false);
+                hop_r1_at<0, false, true>(acc, U, l0 + (xb >> 1) * 12 * N + r, N, sb, false);
+            }
+            eo_r1_hops_global<1, N>(acc, U, in, a, site, c, r);
+            eo_r1_hops_global<2, N>(acc, U, in, a, site, c, r);
+            {
+                // t: entry x / 2 = k of the half lines of t + 1 and t - 1
+                const int L = a.L[3], st = a.stride[3];
+                const bool wrapF = t == L - 1, wrapB = t == 0;
+                const int sb = wrapB ? site + st * (L - 1) : site - st;
+                hop_r1_at<3, true, true>(acc, U, lp + k * 12 * N + r, N, site, wrapF && a.tb < 0);
+                hop_r1_at<3, false, true>(acc, U, lm + k * 12 * N + r, N, sb, wrapB && a.tb < 0);
+            }
+            eo_r1_finish<MODE, N>(acc, M, in, self, out, site, site >> 1, r);
+        }
+        // line i is no longer read by this warp
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cta(empty0 + 8 * (i % RING_SLOTS));
+    }
+}
+
 static KArgsEO eo_args(const mrhs_lattice &lat, int n, int parity, const int pref[4] = nullptr) {
     KArgsEO e{};
     KArgs32 &a = e.k;
@@ -1125,6 +1316,29 @@ static void check_eo(const mrhs_lattice &lat, int n) {
 }
 
 enum { EO_NOMAT = 0, EO_MAT_C = 1, EO_MAT_CINV = 2 };
+
+// dynamic shared memory of the ring kernel: RING_SLOTS half lines of H sites (+ 16 B of alignment slack)
+static size_t ring_smem_bytes(int H, int n) { return (size_t)RING_SLOTS * H * 12 * n * 8 + 16; }
+
+static size_t ring_smem_limit() {
+    static int cached[64] = {};
+    int dev = 0, v = 0;
+    MRHS_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return (size_t)cached[dev];
+    MRHS_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (dev >= 0 && dev < 64) cached[dev] = v;
+    return (size_t)v;
+}
+
+// raise the dynamic shared-memory limit of k_eo_ring<MD, NC> once per device and size
+template <int MD, int NC, typename K> static void ring_set_smem(K kernel, size_t bytes) {
+    static size_t done[64] = {};
+    int dev = 0;
+    MRHS_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && done[dev] >= bytes) return;
+    MRHS_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (dev >= 0 && dev < 64) done[dev] = bytes;
+}
 
 // tune_scratch (EO_CINV_AXPY_HOP_MERGE only): a half field the tuner may write; the merge
 // accumulates into z, so it takes the variant tuned for EO_CINV_AXPY_HOP, timed into the scratch
@@ -1173,6 +1387,24 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
     const int64_t items = (int64_t)args[nx2].V2 * args[nx2].k.G;
     const unsigned blocks = (unsigned)((items + 127) / 128);
     const unsigned blocks_r1 = (unsigned)(((int64_t)args[0].V2 * n + 127) / 128);
+    // half-line ring variants of the two Schur-operator launches (compiled RHS counts
+    // below 64; Lx / 2 x n compute threads, whole warps, four slots of Lx / 2 x 12 x n
+    // values in shared memory): one CTA per (y, z) column and segment of L[3] or
+    // L[3] / 2 time slices.  Measured on GB300 (24^3 x 64, 48 RHS) 44 % slower for
+    // D_hat than the default (18 resident warps per SM against 32); kept as autotuner
+    // candidates for other shapes
+    const int H = lat.g.L[0] / 2;
+    const size_t ring_smem = ring_smem_bytes(H, n);
+    constexpr bool RING_MODE = MODE == EO_CINV_HOP || MODE == EO_SCHUR;
+    if (RING_MODE && nx2 > 0 && n != 64 && H <= 32 && H * n <= RING_MAX_COMPUTE && (H * n) % 32 == 0 && ring_smem <= ring_smem_limit() &&
+        (reinterpret_cast<uintptr_t>(in) & 15u) == 0) {
+        for (int seg : {1, 2}) {
+            if (lat.g.L[3] % seg || lat.g.L[3] / seg < 2) continue;
+            KArgsEO b = args[0];
+            b.ts = lat.g.L[3] / seg;
+            args.push_back(b);
+        }
+    }
     // as the full-lattice stencil: compile-time RHS count and site-major links /
     // site matrices for 16, 24, 32, 48, 64 RHS
     auto launch_m = [&](auto modec, int v, float2 *dst) {
@@ -1186,6 +1418,15 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
             const float2 *M = mat == EO_MAT_C      ? (AO ? lat.C32a.as<float2>() : lat.C32.as<float2>())
                               : mat == EO_MAT_CINV ? (AO ? lat.Cinv32a.as<float2>() : lat.Cinv32.as<float2>())
                                                    : nullptr;
+            if constexpr (NC > 0 && NC != 64 && AO && (MD == EO_CINV_HOP || MD == EO_SCHUR)) {
+                if (e.ts > 0) {
+                    const RingArgs g{H, e.ts, tc::SPIN_LIMIT};
+                    const unsigned grid = (unsigned)(lat.g.L[1] * lat.g.L[2] * (lat.g.L[3] / e.ts));
+                    ring_set_smem<MD, NC>(k_eo_ring<MD, NC>, ring_smem);
+                    k_eo_ring<MD, NC><<<grid, H * NC + 32, ring_smem, s>>>(U, M, in, self, dst, e, g);
+                    return;
+                }
+            }
             if constexpr (NC > 0 && AO) {
                 if (one) {
                     if (e.k.occ8) k_eo_r1<MD, NC, 8><<<blocks_r1, 128, 0, s>>>(U, M, in, self, dst, e);
