@@ -461,6 +461,17 @@ mrhs_status mrhs_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int nrhs, do
  * MRHS_ERR_TIMEOUT.  0 cancels.  MRHS_ERR_INVALID for launches < 0. */
 mrhs_status mrhs_debug_expire_waits(int launches);
 
+/* Testing hook, not part of the paper's method: the next `launches` launches
+ * of the half-line ring form of the even-odd hop (an autotuner variant of the
+ * two launches of mrhs_apply_schur's D_hat) that are not being recorded into
+ * a CUDA graph run with a zero try_wait bound on the first wait of every
+ * compute warp.  Each warp then reads its neighbours from global memory
+ * instead of the shared-memory ring (the same values: the output is bitwise
+ * unchanged), and the copy-issuing warp stops issuing and waits for the
+ * copies it has already issued before it returns, so nothing is left in
+ * flight.  0 cancels.  MRHS_ERR_INVALID for launches < 0. */
+mrhs_status mrhs_debug_expire_ring_waits(int launches);
+
 /* ------------------------------------------------------------------ */
 /* Serving: continuous batching of solve requests                      */
 /* ------------------------------------------------------------------ */

@@ -18,6 +18,7 @@
 // forms a 2-spin half spinor h = psi_up -+ A psi_dn, multiplies it by the
 // link, and rebuilds the lower spins from the two products.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 #include <vector>
 
@@ -1137,6 +1138,23 @@ __global__ void __launch_bounds__(128, MINB) k_eo_r1(const float2 *__restrict__ 
 constexpr int RING_SLOTS = 4;
 constexpr int RING_MAX_COMPUTE = 576;  // compute threads per CTA (Lx / 2 x N)
 
+mrhs_status api_record(mrhs_status code, const std::string &msg);
+
+// eager ring launches whose compute warps are to give up their first wait at once (test hook)
+std::atomic<int> g_expire_ring{0};
+
+static uint32_t ring_first_wait_limit(cudaStream_t s) {
+    if (g_expire_ring.load() <= 0) return tc::SPIN_LIMIT;
+    // a launch recorded into a graph would keep the expired limit for every replay: only eager launches
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MRHS_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return tc::SPIN_LIMIT;
+    int left = g_expire_ring.load();
+    while (left > 0 && !g_expire_ring.compare_exchange_weak(left, left - 1)) {
+    }
+    return left > 0 ? 0u : tc::SPIN_LIMIT;
+}
+
 struct RingArgs {
     int H;                 // sites per half line (L[0] / 2)
     int ts;                // time slices per CTA
@@ -1420,7 +1438,7 @@ static void launch_eo(const mrhs_lattice &lat, int mat, const float2 *in, const 
                                                    : nullptr;
             if constexpr (NC > 0 && NC != 64 && AO && (MD == EO_CINV_HOP || MD == EO_SCHUR)) {
                 if (e.ts > 0) {
-                    const RingArgs g{H, e.ts, tc::SPIN_LIMIT};
+                    const RingArgs g{H, e.ts, ring_first_wait_limit(s)};
                     const unsigned grid = (unsigned)(lat.g.L[1] * lat.g.L[2] * (lat.g.L[3] / e.ts));
                     ring_set_smem<MD, NC>(k_eo_ring<MD, NC>, ring_smem);
                     k_eo_ring<MD, NC><<<grid, H * NC + 32, ring_smem, s>>>(U, M, in, self, dst, e, g);
@@ -1942,3 +1960,9 @@ void build_clover(mrhs_lattice &lat, double mass, double csw, cudaStream_t s) {
 }
 
 }  // namespace mrhs
+
+extern "C" mrhs_status mrhs_debug_expire_ring_waits(int launches) {
+    if (launches < 0) return mrhs::api_record(MRHS_ERR_INVALID, "launches must be >= 0");
+    mrhs::g_expire_ring.store(launches);
+    return mrhs::api_record(MRHS_OK, "");
+}

@@ -172,6 +172,7 @@ PROTOTYPES = {
     "mrhs_coarsest_fused_info": (_I, [_P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "mrhs_mg_setup_times": (_I, [_P, _I, C.POINTER(C.c_double)]),
     "mrhs_debug_expire_waits": (_I, [_I]),
+    "mrhs_debug_expire_ring_waits": (_I, [_I]),
     "mrhs_solve": (_I, [_P, _P, _P, _I, _D, _P, C.POINTER(SolveStats), _P]),
     "mrhs_server_create": (_I, [C.POINTER(ServerParams), C.POINTER(_P)]),
     "mrhs_server_add_config": (_I, [_P, _P, _I, C.POINTER(C.c_int)]),
@@ -425,6 +426,10 @@ def mrhs_vcycle(mg, v_dev, z_dev, nrhs, stream=None):
 
 def mrhs_debug_expire_waits(launches):
     _check(lib().mrhs_debug_expire_waits(int(launches)))
+
+
+def mrhs_debug_expire_ring_waits(launches):
+    _check(lib().mrhs_debug_expire_ring_waits(int(launches)))
 
 
 def mrhs_solve(mg, b_dev, x_dev, nrhs, tol, rel_res_host=None, stream=None, allow_not_converged=False):

@@ -157,3 +157,40 @@ def test_solve_with_ring_variants_is_bitwise_the_default(tuner_state, tmp_path):
         mrhs.mrhs_destroy_lattice(lat)
     for v in rings:
         assert np.array_equal(xs[v], xs[0]), v
+
+
+def test_expired_ring_waits_fall_back_to_global_memory(tuner_state, tmp_path):
+    """mrhs_debug_expire_ring_waits(k): the next k eager ring launches give up their
+    first wait at once, every compute warp reads its neighbours from global memory
+    and the producer drains the copies it issued; D_hat stays bitwise the default's,
+    and the launches after it run the ring again with the same result."""
+    dims, n = (8, 8, 8, 8), 48
+    U = synth.gauge_haar(dims, 7401)
+    V2 = wilson.volume(dims) // 2
+    psi = synth.gaussian_field(V2, 12, n, 7402, np.complex64)
+    lat = make_lattice(U, dims, -0.2, 1.0)
+    try:
+        nv = _nvariants(lat, dims, n)
+        d_in = to_dev(psi)
+        d_out = to_dev(np.zeros_like(psi))
+        _force(tmp_path, dims, n, 0, nv)
+        mrhs.mrhs_tune_set_enabled(False)
+        mrhs.mrhs_apply_schur(lat, d_in, d_out, n)
+        ref = to_host(d_out)
+        for v in _ring_variants(dims, n, nv):
+            _force(tmp_path, dims, n, v, nv)
+            mrhs.mrhs_tune_set_enabled(False)
+            mrhs.mrhs_debug_expire_ring_waits(2)   # both launches of one D_hat
+            d_out.fill_(float("nan"))
+            mrhs.mrhs_apply_schur(lat, d_in, d_out, n)
+            expired = to_host(d_out)
+            d_out.fill_(float("nan"))
+            mrhs.mrhs_apply_schur(lat, d_in, d_out, n)
+            again = to_host(d_out)
+            assert np.array_equal(expired, ref), v
+            assert np.array_equal(again, ref), v
+        with pytest.raises(mrhs.MrhsError):
+            mrhs.mrhs_debug_expire_ring_waits(-1)
+    finally:
+        mrhs.mrhs_debug_expire_ring_waits(0)
+        mrhs.mrhs_destroy_lattice(lat)
