@@ -582,44 +582,62 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if rank == 0:
         # --- end to end through the C ABI with host buffers (pinned), copies inside the timed region.
-        # Every step uploads its sources and downloads its solution; the copies run on their
-        # own stream into double-buffered device fields, so step k+1's upload and step k's
-        # download overlap the solves (mrhs_solve returns when its solve is complete).
-        ke = max(2, min(args.steps, 4))
+        # Every step uploads its sources and downloads its solution; uploads and downloads run
+        # on two copy streams of their own (separate copy engines) into double-buffered device
+        # fields, so step k+1's upload and step k - 1's download overlap step k's solve
+        # (mrhs_solve returns when its solve is complete); only the first upload and the last
+        # download are exposed.
+        ke = max(2, min(args.steps, 8))
         bh = [b.cpu().pin_memory() for _ in range(2)]
         xh = [torch.empty_like(bh[0]).pin_memory() for _ in range(2)]
         bd = [b, torch.empty_like(b)]
         xd = [x, torch.empty_like(x)]
-        cs = torch.cuda.Stream()
+        up, down = torch.cuda.Stream(), torch.cuda.Stream()
         ev_in = [torch.cuda.Event(), torch.cuda.Event()]
         ev_out = [torch.cuda.Event(), torch.cuda.Event()]
+        ev_read = [torch.cuda.Event(), torch.cuda.Event()]
+        # the copy rates alone (one upload, one download of a step's field), for context; the
+        # first download into fresh page-locked memory also pays for touching its pages, so both
+        # download buffers are written once before the timed loop (as in a running pipeline)
+        torch.cuda.synchronize()
+        rates = {}
+        for name, dst, src in (("h2d_GBs", bd[1], bh[0]), ("d2h_first_touch_GBs", xh[0], bd[0]),
+                               ("d2h_GBs", xh[0], bd[0]), ("d2h_first_touch_buffer2_GBs", xh[1], bd[0])):
+            t0c = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            rates[name] = round(src.numel() * src.element_size() / (time.perf_counter() - t0c) / 1e9, 1)
         torch.cuda.synchronize()
         te0 = time.perf_counter()
-        with torch.cuda.stream(cs):
+        with torch.cuda.stream(up):
             bd[0].copy_(bh[0], non_blocking=True)
-            ev_in[0].record(cs)
+            ev_in[0].record(up)
         for k in range(ke):
             i = k % 2
             stream.wait_event(ev_in[i])
             if k + 1 < ke:
                 # buffer 1 - i was last read by step k - 1's solve, which has completed
-                with torch.cuda.stream(cs):
-                    cs.wait_event(ev_out[1 - i])
+                with torch.cuda.stream(up):
+                    up.wait_event(ev_out[1 - i])
                     bd[1 - i].copy_(bh[1 - i], non_blocking=True)
-                    ev_in[1 - i].record(cs)
+                    ev_in[1 - i].record(up)
+            # x buffer i was last read by step k - 2's download
+            stream.wait_event(ev_read[i])
             with torch.cuda.stream(stream):
                 xd[i].zero_()
             mrhs.mrhs_solve(mg, bd[i], xd[i], n, w["tol"], rel, stream=stream)
             ev_out[i].record(stream)
-            with torch.cuda.stream(cs):
-                cs.wait_event(ev_out[i])
+            with torch.cuda.stream(down):
+                down.wait_event(ev_out[i])
                 xh[i].copy_(xd[i], non_blocking=True)
+                ev_read[i].record(down)
         torch.cuda.synchronize()
         te = time.perf_counter() - te0
         bytes_io = V * 12 * n * 16
         extra["e2e"] = {"value": n * ke / te, "unit": "solves/s", "h2d_bytes_per_step": bytes_io,
                         "d2h_bytes_per_step": bytes_io, "steps": ke,
-                        "copies": "pinned host buffers, own copy stream, double-buffered device fields"}
+                        "copies": ("pinned host buffers, upload and download streams of their own, "
+                                   "double-buffered device fields"), "copy_rates_alone": rates}
         del bd[1], xd[1]
         # --- component breakdown (one profiled solve, eager V-cycle): the paper's Sec. 8 table
         # (reported from the solve stats of the timed steps)

@@ -924,7 +924,7 @@ __global__ void k_any_nonzero(const uint4 *__restrict__ p, int64_t count, unsign
 }
 
 void any_nonzero(const void *p, int64_t bytes, unsigned *flag, cudaStream_t s) {
-    MRHS_CUDA(cudaMemsetAsync(flag, 0, sizeof(unsigned), s));
+    zero_on_sms(flag, sizeof(unsigned), s);
     const int64_t count = bytes / 16;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)current_sms() * 8, ceil_div(count, 256)));
     k_any_nonzero<<<blocks, 256, 0, s>>>(static_cast<const uint4 *>(p), count, flag);
@@ -938,11 +938,75 @@ void cast(mrhs_precision pd, void *dst, mrhs_precision ps, const void *src, int6
     else if (pd == MRHS_FP64 && ps == MRHS_FP32)
         k_cast<double, float><<<nb, 256, 0, s>>>(static_cast<double *>(dst), static_cast<const float *>(src), count);
     else if (pd == ps) {
-        MRHS_CUDA(cudaMemcpyAsync(dst, src, count * complex_bytes(pd), cudaMemcpyDeviceToDevice, s));
+        copy_on_sms(dst, src, count * complex_bytes(pd), s);
         return;
     } else
         fail(MRHS_ERR_INVALID, "cast: unsupported precision pair");
     MRHS_LAUNCHED("k_cast");
+}
+
+// ------------------------------------------------- copies on the SMs
+// Copies issued as kernels instead of cudaMemcpyAsync: they never wait behind
+// the copy engines, which a caller's host transfers on other streams may hold
+// for hundreds of milliseconds.
+__global__ void k_copy16(uint4 *__restrict__ dst, const uint4 *__restrict__ src, int64_t n16) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+__global__ void k_copy4(unsigned *__restrict__ dst, const unsigned *__restrict__ src, int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+void copy_on_sms(void *dst, const void *src, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return;
+    if (bytes % 4) fail(MRHS_ERR_INVALID, "copy_on_sms: size must be a multiple of 4 bytes");
+    const bool v16 = bytes % 16 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0 &&
+                     (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
+    const int64_t n = (int64_t)(v16 ? bytes / 16 : bytes / 4);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)current_sms() * 8, ceil_div(n, 256)));
+    if (v16) k_copy16<<<blocks, 256, 0, s>>>(static_cast<uint4 *>(dst), static_cast<const uint4 *>(src), n);
+    else k_copy4<<<blocks, 256, 0, s>>>(static_cast<unsigned *>(dst), static_cast<const unsigned *>(src), n);
+    MRHS_CUDA(cudaGetLastError());
+    MRHS_LAUNCHED("k_copy");
+}
+
+__global__ void k_zero4(unsigned *__restrict__ dst, int64_t n4) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = 0u;
+}
+__global__ void k_zero16(uint4 *__restrict__ dst, int64_t n16) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+void zero_on_sms(void *dst, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return;
+    if (bytes % 4) fail(MRHS_ERR_INVALID, "zero_on_sms: size must be a multiple of 4 bytes");
+    const bool v16 = bytes % 16 == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
+    const int64_t n = (int64_t)(v16 ? bytes / 16 : bytes / 4);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)current_sms() * 8, ceil_div(n, 256)));
+    if (v16) k_zero16<<<blocks, 256, 0, s>>>(static_cast<uint4 *>(dst), n);
+    else k_zero4<<<blocks, 256, 0, s>>>(static_cast<unsigned *>(dst), n);
+    MRHS_CUDA(cudaGetLastError());
+    MRHS_LAUNCHED("k_zero");
+}
+
+void read_back(void *pinned_host, const void *dev, size_t bytes, cudaStream_t s) {
+    // page-locked host memory from cudaMallocHost is mapped at the same address on the device
+    copy_on_sms(pinned_host, dev, bytes, s);
+}
+
+int *pinned_flag_slot() {
+    struct Slot {
+        int *p = nullptr;
+        ~Slot() {
+            if (p) cudaFreeHost(p);
+        }
+    };
+    thread_local Slot slot;
+    if (!slot.p) MRHS_CUDA(cudaMallocHost(&slot.p, 4 * sizeof(int)));
+    return slot.p;
 }
 
 void axpy(mrhs_precision p, double a, const void *x, void *y, int64_t count, cudaStream_t s) {

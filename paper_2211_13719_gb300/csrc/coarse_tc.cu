@@ -320,7 +320,7 @@ void coarse_links_to_16bit(Level &c, mrhs_precision fmt, cudaStream_t s) {
     c.TcErr.alloc(sizeof(int));
     c.LinkScale.alloc(sizeof(float) * (size_t)c.V);
     c.ColScale.alloc(sizeof(float) * 64);
-    MRHS_CUDA(cudaMemsetAsync(c.TcErr.ptr, 0, sizeof(int), s));
+    zero_on_sms(c.TcErr.ptr, sizeof(int), s);
     k_link_scale<<<(unsigned)c.V, 256, 0, s>>>(c.A32.as<float2>(), c.LinkScale.as<float>(), 9);
     MRHS_LAUNCHED("k_link_scale");
     const int64_t count = c.V * 9 * MROWS * NC;
@@ -345,7 +345,7 @@ void coarse_tc_general(const Level &c, const uint8_t *links, const float *link_s
     if (!c.Abf.ptr) fail(MRHS_ERR_INVALID, "16-bit links not prepared");
     if (n < 1 || n > 64) fail(MRHS_ERR_INVALID, "tensor-core coarse stencil supports 1..64 RHS");
     const int npad = npad_of(n);
-    MRHS_CUDA(cudaMemsetAsync(c.ColScale.ptr, 0, sizeof(float) * 64, s));
+    zero_on_sms(c.ColScale.ptr, sizeof(float) * 64, s);
     const int64_t rows = in_sites * NC;
     const int rpb = 256 / n;
     const int ablocks = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(0) * 4, ceil_div(rows, 8LL * rpb)));
@@ -603,10 +603,10 @@ void coarse_parity_merge_add(const Level &c, const float2 *he, const float2 *ho,
 
 int coarse_tc_error(const Level &c, cudaStream_t s) {
     if (!c.TcErr.ptr) return 0;
-    int e = 0;
-    MRHS_CUDA(cudaMemcpyAsync(&e, c.TcErr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int *e = pinned_flag_slot();
+    read_back(e, c.TcErr.ptr, sizeof(int), s);
     MRHS_CUDA(cudaStreamSynchronize(s));
-    return e;
+    return *e;
 }
 
 }  // namespace mrhs

@@ -750,7 +750,7 @@ void CoarsestFused::solve(const Level &c, float2 *Vbasis, const float2 *b, float
     a.sync = sync.as<unsigned>();
     a.err = c.TcErr.as<int>();
     a.first_limit = tc_first_wait_limit(s);
-    MRHS_CUDA(cudaMemsetAsync(sync.ptr, 0, sizeof(unsigned) * 2, s));
+    zero_on_sms(sync.ptr, sizeof(unsigned) * 2, s);
     const size_t smem = smem_bytes(nmax);  // covers every n <= nmax (the sizes grow with n)
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)G);

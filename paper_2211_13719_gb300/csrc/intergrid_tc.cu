@@ -600,7 +600,7 @@ void intergrid_tc_prepare(Level &f, const Level &c, cudaStream_t s, bool split) 
     f.RB.alloc((size_t)c.V * 2 * a.chunks * IG_BTILE);
     f.IgErr.alloc(sizeof(int));
     f.IgBound.alloc(sizeof(float) * 128);
-    MRHS_CUDA(cudaMemsetAsync(f.IgErr.ptr, 0, sizeof(int), s));
+    zero_on_sms(f.IgErr.ptr, sizeof(int), s);
     static const float ones[64] = {1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f,
                                    1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f,
                                    1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f, 1.f,
@@ -625,7 +625,7 @@ void restrict_fields_tc(const Level &f, const Level &c, const float2 *fine, floa
     if (!unit_norm) {
         // bound[r] = max |component| of column r
         unsigned *cm = reinterpret_cast<unsigned *>(f.IgBound.as<float>() + 64);
-        MRHS_CUDA(cudaMemsetAsync(cm, 0, sizeof(unsigned) * 64, s));
+        zero_on_sms(cm, sizeof(unsigned) * 64, s);
         const int64_t rows = f.rows();
         const int rpb = 256 / n;
         const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(sm_count(0) * 4, ceil_div(rows, 16LL * rpb)));
@@ -691,10 +691,10 @@ void prolong_fields_tc(const Level &f, const Level &c, const float2 *coarse, flo
 
 int intergrid_tc_error(const Level &f, cudaStream_t s) {
     if (!f.IgErr.ptr) return 0;
-    int e = 0;
-    MRHS_CUDA(cudaMemcpyAsync(&e, f.IgErr.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int *e = pinned_flag_slot();
+    read_back(e, f.IgErr.ptr, sizeof(int), s);
     MRHS_CUDA(cudaStreamSynchronize(s));
-    return e;
+    return *e;
 }
 
 }  // namespace mrhs

@@ -136,6 +136,14 @@ void lincomb(mrhs_precision pw, void *w, mrhs_precision pb, const void *basis, i
 // dst = src / sqrt(nrm2[r]) (0 where nrm2 == 0); dst may equal src
 void scale_inv_sqrt(mrhs_precision p, void *dst, const void *src, const double *nrm2, int64_t rows, int n,
                     cudaStream_t s);
+// device-to-device copy by a kernel (bytes a multiple of 4), never queued behind the copy engines
+void copy_on_sms(void *dst, const void *src, size_t bytes, cudaStream_t s);
+// zero `bytes` (a multiple of 4) of device memory by a kernel
+void zero_on_sms(void *dst, size_t bytes, cudaStream_t s);
+// device -> page-locked host memory (cudaMallocHost) by a kernel; the caller synchronises s
+void read_back(void *pinned_host, const void *dev, size_t bytes, cudaStream_t s);
+// a page-locked int[4] of the calling host thread, for flag read-backs
+int *pinned_flag_slot();
 // dst (pd) = src (ps) elementwise conversion
 void cast(mrhs_precision pd, void *dst, mrhs_precision ps, const void *src, int64_t count, cudaStream_t s);
 // y = a*x + y with real a, same precision

@@ -150,7 +150,7 @@ struct HostCheck {
     double *res_host;      // pinned, [n]
     bool done = false;
     bool test(KrylovState &ks, int n, cudaStream_t s) {
-        MRHS_CUDA(cudaMemcpyAsync(res_host, ks.res.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        read_back(res_host, ks.res.ptr, sizeof(double) * n, s);
         MRHS_CUDA(cudaStreamSynchronize(s));
         for (int r = 0; r < n; ++r)
             if (!(res_host[r] <= target[r])) return false;
@@ -168,9 +168,9 @@ int krylov_cycle(Op &A, Precond *M, const float2 *b, float2 *x, int n, int m, KW
     const int64_t F = rows * n;
     float2 *V0 = w.Vj(0, n);
     if (x_zero) {
-        MRHS_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * F, s));
-        if (b) MRHS_CUDA(cudaMemcpyAsync(V0, b, sizeof(float2) * F, cudaMemcpyDeviceToDevice, s));
-        else MRHS_CUDA(cudaMemsetAsync(V0, 0, sizeof(float2) * F, s));
+        zero_on_sms(x, sizeof(float2) * F, s);
+        if (b) copy_on_sms(V0, b, sizeof(float2) * F, s);
+        else zero_on_sms(V0, sizeof(float2) * F, s);
     } else if (b) {
         A.residual(x, b, V0, n, s);
     } else {
@@ -295,14 +295,14 @@ void gcro_solve(Op &A, GcroWork &g, const float2 *b, float2 *x, int n, int cycle
     float2 *r = g.r.as<float2>();
     if (n != g.last_n) g.has_recycle = false;  // the recycle fields hold another RHS count's layout
     g.last_n = n;
-    MRHS_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * F, s));
-    MRHS_CUDA(cudaMemcpyAsync(r, b, sizeof(float2) * F, cudaMemcpyDeviceToDevice, s));
+    zero_on_sms(x, sizeof(float2) * F, s);
+    copy_on_sms(r, b, sizeof(float2) * F, s);
     if (g.has_recycle && k > 0) {
         // C = Q, U = U R^{-1} from A U = Q R (Gram-Schmidt on the batched fields)
         for (int i = 0; i < k; ++i) A.apply(g.fld(g.U, i, n), g.fld(g.AU, i, n), n, s);
         for (int i = 0; i < k; ++i) {
             float2 *ci = g.fld(g.C, i, n);
-            MRHS_CUDA(cudaMemcpyAsync(ci, g.fld(g.AU, i, n), sizeof(float2) * F, cudaMemcpyDeviceToDevice, s));
+            copy_on_sms(ci, g.fld(g.AU, i, n), sizeof(float2) * F, s);
             double *rii2 = g.rin2.as<double>() + (size_t)i * n;
             if (i == 0) {
                 norm2(MRHS_FP32, ci, g.rows, n, rii2, g.sc, s);
@@ -332,8 +332,8 @@ void gcro_solve(Op &A, GcroWork &g, const float2 *b, float2 *x, int n, int cycle
             gcro_coef_vec(g.coef.as<double2>(), g.Y.as<double2>(), 0, m, 1.0, n, s);
             lincomb(MRHS_FP32, x, MRHS_FP32, g.V.ptr, F, m, g.coef.as<double2>(), 1.0, g.rows, n, s);
             if (k > 0) {
-                MRHS_CUDA(cudaMemsetAsync(g.C.ptr, 0, sizeof(float2) * F * k, s));
-                MRHS_CUDA(cudaMemsetAsync(g.U.ptr, 0, sizeof(float2) * F * k, s));
+                zero_on_sms(g.C.ptr, sizeof(float2) * F * k, s);
+                zero_on_sms(g.U.ptr, sizeof(float2) * F * k, s);
                 for (int i = 0; i < k; ++i) {
                     gcro_combine(g, g.QC, g.V.ptr, 0, m + 1, g.C, i, n, s);
                     gcro_combine(g, g.PU, g.V.ptr, 0, m, g.U, i, n, s);
@@ -365,16 +365,16 @@ void gcro_solve(Op &A, GcroWork &g, const float2 *b, float2 *x, int n, int cycle
             gcro_coef_vec(g.coef.as<double2>(), g.Y.as<double2>(), k, p, 1.0, n, s);
             lincomb(MRHS_FP32, x, MRHS_FP32, g.V.ptr, F, p, g.coef.as<double2>(), 1.0, g.rows, n, s);
             // C <- [C, V_{p+1}] Q, U <- [U D, V_p] P R^{-1}
-            MRHS_CUDA(cudaMemsetAsync(g.C2.ptr, 0, sizeof(float2) * F * k, s));
-            MRHS_CUDA(cudaMemsetAsync(g.U2.ptr, 0, sizeof(float2) * F * k, s));
+            zero_on_sms(g.C2.ptr, sizeof(float2) * F * k, s);
+            zero_on_sms(g.U2.ptr, sizeof(float2) * F * k, s);
             for (int i = 0; i < k; ++i) {
                 gcro_combine(g, g.QC, g.C.ptr, 0, k, g.C2, i, n, s);
                 gcro_combine(g, g.QC, g.V.ptr, k, p + 1, g.C2, i, n, s);
                 gcro_combine(g, g.PU, g.U.ptr, 0, k, g.U2, i, n, s);
                 gcro_combine(g, g.PU, g.V.ptr, k, p, g.U2, i, n, s);
             }
-            MRHS_CUDA(cudaMemcpyAsync(g.C.ptr, g.C2.ptr, sizeof(float2) * F * k, cudaMemcpyDeviceToDevice, s));
-            MRHS_CUDA(cudaMemcpyAsync(g.U.ptr, g.U2.ptr, sizeof(float2) * F * k, cudaMemcpyDeviceToDevice, s));
+            copy_on_sms(g.C.ptr, g.C2.ptr, sizeof(float2) * F * k, s);
+            copy_on_sms(g.U.ptr, g.U2.ptr, sizeof(float2) * F * k, s);
         }
         A.residual(x, b, r, n, s);
     }
@@ -635,11 +635,11 @@ int inner_solve(mrhs_mg &mg, const float2 *b, float2 *x, int n, const std::vecto
     Op &A = *mg.ops[0];
     FinePrecond M(&mg);
     const int64_t F = A.rows * n;
-    MRHS_CUDA(cudaMemsetAsync(x, 0, sizeof(float2) * F, s));
+    zero_on_sms(x, sizeof(float2) * F, s);
     double *bn = mg.pinned + 2 * mg.nmax;
     double *target = mg.pinned + 3 * mg.nmax;
     norm2(MRHS_FP32, b, A.rows, n, mg.inner.ks.beta2.as<double>(), mg.inner.sc, s);
-    MRHS_CUDA(cudaMemcpyAsync(bn, mg.inner.ks.beta2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    read_back(bn, mg.inner.ks.beta2.ptr, sizeof(double) * n, s);
     MRHS_CUDA(cudaStreamSynchronize(s));
     for (int r = 0; r < n; ++r) target[r] = rel[r] * std::sqrt(bn[r]);
     HostCheck chk{target, mg.pinned + mg.nmax};
@@ -856,12 +856,12 @@ namespace mrhs {
 // queued on s, clear them, and fail with MRHS_ERR_TIMEOUT if one was set.
 void check_wait_flags(const Level &L, cudaStream_t s) {
     if (coarse_tc_error(L, s)) {
-        MRHS_CUDA(cudaMemsetAsync(L.TcErr.ptr, 0, sizeof(int), s));
+        zero_on_sms(L.TcErr.ptr, sizeof(int), s);
         MRHS_CUDA(cudaStreamSynchronize(s));
         fail(MRHS_ERR_TIMEOUT, "tensor-core coarse stencil gave up waiting for its operands");
     }
     if (intergrid_tc_error(L, s)) {
-        MRHS_CUDA(cudaMemsetAsync(L.IgErr.ptr, 0, sizeof(int), s));
+        zero_on_sms(L.IgErr.ptr, sizeof(int), s);
         MRHS_CUDA(cudaStreamSynchronize(s));
         fail(MRHS_ERR_TIMEOUT, "tensor-core restriction / prolongation gave up waiting");
     }
@@ -873,8 +873,8 @@ void check_all_wait_flags(const mrhs_mg &mg, cudaStream_t s) {
 
 void clear_all_wait_flags(const mrhs_mg &mg, cudaStream_t s) {
     for (int l = 0; l < mg.nlev; ++l) {
-        if (mg.lev[l].TcErr.ptr) MRHS_CUDA(cudaMemsetAsync(mg.lev[l].TcErr.ptr, 0, sizeof(int), s));
-        if (mg.lev[l].IgErr.ptr) MRHS_CUDA(cudaMemsetAsync(mg.lev[l].IgErr.ptr, 0, sizeof(int), s));
+        if (mg.lev[l].TcErr.ptr) zero_on_sms(mg.lev[l].TcErr.ptr, sizeof(int), s);
+        if (mg.lev[l].IgErr.ptr) zero_on_sms(mg.lev[l].IgErr.ptr, sizeof(int), s);
     }
 }
 
@@ -897,7 +897,7 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
     int outer = 0, inner_total = 0;
     clear_all_wait_flags(mg, s);
     norm2(MRHS_FP64, b, rows, n, mg.obn2.as<double>(), mg.osc, s);
-    MRHS_CUDA(cudaMemcpyAsync(hbn2, mg.obn2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    read_back(hbn2, mg.obn2.ptr, sizeof(double) * n, s);
     MRHS_CUDA(cudaStreamSynchronize(s));
     std::vector<double> bn2(hbn2, hbn2 + n);
     for (int r = 0; r < n; ++r) target[r] = 0.5 * tols[r] * std::sqrt(bn2[r]);
@@ -910,21 +910,21 @@ bool mg_solve(mrhs_mg &mg, const double2 *b, double2 *x, int n, const double *to
         unsigned *flag = reinterpret_cast<unsigned *>(mg.oks.nn.as<double>());
         any_nonzero(x, sizeof(double2) * F, flag, s);
         unsigned *hflag = reinterpret_cast<unsigned *>(hres);
-        MRHS_CUDA(cudaMemcpyAsync(hflag, flag, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        read_back(hflag, flag, sizeof(unsigned), s);
         MRHS_CUDA(cudaStreamSynchronize(s));
         x_zero = *hflag == 0u;
     }
     while (true) {
         // true residual in FP64 (for x = 0 it is b, whose norms are known)
         if (x_zero) {
-            MRHS_CUDA(cudaMemcpyAsync(V0, b, sizeof(double2) * F, cudaMemcpyDeviceToDevice, s));
-            MRHS_CUDA(cudaMemcpyAsync(mg.oks.beta2.ptr, mg.obn2.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            copy_on_sms(V0, b, sizeof(double2) * F, s);
+            copy_on_sms(mg.oks.beta2.ptr, mg.obn2.ptr, sizeof(double) * n, s);
             x_zero = false;
         } else {
             dslash(lat, MRHS_FP64, MRHS_FP64, x, V0, b, n, s);
             norm2(MRHS_FP64, V0, rows, n, mg.oks.beta2.as<double>(), mg.osc, s);
         }
-        MRHS_CUDA(cudaMemcpyAsync(hres, mg.oks.beta2.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        read_back(hres, mg.oks.beta2.ptr, sizeof(double) * n, s);
         MRHS_CUDA(cudaStreamSynchronize(s));
         converged = true;
         for (int r = 0; r < n; ++r) {
@@ -1296,10 +1296,10 @@ mrhs_status mrhs_coarsest_solve(mrhs_mg *mg, const void *b_dev, void *x_dev, int
     float2 *x = static_cast<float2 *>(x_dev);
     coarsest_solve(*mg, b, x, nrhs, s);
     if (W.gcro) {
-        int e = 0;
-        MRHS_CUDA(cudaMemcpyAsync(&e, W.gcro->err.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        int *e = pinned_flag_slot();
+        read_back(e, W.gcro->err.ptr, sizeof(int), s);
         MRHS_CUDA(cudaStreamSynchronize(s));
-        if (e) {
+        if (*e) {
             MRHS_CUDA(cudaMemset(W.gcro->err.ptr, 0, sizeof(int)));
             fail(MRHS_ERR_CUDA, "GCRO-DR: the QR algorithm of a harmonic Ritz problem did not converge");
         }
