@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = dict(dims=(24, 24, 24, 64), eps=0.25, gauge_seed=1301, source_seed=2301, mass=-0.13, csw=1.0,
                 nrhs=48, tol=1e-10, n_levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nvec=[32, 32])
-MG_PARAMS = dict(setup_sweeps=6, setup_m=8, smooth_m=3, coarse_m=14, coarse_cycles=1, inter_m=4, inner_m=8,
+MG_PARAMS = dict(setup_sweeps=6, setup_m=8, smooth_m=3, coarse_m=14, coarse_cycles=1, inter_m=4, inner_m=5,
                  inner_max_iters=200, inner_tol=1e-5, outer_m=4, max_outer_iters=30, smoother_evenodd=1)
 # the kernel with the largest share of a timed solve in the profiler's launch list (the even-odd
 # hopping kernel of the fine smoother's Schur operator), and the full-lattice fine stencil; the
