@@ -167,9 +167,10 @@ int krylov_cycle(Op &A, Precond *M, const float2 *b, float2 *x, int n, int m, KW
     const int64_t rows = A.rows;
     const int64_t F = rows * n;
     float2 *V0 = w.Vj(0, n);
+    const float2 *r0 = V0;  // the initial residual; from a zero x it is b itself, normalised into V0 directly
     if (x_zero) {
         zero_on_sms(x, sizeof(float2) * F, s);
-        if (b) copy_on_sms(V0, b, sizeof(float2) * F, s);
+        if (b) r0 = b;
         else zero_on_sms(V0, sizeof(float2) * F, s);
     } else if (b) {
         A.residual(x, b, V0, n, s);
@@ -178,9 +179,9 @@ int krylov_cycle(Op &A, Precond *M, const float2 *b, float2 *x, int n, int m, KW
         scale_real(MRHS_FP32, -1.0, V0, F, s);
     }
     KrylovState &ks = w.ks;
-    norm2(MRHS_FP32, V0, rows, n, ks.beta2.as<double>(), w.sc, s);
+    norm2(MRHS_FP32, r0, rows, n, ks.beta2.as<double>(), w.sc, s);
     krylov_start(ks, n, s);
-    scale_inv_sqrt(MRHS_FP32, V0, V0, ks.beta2.as<double>(), rows, n, s);
+    scale_inv_sqrt(MRHS_FP32, V0, r0, ks.beta2.as<double>(), rows, n, s);
     int steps = m;
     for (int j = 0; j < m; ++j) {
         const float2 *vj = w.Vj(j, n);
